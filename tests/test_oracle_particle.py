@@ -1,0 +1,138 @@
+"""Pins of the oracle's rigid-body update (Sec. 2.3) and of the coupled step.
+
+Closed forms: constant-acceleration leap-frog, angular momentum conservation
+of the torque-free update, the exact norm growth and rotation angle of the
+orientation predictor-corrector for a spin about a fixed axis, agreement of
+the printed and the angular-momentum rotation forms for a sphere."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2408_15115_gb300 import inputs as I
+
+
+def _sim_with(verts, tris, kappa=2.0, g=(0, 0, 0), rot_form=0, gravity=0, n=16):
+    s = O.Sim(n, n, n, tau=0.8, kappa=kappa, g=g, rot_form=rot_form, gravity=gravity)
+    s.init_fields()
+    s.load_particle(verts, tris, r0=(n / 2 - 0.3, n / 2 + 0.1, n / 2 + 0.2))
+    return s
+
+
+def test_constant_acceleration_leapfrog_exact():
+    V, T = I.icosphere(2, 2.0)
+    kappa, g = 2.5, np.array([0.0, 0.0, -1e-3])
+    s = _sim_with(V, T, kappa, g)
+    st = s.state()
+    m = kappa * st["volume"]
+    F = np.array([1e-3, -2e-3, 5e-4])
+    r0 = np.array([3.0, 4.0, 5.0])
+    v0 = np.array([1e-3, 0.0, -2e-3])
+    s.set_particle_dyn(r0, np.eye(3), v0, np.zeros(3), np.zeros(3), F, np.zeros(3))
+    n = 50
+    s.advance_particle_only(n)
+    a = (1 - 1 / kappa) * g + F / m
+    st = s.state()
+    assert np.abs(st["v"] - (v0 + n * a)).max() < 1e-15
+    assert np.abs(st["r"] - (r0 + n * v0 + a * n * (n + 1) / 2)).max() < 1e-12
+
+
+def test_literal_gravity_flag():
+    V, T = I.icosphere(2, 2.0)
+    s = _sim_with(V, T, 2.0, (0, 0, -1e-3), gravity=1)
+    s.set_particle_dyn(np.zeros(3) + 8, np.eye(3), np.zeros(3), np.zeros(3), np.zeros(3), np.zeros(3), np.zeros(3))
+    s.advance_particle_only(1)
+    assert abs(s.state()["v"][2] + 1e-3) < 1e-18
+
+
+def _dyn(s):
+    st = s.state()
+    return st["d"], st["w"], st["L"]
+
+
+def _torque_free_run(scale, n):
+    V, T = I.ellipsoid(3, (4.0, 2.5, 1.5))
+    s = _sim_with(V, T, 2.0)
+    st = s.state()
+    m = 2.0 * st["volume"]
+    Jb = m * st["J_over_m"]
+    w0 = scale * np.array([2e-3, -1e-3, 3e-3])
+    L0 = Jb @ w0
+    s.set_particle_dyn(np.zeros(3) + 8, np.eye(3), np.zeros(3), w0, L0, np.zeros(3), np.zeros(3))
+    s.advance_particle_only(n)
+    d, w, L = _dyn(s)
+    return L0, L, d, 0.5 * w @ L / (0.5 * w0 @ L0) - 1
+
+
+def test_torque_free_angular_momentum_and_energy():
+    # angular-momentum form (reading of Sec. 2.3): L is conserved exactly; the
+    # frame M(t) used for omega(t+1/2) makes the energy error first order in
+    # the turn per step, so at a fixed total turn it halves when the step turn halves
+    L0, L, d, e1 = _torque_free_run(1.0, 5000)
+    assert np.array_equal(L, L0)
+    # frame norm grows by at most |w|^4/4 per step (closed form of the spin test below)
+    wmag = np.linalg.norm([2e-3, -1e-3, 3e-3])
+    assert np.abs(d @ d.T - np.eye(3)).max() < 5000 * wmag ** 4
+    _, _, _, e2 = _torque_free_run(0.5, 10000)
+    assert abs(e1) < 0.01
+    assert 1.8 < e1 / e2 < 2.2
+
+
+def test_spin_about_fixed_axis_closed_form():
+    # sphere, omega along z: d' = d + w x d + (w x (w x d))/2, so for d perpendicular to w
+    # |d'|^2 = |d|^2 (1 + w^4/4) and the turn per step is atan2(w, 1 - w^2/2)
+    V, T = I.icosphere(2, 2.0)
+    s = _sim_with(V, T, 2.0)
+    st = s.state()
+    m = 2.0 * st["volume"]
+    Jb = m * st["J_over_m"]
+    om = 0.05
+    w0 = np.array([0, 0, om])
+    s.set_particle_dyn(np.zeros(3) + 8, np.eye(3), np.zeros(3), w0, Jb @ w0, np.zeros(3), np.zeros(3))
+    n = 200
+    s.advance_particle_only(n)
+    d, w, L = _dyn(s)
+    # sphere inertia from a polyhedron is isotropic to rounding, so omega stays on z
+    assert abs(np.dot(d[0], d[0]) - (1 + om ** 4 / 4) ** n) < 1e-12
+    ang = math.atan2(d[0][1], d[0][0])
+    want = (n * math.atan2(om, 1 - om * om / 2) + math.pi) % (2 * math.pi) - math.pi
+    assert abs(ang - want) < 1e-10
+    assert np.abs(d[2] - np.array([0, 0, 1])).max() < 1e-14
+
+
+def test_literal_rotation_equals_angmom_for_sphere():
+    V, T = I.icosphere(3, 2.0)
+    out = []
+    for rf in (0, 1):
+        s = _sim_with(V, T, 2.0, rot_form=rf)
+        st = s.state()
+        m = 2.0 * st["volume"]
+        Jb = m * st["J_over_m"]
+        w0 = np.array([1e-3, 2e-3, -1e-3])
+        Tq = np.array([1e-4, -3e-4, 2e-4])
+        s.set_particle_dyn(np.zeros(3) + 8, np.eye(3), np.zeros(3), w0, Jb @ w0, np.zeros(3), Tq)
+        s.advance_particle_only(30)
+        out.append(_dyn(s)[1])
+    assert np.abs(out[0] - out[1]).max() < 1e-6 * np.abs(out[0]).max()
+
+
+def test_coupled_rest_state_stays_at_rest():
+    V, T = I.icosphere(3, 3.0)
+    s = O.Sim(16, 16, 16, tau=0.7, kappa=2.0, g=(0, 0, 0), bc_bottom=1, bc_top=1)
+    s.init_fields()
+    s.load_particle(V, T, r0=(8.2, 7.9, 8.1))
+    s.step(3)
+    st = s.state()
+    # nothing drives the fluid or the body: only rounding of the rest populations remains
+    assert np.abs(st["F"]).max() < 1e-13 and np.abs(st["v"]).max() < 1e-16
+    xi, w = O.lattice()
+    assert np.abs(s.f() - w).max() < 1e-15
+
+
+def test_marker_too_close_to_wall_rejected():
+    V, T = I.icosphere(2, 3.0)
+    s = O.Sim(16, 16, 16, tau=0.7, kappa=2.0, bc_bottom=1, bc_top=1)
+    s.init_fields()
+    with pytest.raises(ValueError):
+        s.load_particle(V, T, r0=(8.0, 8.0, 3.5))
