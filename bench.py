@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the Turret hot path on one GB300 (or N replicas, one per GPU).
+
+Workload: the 96 x 96 x 192 sliding turret window with a prolate spheroid
+16:8:8 (812 surface markers) tilted 30 degrees, nu = 0.02, kappa = 2, Re ~ 10,
+FP32 population storage.  One step = collide+stream over every window cell,
+particle update, window slide, stress/velocity on the support box, surface
+force/torque and four IBM cycles (one replay of the step's CUDA graph).
+
+Printed JSON line (rank 0):
+  value     window cells x steps / s over the timed steps, in GLUPS (all ranks)
+  roofline  the fused collide+stream kernel timed alone: 216 algorithmic
+            bytes per cell / its mean launch time, against the measured HBM
+            copy bandwidth
+  e2e       the same metric through the public C ABI from host data:
+            context + surface upload + steps with a particle-state read
+            after every step
+  cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the
+            same workload
+--impl reference times the oracle alone as the reference arm.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & %HBM roofline per RR-LBM+IBM step; mixed/batched vs FP32 at ≤1% drag err"
+BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}
+K1_PROFILE = os.path.join(ROOT, "profiles", "k_collide_stream_prolate_96x96x192.md")
+K1_SOURCE = os.path.join(ROOT, "paper_2408_15115_gb300", "csrc", "lbm_kernels.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="prolate_turret")
+    p.add_argument("--storage", default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the collide+stream kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    try:
+        txt = open(K1_PROFILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(K1_SOURCE, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("machine:"):
+            for kv in line[len("machine:"):].split():
+                k, _, v = kv.partition("=")
+                vals[k] = v
+    if vals.get("source_sha256_16") != src_hash or "dram_bytes_per_launch" not in vals:
+        return None
+    return float(vals["dram_bytes_per_launch"])
+
+
+def oracle_sample(cfg, budget_s=15.0, max_steps=None):
+    """Time the FP64 oracle on the workload: coupled steps of the full window
+    from rest; returns (cells*steps/s in GLUPS, threads, steps, seconds)."""
+    from oracle import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    bc = cfg["bc"]
+    s = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], 3 * cfg["nu"] + 0.5, *bc, sponge=cfg["sponge"], slide=cfg["slide"],
+              anchor_frac=cfg["anchor"], kappa=cfg["kappa"], g=cfg["g"])
+    s.init_fields()
+    s.load_particle(cfg["verts"], cfg["tris"], cfg["r0"])
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(t1, 1e-6)))
+    if max_steps is not None:
+        n = min(n, max_steps)
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    return cells * n / dt / 1e9, O.get_threads(), n, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2408_15115_gb300 import configs
+    cfg = configs.WORKLOADS[args.workload]()
+    # each reference step is one coupled oracle step of the full window; the
+    # count is capped so the whole arm ends within a few minutes
+    budget = 150.0
+    from oracle import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    s = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], 3 * cfg["nu"] + 0.5, *cfg["bc"], sponge=cfg["sponge"],
+              slide=cfg["slide"], anchor_frac=cfg["anchor"], kappa=cfg["kappa"], g=cfg["g"])
+    s.init_fields()
+    s.load_particle(cfg["verts"], cfg["tris"], cfg["r0"])
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    warm = min(args.warmup, 1)
+    if warm > 1:
+        s.step(warm - 1)
+    k = max(1, min(args.steps, int(budget / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(k)
+    dt = time.perf_counter() - t0
+    v = cells * k / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": args.gpus,
+           "steps": k, "warmup": warm, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
+                      "steps_requested": args.steps},
+           "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
+                            "sample": "%d coupled FP64 oracle steps of the full %s window (of %d requested)" %
+                                      (k, cfg["name"], args.steps)},
+           "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2408_15115_gb300 import build as B
+    from paper_2408_15115_gb300 import configs
+
+    rank, world, local = dist_env()
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = configs.WORKLOADS[args.workload]() if args.storage is None else \
+        configs.WORKLOADS[args.workload](storage=args.storage)
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    # ---- device-resident timed steps ------------------------------------
+    t = configs.make_turret(cfg, device=dev)
+    t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
+    st = t.stream
+    t.step(W)  # first calls capture the two per-parity step graphs
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        ev0.record(st)
+        t.step(K)
+        ev1.record(st)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    clocks = clk.summary()
+    state = t.state()
+    kps = state["kernels_per_step"]
+    value = world * cells * K / (ms / 1e3) / 1e9
+
+    # ---- the fused collide+stream kernel alone (roofline) -------------------
+    t.fluid_step(W)
+    torch.cuda.synchronize(dev)
+    k1_launches = max(200, min(K, 5000))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    t.fluid_step(k1_launches)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    k1_ms = e0.elapsed_time(e1) / k1_launches
+    bpc = BYTES_PER_CELL[cfg["storage"]]
+    peaks, peak_kind = measured_peaks()
+    achieved = bpc * cells / (k1_ms / 1e3) / 1e9
+    traffic = profile_traffic()
+    t.close()
+    del t
+
+    # ---- end to end through the C ABI from host data ----------------------
+    from paper_2408_15115_gb300 import turret as T
+    V = np.ascontiguousarray(cfg["verts"])
+    Tr = np.ascontiguousarray(cfg["tris"], dtype=np.int32)
+    K2 = K
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    t2 = configs.make_turret(cfg, device=dev)
+    t2.load_surface(V, Tr, cfg["r0"])
+    for _ in range(K2):
+        t2.step(1)
+        t2.state()
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    t2.close()
+    e2e = {"value": world * cells * K2 / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": (V.nbytes + Tr.nbytes) / K2,
+           "d2h_bytes_per_step": __import__("ctypes").sizeof(T.ParticleState),
+           "includes": "context creation, surface upload, and a particle-state read after every step"}
+
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": cfg["storage"], "data": "synthetic",
+           "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
+                      "storage": cfg["storage"], "nu": cfg["nu"], "kappa": cfg["kappa"], "g": cfg["g"][2],
+                      "l2": "inputs larger than L2 (two population buffers of %d MB)" % (27 * cells * bpc // 2 // 2**20),
+                      "replicas": world},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                        "kernel": "k_collide_stream", "algorithmic_bytes_per_launch": bpc * cells,
+                        "us_per_launch": 1e3 * k1_ms, "glups_kernel": cells / (k1_ms / 1e3) / 1e9,
+                        "peak_kind": peak_kind,
+                        "whole_step_frac": (bpc * cells / (ms / K / 1e3) / 1e9) / peaks["hbm_gbs"]},
+           "e2e": e2e, "gpu_launches": kps * K, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, n, dt = oracle_sample(cfg)
+        out["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                               "sample": "%d coupled FP64 oracle steps of the full %s window from rest (%.1f s)" %
+                                         (n, cfg["name"], dt)}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * turret.h -- C ABI of libturret.so, the GB300 (sm_103a) hot path of one time
+ * step of the Palabos Turret method (Bhowmick, Latt, Wang, Bagheri,
+ * arXiv 2408.15115): recursive-regularized D3Q27 lattice Boltzmann
+ * collide+stream over a window that follows a settling particle, immersed-
+ * boundary multi-direct forcing on the particle's surface markers, the
+ * stress-based surface force and torque, and the rigid-body (6DOF) update.
+ *
+ * Conventions shared by every call
+ *   - Lattice units: dx = dt = 1, rho_0 = 1, c_s^2 = 1/3 (Sec. 2.1).
+ *   - Window coordinates: cell centres at integer (x, y, z), 0 <= x < nx, ...;
+ *     x is the fastest index of every field; z is "up" (gravity along -z).
+ *   - Device memory is owned by the caller.  lbm_init and ibm_load_surface
+ *     borrow a caller-allocated device workspace (sizes from the *_bytes
+ *     queries) until lbm_destroy; host arrays are copied during the call.
+ *   - Every call enqueues its GPU work on the caller's CUDA stream given to
+ *     lbm_init.  Only query_particle_state, lbm_copy_* and lbm_set_fields wait
+ *     for the stream.
+ *   - Errors: every call returns a turret_status; nothing aborts or throws
+ *     across the ABI.  turret_last_error() holds a message for the last
+ *     failure.  Conditions detected on the device during step() (a marker
+ *     stencil leaving the window, a non-finite force) are latched in a device
+ *     status word and returned by the next query_particle_state().
+ */
+#ifndef TURRET_H
+#define TURRET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TURRET_API __attribute__((visibility("default")))
+#else
+#define TURRET_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct turret_ctx turret_ctx;
+
+typedef enum {
+    TURRET_OK = 0,
+    TURRET_EINVAL = 1,    /* invalid argument (sizes, tau <= 1/2, bad mesh, ...)      */
+    TURRET_ENOMEM = 2,    /* workspace too small                                       */
+    TURRET_ECUDA = 3,     /* a CUDA runtime call failed                                */
+    TURRET_ESTATE = 4,    /* call out of order (e.g. step before ibm_load_surface)     */
+    TURRET_EDIVERGED = 5, /* non-finite force or torque                                */
+    TURRET_ETIMEOUT = 6,  /* a bounded device wait gave up                             */
+    TURRET_EDOMAIN = 7    /* a marker stencil left the window along a closed axis      */
+} turret_status;
+
+typedef enum { TURRET_D3Q27 = 27 } turret_lattice;
+
+/* Population storage.  Populations are stored as deviations q_i = f_i - w_i
+ * from the rest equilibrium: FP32 as is; FP16 as q_i * 16 / w_i; BF16 as
+ * q_i / w_i (round to nearest even).  Arithmetic is FP32 in every case.     */
+typedef enum { TURRET_F32 = 0, TURRET_F16 = 1, TURRET_BF16 = 2 } turret_storage;
+
+enum { TURRET_BC_PERIODIC = 0, TURRET_BC_NOSLIP = 1, TURRET_BC_PRESSURE = 2 };
+
+/* Simulation window (Sec. 2.5, Fig. 1).  bc_x, bc_y: periodic or no-slip
+ * (halfway bounce-back).  bc_bottom: periodic or no-slip.  bc_top: periodic,
+ * no-slip or constant pressure (ghost plane at rest density with the velocity
+ * of the top plane).  sponge_cells: planes below the top over which tau rises
+ * linearly to 1 on the top plane.  slide = 1: the window follows the particle
+ * vertically as a ring buffer (replaces the re-injection copy of Sec. 2.5);
+ * the particle centre is kept within one cell of z = anchor_frac * nz.      */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t bc_x, bc_y;
+    int32_t bc_bottom, bc_top;
+    int32_t sponge_cells;
+    int32_t slide;
+    int32_t pad0;
+    double anchor_frac;
+} turret_window;
+
+/* Readings of points the paper leaves open (all default 0):
+ *   force_scheme 0: f* = (1-1/tau) f0(u) + (1/tau) f0(u + tau h) + (1-1/tau) f1
+ *                   (adds rho h per step); 1: Eq. 15 as printed.
+ *   rot_form     0: angular momentum L advanced by T, omega = M^T J^-1 M L;
+ *                1: omega advanced by M^T J^-1 M T as printed (Sec. 2.3).
+ *   gravity      0: g_eff = (1 - 1/kappa) g (buoyancy); 1: g as printed.
+ *   renorm_orientation 1: modified Gram-Schmidt of d_0, d_1, d_2 each step.
+ *   ibm_cycles: number n of IBM cycles (Sec. 2.2: n = 4).
+ *   no_graph 1: launch every kernel of a step directly instead of replaying a
+ *               captured CUDA graph (same results; for debugging).           */
+typedef struct {
+    int32_t force_scheme;
+    int32_t rot_form;
+    int32_t gravity;
+    int32_t renorm_orientation;
+    int32_t ibm_cycles;
+    int32_t no_graph;
+} turret_flags;
+
+/* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates
+ * (window origin included), d = rows d_0, d_1, d_2 of the orientation matrix M,
+ * v, w at t - 1/2 (leap-frog), F, T = hydrodynamic force and torque at t
+ * (rho_f = 1), L = angular momentum at t - 1/2, origin = global coordinates of
+ * window cell (0, 0, 0), step = t, status = latched device status.           */
+typedef struct {
+    double r[3], d[9], v[3], w[3], F[3], T[3], L[3];
+    int64_t origin[3];
+    int64_t step;
+    int32_t status;
+    int32_t n_markers;
+    double volume;   /* particle volume V                                  */
+    double area;     /* surface area, sum of the marker areas dS_k          */
+    int32_t kernels_per_step;  /* kernel launches one step() enqueues      */
+    int32_t pad0;
+} turret_particle_state;
+
+/* ---- fluid ------------------------------------------------------------- */
+
+/* Bytes of device workspace lbm_init needs for this window and storage.     */
+TURRET_API size_t lbm_workspace_bytes(const turret_window *win, turret_storage st);
+
+/* Creates a context.  nu: kinematic viscosity, tau = 3 nu + 1/2 (Eq. 9), must
+ * give tau > 1/2.  rho_ratio: kappa = rho_p / rho_f.  g: gravity (3 doubles).
+ * device_workspace: >= lbm_workspace_bytes bytes of device memory, 256-byte
+ * aligned.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * The fluid starts at rest (all deviations zero).  *out receives the context. */
+TURRET_API turret_status lbm_init(turret_ctx **out, const turret_window *win, turret_lattice lat, double nu,
+                       double rho_ratio, const double g[3], turret_storage st, void *device_workspace,
+                       size_t workspace_bytes, void *cuda_stream);
+
+/* Replaces the reading flags (before ibm_load_surface). */
+TURRET_API turret_status lbm_set_flags(turret_ctx *c, const turret_flags *flags);
+
+/* Sets the state to the equilibrium of the given host fields, as the
+ * post-collision populations at t = -1: rho (nz*ny*nx doubles, NULL = 1) and
+ * u (nz*ny*nx*3 doubles, (x,y,z) per cell, NULL = 0), z-major then y then x.
+ * The pressure-ghost velocity is the u of the top plane.  Synchronous.      */
+TURRET_API turret_status lbm_set_fields(turret_ctx *c, const double *rho, const double *u);
+
+/* ---- particle ------------------------------------------------------------ */
+
+/* Bytes of device workspace ibm_load_surface needs for this surface.        */
+TURRET_API size_t ibm_workspace_bytes(const turret_ctx *c, const double *verts_body, int64_t n_verts, const int32_t *tris,
+                           int64_t n_tris);
+
+/* Loads the particle surface (Sec. 2.2: the mesh vertices are the Lagrangian
+ * markers; dS_k is one third of the area of the triangles sharing vertex k).
+ * verts_body: n_verts x 3 doubles; tris: n_tris x 3 int32, counter-clockwise
+ * seen from outside; the mesh must be closed.  The body is re-centred on its
+ * centre of mass; body frame = lab frame at t = 0.  r0: centre of mass in
+ * window coordinates; v0, w0: v(-1/2), omega(-1/2).  Computes F(0), T(0) and
+ * h_imm(0) (Table 1 events 3 and 4 at t = 0).  device_workspace: >=
+ * ibm_workspace_bytes bytes, 256-byte aligned.                               */
+TURRET_API turret_status ibm_load_surface(turret_ctx *c, const double *verts_body, int64_t n_verts, const int32_t *tris,
+                               int64_t n_tris, const double r0[3], const double v0[3], const double w0[3],
+                               void *device_workspace, size_t workspace_bytes);
+
+/* ---- time stepping ---------------------------------------------------------- */
+
+/* Advances n coupled time steps in the order of Table 1: collide+stream with
+ * h_imm(t), particle update with F(t), T(t), window slide, stress and velocity
+ * at t+1 on the support box, F(t+1), T(t+1), IBM cycles -> h_imm(t+1).
+ * Without a particle, advances the fluid alone.  Asynchronous; replays a CUDA
+ * graph per step after the first call.                                      */
+TURRET_API turret_status step(turret_ctx *c, int64_t n);
+
+/* Advances the fluid alone by n collide+stream steps (Eq. 7 / Eq. 15 with
+ * h_imm held at its current value; the particle does not move).  Launches
+ * only the fused collide+stream kernel; asynchronous.                      */
+TURRET_API turret_status lbm_fluid_step(turret_ctx *c, int64_t n);
+
+/* Copies the particle state to the host (waits for the stream); returns the
+ * latched device status (TURRET_EDOMAIN, TURRET_EDIVERGED) if one was set.   */
+TURRET_API turret_status query_particle_state(turret_ctx *c, turret_particle_state *out);
+
+/* Density and unforced velocity u = sum xi f / sum f of f(t) at every cell
+ * (Eqs. 5-6), written to caller device memory dev_out as 4 planes
+ * [rho, u_x, u_y, u_z][nz][ny][nx] of floats in window order.  Waits.        */
+TURRET_API turret_status lbm_copy_macro(turret_ctx *c, float *dev_out);
+
+/* Deviations q_i = f_i(t) - w_i of the pre-collision populations at every
+ * cell, written as float [27][nz][ny][nx] in window order, population index
+ * i = (xi_x+1) + 3 (xi_y+1) + 9 (xi_z+1).  Waits.                           */
+TURRET_API turret_status lbm_copy_populations(turret_ctx *c, float *dev_out);
+
+/* Releases the context (not the caller's workspaces).                       */
+TURRET_API turret_status lbm_destroy(turret_ctx *c);
+
+/* Message of the last failure on this context (or of the last failed
+ * lbm_init when c is NULL).                                                 */
+TURRET_API const char *turret_last_error(const turret_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TURRET_H */

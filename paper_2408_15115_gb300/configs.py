@@ -1,0 +1,78 @@
+"""Synthetic workloads in lattice units (dx = dt = 1) for the settling cases.
+
+Each workload keeps the paper's set-up (Sec. 2.5 and Table 2): a window that
+is periodic laterally, no-slip at the bottom, constant pressure with a sponge
+at the top, the time step normalised so that the terminal velocity is about
+0.02 (Sec. 3 opening), gravity along -z.  Where only a Reynolds number is
+given, g follows from the Clift-Gauvin drag curve (Eq. 28) for the
+volume-equivalent sphere with the buoyancy-reduced weight:
+(kappa - 1) V g = C_D(Re) pi d^2 v^2 / 8.
+"""
+import math
+
+import numpy as np
+
+from . import inputs as I
+
+
+def cg71_cd(re):
+    """Clift & Gauvin (1971) drag coefficient, Eq. 28."""
+    return 24.0 / re * (1.0 + 0.15 * re ** 0.687) + 0.42 / (1.0 + 4.25e4 * re ** -1.16)
+
+
+def gravity_for(re, d, nu, kappa):
+    """|g| (lattice units) that makes a sphere of diameter d settle at Reynolds number re."""
+    v = re * nu / d
+    return 3.0 * cg71_cd(re) * v * v / (4.0 * d * (kappa - 1.0))
+
+
+def sphere_box():
+    """32 x 32 x 64 closed box, sphere d = 8 (252 markers), nu 0.05, kappa 2.5, g 1e-5 (Re ~ 0.2)."""
+    V, T = I.sphere(5, 8.0)
+    return dict(name="sphere_32x32x64_closed", nx=32, ny=32, nz=64, nu=0.05, kappa=2.5, g=(0.0, 0.0, -1e-5),
+                bc=(1, 1, 1, 1), sponge=0, slide=0, anchor=0.25, storage="f32", verts=V, tris=T,
+                r0=(15.5, 15.5, 44.0))
+
+
+def prolate_turret(storage="f32"):
+    """96 x 96 x 192 sliding turret window, prolate spheroid 16:8:8 (812 markers)
+    tilted 30 degrees about x, nu 0.02, kappa 2, g from Eq. 28 at Re ~ 10."""
+    V, T = I.ellipsoid(9, (4.0, 8.0, 4.0))  # major axis (16) along y
+    V = I.rotate(V, "x", 30.0)
+    d_eq = (6.0 * (4.0 / 3.0) * math.pi * 4.0 * 8.0 * 4.0 / math.pi) ** (1.0 / 3.0)
+    nu, kappa = 0.02, 2.0
+    g = gravity_for(10.0, d_eq, nu, kappa)
+    return dict(name="prolate_96x96x192_turret", nx=96, ny=96, nz=192, nu=nu, kappa=kappa, g=(0.0, 0.0, -g),
+                bc=(0, 0, 1, 2), sponge=15, slide=1, anchor=0.25, storage=storage, verts=V, tris=T,
+                r0=(47.5, 47.5, 48.0), d_eq=d_eq)
+
+
+def irregular_turret(storage="f16"):
+    """192 x 192 x 384 window, spherical-harmonic particle d_eq = 24 (3612 markers), Re ~ 200."""
+    V, T = I.sh_particle(19, 24.0, seed=3)
+    nu, kappa = 0.02 * 24.0 / 200.0, 2.0
+    g = gravity_for(200.0, 24.0, nu, kappa)
+    return dict(name="irregular_192x192x384_turret", nx=192, ny=192, nz=384, nu=nu, kappa=kappa, g=(0.0, 0.0, -g),
+                bc=(0, 0, 1, 2), sponge=30, slide=1, anchor=0.25, storage=storage, verts=V, tris=T,
+                r0=(95.5, 95.5, 96.0), d_eq=24.0)
+
+
+def irregular_large(storage="f16"):
+    """256 x 256 x 512 window, spherical-harmonic particle d_eq = 32 (6252 markers), Re ~ 1000."""
+    V, T = I.sh_particle(25, 32.0, seed=5)
+    nu, kappa = 0.02 * 32.0 / 1000.0, 2.0
+    g = gravity_for(1000.0, 32.0, nu, kappa)
+    return dict(name="irregular_256x256x512_turret", nx=256, ny=256, nz=512, nu=nu, kappa=kappa, g=(0.0, 0.0, -g),
+                bc=(0, 0, 1, 2), sponge=40, slide=1, anchor=0.25, storage=storage, verts=V, tris=T,
+                r0=(127.5, 127.5, 128.0), d_eq=32.0)
+
+
+WORKLOADS = {"sphere_box": sphere_box, "prolate_turret": prolate_turret, "irregular_turret": irregular_turret,
+             "irregular_large": irregular_large}
+
+
+def make_turret(cfg, **kw):
+    from .turret import Turret
+    t = Turret(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nu"], cfg["kappa"], cfg["g"], *cfg["bc"], sponge=cfg["sponge"],
+               slide=cfg["slide"], anchor_frac=cfg["anchor"], storage=cfg["storage"], **kw)
+    return t

@@ -1,0 +1,595 @@
+// turret_api.cu -- the extern "C" boundary of libturret.so (include/turret.h):
+// context creation over caller-owned device workspaces, surface loading with
+// host FP64 mesh properties, and the per-step launch sequence captured as one
+// CUDA graph per ping-pong parity.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/turret.h"
+#include "turret_internal.cuh"
+
+using namespace turret;
+
+struct turret_ctx {
+    turret_window win;
+    turret_flags flags;
+    int storage;
+    double nu, tau0, kappa, g[3];
+    cudaStream_t stream;
+    Geom geom;
+    // fluid workspace
+    void *f[2];
+    float *utop[2];
+    DevState *dstate;
+    double *scratch_d;  // lbm_set_fields staging (aliases the idle population buffer)
+    // particle
+    bool has_particle;
+    int nm;
+    BodyConst body;
+    BoxGeom box;
+    MarkerArrays mk;
+    BoxArrays ba;
+    int *tile_list, *tile_count;
+    int cap;
+    double *partials;
+    double vol, area;
+    DevState host_state;
+    DevState *pinned;  // page-locked staging of the device state for queries
+    std::vector<float> staging;
+    // stepping
+    long long step;
+    cudaGraphExec_t graph[2];
+    bool graph_ready[2];
+    std::string err;
+};
+
+static std::string g_init_err;
+
+static turret_status fail(turret_ctx *c, turret_status s, const std::string &msg) {
+    if (c) c->err = msg; else g_init_err = msg;
+    return s;
+}
+
+static turret_status cuda_fail(turret_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, TURRET_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+// Sequential 256-byte-aligned carving of a caller workspace (or size count).
+struct Carver {
+    char *base;
+    size_t off;
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+static bool valid_window(const turret_window *w) {
+    if (!w || w->nx < 1 || w->ny < 1 || w->nz < 1) return false;
+    if (w->bc_x < 0 || w->bc_x > 1 || w->bc_y < 0 || w->bc_y > 1) return false;
+    if (w->bc_bottom < 0 || w->bc_bottom > 1 || w->bc_top < 0 || w->bc_top > 2) return false;
+    if ((w->bc_bottom == TURRET_BC_PERIODIC) != (w->bc_top == TURRET_BC_PERIODIC)) return false;
+    if (w->sponge_cells < 0 || w->sponge_cells > w->nz) return false;
+    if (w->slide && (w->bc_bottom == TURRET_BC_PERIODIC)) return false;
+    if (w->slide && !(w->anchor_frac > 0.0 && w->anchor_frac < 1.0)) return false;
+    if ((long long)w->nx * w->ny * w->nz > (1LL << 31) / 27) return false;
+    return true;
+}
+
+static void carve_fluid(Carver &cv, const turret_window *w, int st, void **f, float **utop, DevState **ds) {
+    const size_t ncell = (size_t)w->nx * w->ny * w->nz, plane = (size_t)w->nx * w->ny;
+    for (int k = 0; k < 2; ++k) f[k] = cv.take(27 * ncell * storage_bytes(st));
+    for (int k = 0; k < 2; ++k) utop[k] = (float *)cv.take(3 * plane * sizeof(float));
+    *ds = (DevState *)cv.take(sizeof(DevState));
+}
+
+extern "C" size_t lbm_workspace_bytes(const turret_window *win, turret_storage st) {
+    if (!valid_window(win) || st < 0 || st > 2) return 0;
+    Carver cv{nullptr, 0};
+    void *f[2];
+    float *u[2];
+    DevState *ds;
+    carve_fluid(cv, win, (int)st, f, u, &ds);
+    return cv.off + 256;
+}
+
+extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, turret_lattice lat, double nu,
+                                  double rho_ratio, const double g[3], turret_storage st, void *ws,
+                                  size_t ws_bytes, void *stream) {
+    turret_ctx *c = nullptr;
+    if (!out) return fail(c, TURRET_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (lat != TURRET_D3Q27) return fail(c, TURRET_EINVAL, "only the D3Q27 lattice is supported");
+    if (!valid_window(win)) return fail(c, TURRET_EINVAL, "invalid window");
+    if (st < 0 || st > 2) return fail(c, TURRET_EINVAL, "invalid storage");
+    const double tau = 3.0 * nu + 0.5;  // nu = c_s^2 (tau - 1/2), Eq. 9
+    if (!(nu > 0.0) || !(tau > 0.5) || !isfinite(tau)) return fail(c, TURRET_EINVAL, "nu must give tau > 1/2");
+    if (!(rho_ratio > 0.0) || !isfinite(rho_ratio)) return fail(c, TURRET_EINVAL, "rho_ratio must be positive");
+    if (!g || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) return fail(c, TURRET_EINVAL, "invalid g");
+    const size_t need = lbm_workspace_bytes(win, st);
+    if (!ws || ws_bytes < need) return fail(c, TURRET_ENOMEM, "fluid workspace too small");
+    if (((uintptr_t)ws & 255) != 0) return fail(c, TURRET_EINVAL, "workspace must be 256-byte aligned");
+
+    c = new turret_ctx();
+    c->win = *win;
+    memset(&c->flags, 0, sizeof c->flags);
+    c->flags.ibm_cycles = 4;
+    c->storage = (int)st;
+    c->nu = nu;
+    c->tau0 = tau;
+    c->kappa = rho_ratio;
+    for (int a = 0; a < 3; ++a) c->g[a] = g[a];
+    c->stream = (cudaStream_t)stream;
+    Geom &G = c->geom;
+    G.nx = win->nx; G.ny = win->ny; G.nz = win->nz;
+    G.bc_x = win->bc_x; G.bc_y = win->bc_y; G.bc_bottom = win->bc_bottom; G.bc_top = win->bc_top;
+    G.sponge = win->sponge_cells;
+    G.plane = (long long)win->nx * win->ny;
+    G.ncell = G.plane * win->nz;
+    G.tau0 = (float)tau;
+    G.force_scheme = 0;
+    Carver cv{(char *)ws, 0};
+    carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate);
+    c->scratch_d = (double *)c->f[1];
+    c->has_particle = false;
+    c->step = 0;
+    c->graph_ready[0] = c->graph_ready[1] = false;
+    if (cudaMallocHost((void **)&c->pinned, sizeof(DevState)) != cudaSuccess) {
+        c->pinned = nullptr;  // queries then stage through pageable memory
+        cudaGetLastError();
+    }
+    // fluid at rest: all deviations zero, ghost velocity zero, window state reset
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMemsetAsync(c->f[k], 0, 27 * (size_t)G.ncell * storage_bytes(c->storage), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->utop[k], 0, 3 * (size_t)G.plane * sizeof(float), c->stream);
+        if (e != cudaSuccess) {
+            cuda_fail(nullptr, e, "lbm_init memset");
+            if (c->pinned) cudaFreeHost(c->pinned);
+            delete c;
+            return TURRET_ECUDA;
+        }
+    }
+    memset(&c->host_state, 0, sizeof(DevState));
+    for (int i = 0; i < 9; ++i) c->host_state.d[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    c->host_state.reseed_plane = -1;
+    cudaError_t e = cudaMemcpyAsync(c->dstate, &c->host_state, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "lbm_init state upload");
+        if (c->pinned) cudaFreeHost(c->pinned);
+        delete c;
+        return TURRET_ECUDA;
+    }
+    *out = c;
+    return TURRET_OK;
+}
+
+static void drop_graphs(turret_ctx *c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph_ready[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph_ready[k] = false;
+    }
+}
+
+extern "C" turret_status lbm_set_flags(turret_ctx *c, const turret_flags *fl) {
+    if (!c || !fl) return fail(c, TURRET_EINVAL, "NULL argument");
+    if (fl->force_scheme < 0 || fl->force_scheme > 1 || fl->rot_form < 0 || fl->rot_form > 1 || fl->gravity < 0 ||
+        fl->gravity > 1 || fl->ibm_cycles < 1 || fl->ibm_cycles > 64)
+        return fail(c, TURRET_EINVAL, "invalid flags");
+    if (c->has_particle) return fail(c, TURRET_ESTATE, "flags must be set before ibm_load_surface");
+    c->flags = *fl;
+    c->geom.force_scheme = fl->force_scheme;
+    drop_graphs(c);
+    return TURRET_OK;
+}
+
+extern "C" turret_status lbm_set_fields(turret_ctx *c, const double *rho, const double *u) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (c->has_particle) return fail(c, TURRET_ESTATE, "fields must be set before ibm_load_surface");
+    const size_t n = (size_t)c->geom.ncell;
+    const int p = (int)(c->step & 1);
+    double *dr = (double *)c->f[1 - p];  // the idle buffer holds >= 32 bytes per cell
+    double *du = dr + n;
+    std::vector<double> h(n);
+    if (rho) {
+        for (size_t k = 0; k < n; ++k) h[k] = rho[k] - 1.0;
+        CK(cudaMemcpyAsync(dr, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "set_fields rho");
+    }
+    if (u) CK(cudaMemcpyAsync(du, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "set_fields u");
+    CK(launch_init_equilibrium(c->geom, c->storage, c->f[p], rho ? dr : nullptr, u ? du : nullptr,
+                               c->utop[1 - p], c->stream),
+       "init_equilibrium");
+    CK(cudaStreamSynchronize(c->stream), "set_fields sync");
+    return TURRET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host FP64 surface properties: dS_k (one third of the adjacent triangle
+// areas, Sec. 2.2), outward vertex normals (area-weighted), volume, centre of
+// mass and J/m about it from the divergence theorem (every triangle closes a
+// tetrahedron with the origin).
+struct MeshProps {
+    std::vector<double> dS, nrm;
+    double vol, area, com[3], Jm[9];
+};
+
+static bool mesh_props(const double *V, int64_t nv, const int32_t *T, int64_t nt, MeshProps &mp) {
+    std::map<std::pair<int64_t, int64_t>, int> edges;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int e = 0; e < 3; ++e) {
+            const int64_t a = T[3 * t + e], b = T[3 * t + (e + 1) % 3];
+            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) return false;
+            if (++edges[{a, b}] > 1) return false;
+        }
+    for (auto &kv : edges)
+        if (!edges.count({kv.first.second, kv.first.first})) return false;
+    std::vector<int> used(nv, 0);
+    for (int64_t t = 0; t < 3 * nt; ++t) used[T[t]] = 1;
+    for (int64_t k = 0; k < nv; ++k)
+        if (!used[k]) return false;
+    mp.dS.assign(nv, 0.0);
+    mp.nrm.assign(3 * nv, 0.0);
+    double vol = 0.0, area = 0.0, s1[3] = {0, 0, 0}, s2[9] = {0};
+    for (int64_t t = 0; t < nt; ++t) {
+        const double *p0 = V + 3 * T[3 * t], *p1 = V + 3 * T[3 * t + 1], *p2 = V + 3 * T[3 * t + 2];
+        const double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+        const double w[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+        const double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double ar = 0.5 * sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        area += ar;
+        for (int e = 0; e < 3; ++e) {
+            const int64_t k = T[3 * t + e];
+            mp.dS[k] += ar / 3.0;
+            for (int a = 0; a < 3; ++a) mp.nrm[3 * k + a] += 0.5 * cr[a];
+        }
+        // signed volume of the tetrahedron (0, p0, p1, p2) = p0 . (p1 x p2) / 6
+        const double c12[3] = {p1[1] * p2[2] - p1[2] * p2[1], p1[2] * p2[0] - p1[0] * p2[2],
+                               p1[0] * p2[1] - p1[1] * p2[0]};
+        const double tv = (p0[0] * c12[0] + p0[1] * c12[1] + p0[2] * c12[2]) / 6.0;
+        vol += tv;
+        double sum[3];
+        for (int a = 0; a < 3; ++a) {
+            sum[a] = p0[a] + p1[a] + p2[a];
+            s1[a] += tv * sum[a] * 0.25;
+        }
+        // second moments of a tetrahedron with one vertex at the origin
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                s2[3 * a + b] += tv * 0.05 * (p0[a] * p0[b] + p1[a] * p1[b] + p2[a] * p2[b] + sum[a] * sum[b]);
+    }
+    if (!(vol > 0.0)) return false;
+    for (int64_t k = 0; k < nv; ++k) {
+        double *n = &mp.nrm[3 * k];
+        const double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(l > 0.0)) return false;
+        for (int a = 0; a < 3; ++a) n[a] /= l;
+    }
+    for (int a = 0; a < 3; ++a) mp.com[a] = s1[a] / vol;
+    double C[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) C[3 * a + b] = s2[3 * a + b] - vol * mp.com[a] * mp.com[b];
+    const double tr = C[0] + C[4] + C[8];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) mp.Jm[3 * a + b] = ((a == b) ? tr : 0.0) / vol - C[3 * a + b] / vol;
+    mp.vol = vol;
+    mp.area = area;
+    return true;
+}
+
+static bool inverse3(const double *A, double *B) {
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (!(fabs(det) > 0.0)) return false;
+    const double id = 1.0 / det;
+    B[0] = (A[4] * A[8] - A[5] * A[7]) * id;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    B[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    B[6] = (A[3] * A[7] - A[4] * A[6]) * id;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    return true;
+}
+
+struct IbmLayout {
+    BoxGeom box;
+    int nm, cap, rc;
+};
+
+static bool ibm_layout(const turret_ctx *c, const MeshProps &mp, const double *V, int64_t nv, IbmLayout &L) {
+    double rb = 0.0;
+    for (int64_t k = 0; k < nv; ++k) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) s += (V[3 * k + a] - mp.com[a]) * (V[3 * k + a] - mp.com[a]);
+        rb = fmax(rb, sqrt(s));
+    }
+    L.rc = (int)ceil(rb + 1e-6);
+    const int B = 2 * L.rc + 6;
+    L.box.Bx = L.box.By = L.box.Bz = B;
+    L.box.tx = L.box.ty = L.box.tz = (B + 7) / 8;
+    L.box.nbox = (long long)B * B * B;
+    L.nm = (int)nv;
+    L.cap = (int)nv;
+    (void)c;
+    return nv > 0 && nv < (1 << 24);
+}
+
+static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
+    const size_t nm = (size_t)L.nm, nb = (size_t)L.box.nbox;
+    const size_t ntiles = (size_t)L.box.tx * L.box.ty * L.box.tz;
+    MarkerArrays m;
+    m.Xb = (const float *)cv.take(3 * nm * 4);
+    m.nb = (const float *)cv.take(3 * nm * 4);
+    m.dS = (const float *)cv.take(nm * 4);
+    m.bb = (int *)cv.take(3 * nm * 4);
+    m.wgt = (float *)cv.take(12 * nm * 4);
+    m.U = (float *)cv.take(3 * nm * 4);
+    m.n = (float *)cv.take(3 * nm * 4);
+    m.arm = (float *)cv.take(3 * nm * 4);
+    m.hl = (float *)cv.take(3 * nm * 4);
+    m.ft = (float *)cv.take(6 * nm * 4);
+    BoxArrays ba;
+    ba.u = (float *)cv.take(3 * nb * 4);
+    ba.s = (float *)cv.take(6 * nb * 4);
+    ba.h = (float *)cv.take(3 * nb * 4);
+    int *tl = (int *)cv.take(ntiles * (size_t)L.cap * 4);
+    int *tc = (int *)cv.take(ntiles * 4);
+    double *part = (double *)cv.take(REDUCE_BLOCKS * 6 * sizeof(double));
+    if (c) {
+        c->mk = m;
+        c->ba = ba;
+        c->tile_list = tl;
+        c->tile_count = tc;
+        c->partials = part;
+    }
+    return cv.off + 256;
+}
+
+extern "C" size_t ibm_workspace_bytes(const turret_ctx *c, const double *V, int64_t nv, const int32_t *T,
+                                      int64_t nt) {
+    if (!c || !V || !T || nv <= 0 || nt <= 0) return 0;
+    MeshProps mp;
+    if (!mesh_props(V, nv, T, nt, mp)) return 0;
+    IbmLayout L;
+    if (!ibm_layout(c, mp, V, nv, L)) return 0;
+    Carver cv{nullptr, 0};
+    return carve_ibm(cv, L, nullptr);
+}
+
+// Events (3) and (4) of Table 1 at time t: markers at the current particle
+// state, u* and sigma on the support box from f(t) = pull(f*(t-1)), surface
+// force and torque, n IBM cycles -> h_imm(t).
+static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float *utop_in) {
+    cudaError_t e;
+    const int nm = c->nm;
+    if ((e = launch_markers(c->geom, c->body, c->box, c->dstate, c->mk, c->stream)) != cudaSuccess) return e;
+    if ((e = launch_box_moments(c->geom, c->storage, fsrc, utop_in, c->dstate, c->box, c->ba, c->stream)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_bin(c->box, nm, c->mk.bb, c->tile_list, c->tile_count, c->cap, c->stream)) != cudaSuccess)
+        return e;
+    if ((e = launch_interp(c->box, nm, c->mk, c->ba, 0, c->stream)) != cudaSuccess) return e;
+    if ((e = launch_reduce_ft(nm, c->mk, c->partials, c->dstate, c->stream)) != cudaSuccess) return e;
+    for (int cyc = 1; cyc < c->flags.ibm_cycles; ++cyc) {
+        if ((e = launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->stream)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_interp(c->box, nm, c->mk, c->ba, 1, c->stream)) != cudaSuccess) return e;
+    }
+    return launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->stream);
+}
+
+// One step from parity p: f[p] holds f*(t-1), f[1-p] receives f*(t).
+static cudaError_t enqueue_step(turret_ctx *c, int p) {
+    cudaError_t e = launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p],
+                                          c->dstate, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle,
+                                          c->stream);
+    if (e != cudaSuccess || !c->has_particle) return e;
+    if ((e = launch_particle(c->geom, c->body, c->dstate, c->stream)) != cudaSuccess) return e;
+    if ((e = launch_reseed(c->geom, c->storage, c->f[1 - p], c->dstate, c->stream)) != cudaSuccess) return e;
+    return enqueue_coupling(c, c->f[1 - p], c->utop[p]);
+}
+
+extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_t nv, const int32_t *T, int64_t nt,
+                                          const double r0[3], const double v0[3], const double w0[3], void *ws,
+                                          size_t ws_bytes) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (c->has_particle) return fail(c, TURRET_ESTATE, "a surface is already loaded");
+    if (!V || !T || nv <= 0 || nt <= 0 || !r0 || !v0 || !w0) return fail(c, TURRET_EINVAL, "invalid surface arguments");
+    MeshProps mp;
+    if (!mesh_props(V, nv, T, nt, mp))
+        return fail(c, TURRET_EINVAL, "surface is not a closed, outward-oriented triangle mesh");
+    IbmLayout L;
+    if (!ibm_layout(c, mp, V, nv, L)) return fail(c, TURRET_EINVAL, "too many markers");
+    const int n[3] = {c->win.nx, c->win.ny, c->win.nz};
+    const bool per[3] = {c->win.bc_x == 0, c->win.bc_y == 0, c->win.bc_bottom == 0};
+    for (int a = 0; a < 3; ++a)
+        if (per[a] && L.box.Bx > n[a])
+            return fail(c, TURRET_EINVAL, "support box wider than the window along a periodic axis");
+    // every marker stencil must start inside the window along closed axes
+    for (int64_t k = 0; k < nv; ++k)
+        for (int a = 0; a < 3; ++a) {
+            if (per[a]) continue;
+            const double X = r0[a] + (V[3 * k + a] - mp.com[a]);
+            const int b = (int)floor(X);
+            if (b - 1 < 0 || b + 2 > n[a] - 1)
+                return fail(c, TURRET_EINVAL, "a marker is closer than 2 cells to a closed face");
+        }
+    double Jinv[9];
+    if (!inverse3(mp.Jm, Jinv)) return fail(c, TURRET_EINVAL, "singular inertia tensor");
+    Carver cv{(char *)ws, 0};
+    const size_t need = carve_ibm(cv, L, nullptr);
+    if (!ws || ws_bytes < need) return fail(c, TURRET_ENOMEM, "ibm workspace too small");
+    if (((uintptr_t)ws & 255) != 0) return fail(c, TURRET_EINVAL, "workspace must be 256-byte aligned");
+    Carver cv2{(char *)ws, 0};
+    carve_ibm(cv2, L, c);
+    c->nm = L.nm;
+    c->cap = L.cap;
+    c->box = L.box;
+    c->vol = mp.vol;
+    c->area = mp.area;
+    BodyConst &B = c->body;
+    B.vol = mp.vol;
+    B.kappa = c->kappa;
+    B.mass = c->kappa * mp.vol;
+    for (int i = 0; i < 9; ++i) B.Jinv_b[i] = Jinv[i];
+    for (int a = 0; a < 3; ++a) B.g_eff[a] = (c->flags.gravity == 1 ? 1.0 : 1.0 - 1.0 / c->kappa) * c->g[a];
+    B.anchor_z = c->win.anchor_frac * c->win.nz;
+    B.rot_form = c->flags.rot_form;
+    B.renorm = c->flags.renorm_orientation;
+    B.slide = c->win.slide;
+    B.nm = L.nm;
+    B.rc = L.rc;
+    // static marker data (body frame): offsets from C_m, normals, areas
+    const size_t nm = (size_t)L.nm;
+    c->staging.assign(7 * nm, 0.0f);
+    for (size_t k = 0; k < nm; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            c->staging[a * nm + k] = (float)(V[3 * k + a] - mp.com[a]);
+            c->staging[(3 + a) * nm + k] = (float)mp.nrm[3 * k + a];
+        }
+        c->staging[6 * nm + k] = (float)mp.dS[k];
+    }
+    CK(cudaMemcpyAsync((void *)c->mk.Xb, c->staging.data(), 3 * nm * 4, cudaMemcpyHostToDevice, c->stream), "Xb");
+    CK(cudaMemcpyAsync((void *)c->mk.nb, c->staging.data() + 3 * nm, 3 * nm * 4, cudaMemcpyHostToDevice, c->stream),
+       "nb");
+    CK(cudaMemcpyAsync((void *)c->mk.dS, c->staging.data() + 6 * nm, nm * 4, cudaMemcpyHostToDevice, c->stream), "dS");
+    CK(cudaMemsetAsync(c->ba.h, 0, 3 * (size_t)L.box.nbox * 4, c->stream), "h");
+    // rigid-body state at t: r(t), d = I, v(t-1/2) = v0, w(t-1/2) = w0, L = J w0
+    CK(cudaMemcpyAsync(&c->host_state, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state");
+    CK(cudaStreamSynchronize(c->stream), "load sync");
+    DevState &S = c->host_state;
+    for (int a = 0; a < 3; ++a) {
+        S.r[a] = r0[a] + (double)S.origin[a];
+        S.v[a] = v0[a];
+        S.w[a] = w0[a];
+        S.F[a] = S.T[a] = 0.0;
+        S.L[a] = B.mass * (mp.Jm[3 * a] * w0[0] + mp.Jm[3 * a + 1] * w0[1] + mp.Jm[3 * a + 2] * w0[2]);
+        const double C = r0[a];
+        S.Ci[a] = (int)floor(C);
+        S.Cf[a] = C - floor(C);
+        S.box_lo[a] = S.Ci[a] - L.rc - 2;
+    }
+    for (int i = 0; i < 9; ++i) S.d[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    S.step = c->step;
+    S.reseed_plane = -1;
+    S.status = 0;
+    S.counter = 0;
+    CK(cudaMemcpyAsync(c->dstate, &S, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "state upload");
+    c->has_particle = true;
+    drop_graphs(c);
+    const int t = (int)(c->step & 1);
+    CK(enqueue_coupling(c, c->f[t], c->utop[1 - t]), "initial coupling");
+    CK(cudaStreamSynchronize(c->stream), "initial coupling sync");
+    return TURRET_OK;
+}
+
+extern "C" turret_status step(turret_ctx *c, int64_t n) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
+    const bool graphs = (c->stream != nullptr) && !c->flags.no_graph;
+    for (int64_t k = 0; k < n; ++k) {
+        const int p = (int)(c->step & 1);
+        if (graphs) {
+            if (!c->graph_ready[p]) {
+                cudaGraph_t gr;
+                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+                cudaError_t e = enqueue_step(c, p);
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+                if (e != cudaSuccess) return cuda_fail(c, e, "capture enqueue");
+                CK(e2, "end capture");
+                e = cudaGraphInstantiate(&c->graph[p], gr, 0);
+                cudaGraphDestroy(gr);
+                CK(e, "graph instantiate");
+                c->graph_ready[p] = true;
+            }
+            CK(cudaGraphLaunch(c->graph[p], c->stream), "graph launch");
+        } else {
+            CK(enqueue_step(c, p), "step launch");
+        }
+        c->step++;
+    }
+    return TURRET_OK;
+}
+
+extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
+    for (int64_t k = 0; k < n; ++k) {
+        const int p = (int)(c->step & 1);
+        CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
+                                 c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle, c->stream),
+           "fluid step");
+        c->step++;
+    }
+    return TURRET_OK;
+}
+
+extern "C" turret_status query_particle_state(turret_ctx *c, turret_particle_state *out) {
+    if (!c || !out) return fail(c, TURRET_EINVAL, "NULL argument");
+    DevState S;
+    DevState *dst = c->pinned ? c->pinned : &S;
+    CK(cudaMemcpyAsync(dst, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "query");
+    CK(cudaStreamSynchronize(c->stream), "query sync");
+    if (c->pinned) S = *c->pinned;
+    memset(out, 0, sizeof *out);
+    for (int a = 0; a < 3; ++a) {
+        out->r[a] = S.r[a];
+        out->v[a] = S.v[a];
+        out->w[a] = S.w[a];
+        out->F[a] = S.F[a];
+        out->T[a] = S.T[a];
+        out->L[a] = S.L[a];
+        out->origin[a] = S.origin[a];
+    }
+    for (int i = 0; i < 9; ++i) out->d[i] = S.d[i];
+    out->step = c->has_particle ? S.step : c->step;
+    out->status = S.status;
+    out->n_markers = c->has_particle ? c->nm : 0;
+    out->volume = c->has_particle ? c->vol : 0.0;
+    out->area = c->has_particle ? c->area : 0.0;
+    // enqueue_step: collide+stream, particle, reseed; enqueue_coupling: markers,
+    // box moments, bin, interp, reduce, (spread + interp) per extra cycle, spread
+    out->kernels_per_step = c->has_particle ? 3 + 6 + 2 * (c->flags.ibm_cycles - 1) : 1;
+    if (S.status == STAT_DOMAIN) return fail(c, TURRET_EDOMAIN, "a marker stencil left the window");
+    if (S.status == STAT_DIVERGED) return fail(c, TURRET_EDIVERGED, "non-finite force or torque");
+    return TURRET_OK;
+}
+
+static turret_status copy_fields(turret_ctx *c, float *dev_out, bool pops) {
+    if (!c || !dev_out) return fail(c, TURRET_EINVAL, "NULL argument");
+    const int p = (int)(c->step & 1);
+    CK(launch_macro(c->geom, c->storage, c->f[p], c->utop[1 - p], c->dstate, dev_out, pops, c->stream), "macro");
+    CK(cudaStreamSynchronize(c->stream), "macro sync");
+    return TURRET_OK;
+}
+
+extern "C" turret_status lbm_copy_macro(turret_ctx *c, float *dev_out) { return copy_fields(c, dev_out, false); }
+extern "C" turret_status lbm_copy_populations(turret_ctx *c, float *dev_out) { return copy_fields(c, dev_out, true); }
+
+extern "C" turret_status lbm_destroy(turret_ctx *c) {
+    if (!c) return TURRET_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+    return TURRET_OK;
+}
+
+extern "C" const char *turret_last_error(const turret_ctx *c) { return c ? c->err.c_str() : g_init_err.c_str(); }

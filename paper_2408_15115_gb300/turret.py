@@ -1,0 +1,197 @@
+"""ctypes binding of libturret.so (declared in include/turret.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides the device workspaces and the CUDA stream.
+The library is built in-tree (``paper_2408_15115_gb300/libturret.so``); if it
+is missing this module raises instead of falling back to anything else.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libturret.so")
+
+STATUS = {0: "TURRET_OK", 1: "TURRET_EINVAL", 2: "TURRET_ENOMEM", 3: "TURRET_ECUDA", 4: "TURRET_ESTATE",
+          5: "TURRET_EDIVERGED", 6: "TURRET_ETIMEOUT", 7: "TURRET_EDOMAIN"}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+PERIODIC, NOSLIP, PRESSURE = 0, 1, 2
+
+
+class Window(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("bc_bottom", C.c_int32), ("bc_top", C.c_int32),
+                ("sponge_cells", C.c_int32), ("slide", C.c_int32), ("pad0", C.c_int32),
+                ("anchor_frac", C.c_double)]
+
+
+class Flags(C.Structure):
+    _fields_ = [("force_scheme", C.c_int32), ("rot_form", C.c_int32), ("gravity", C.c_int32),
+                ("renorm_orientation", C.c_int32), ("ibm_cycles", C.c_int32), ("no_graph", C.c_int32)]
+
+
+class ParticleState(C.Structure):
+    _fields_ = [("r", C.c_double * 3), ("d", C.c_double * 9), ("v", C.c_double * 3), ("w", C.c_double * 3),
+                ("F", C.c_double * 3), ("T", C.c_double * 3), ("L", C.c_double * 3),
+                ("origin", C.c_int64 * 3), ("step", C.c_int64), ("status", C.c_int32), ("n_markers", C.c_int32),
+                ("volume", C.c_double), ("area", C.c_double), ("kernels_per_step", C.c_int32),
+                ("pad0", C.c_int32)]
+
+
+class TurretError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libturret.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libturret.so is not built; run paper_2408_15115_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.lbm_workspace_bytes.restype = C.c_size_t
+        L.lbm_workspace_bytes.argtypes = [C.POINTER(Window), C.c_int]
+        L.lbm_init.restype = C.c_int
+        L.lbm_init.argtypes = [C.POINTER(vp), C.POINTER(Window), C.c_int, C.c_double, C.c_double, _dp, C.c_int,
+                               vp, C.c_size_t, vp]
+        L.lbm_set_flags.restype = C.c_int
+        L.lbm_set_flags.argtypes = [vp, C.POINTER(Flags)]
+        L.lbm_set_fields.restype = C.c_int
+        L.lbm_set_fields.argtypes = [vp, _dp, _dp]
+        L.ibm_workspace_bytes.restype = C.c_size_t
+        L.ibm_workspace_bytes.argtypes = [vp, _dp, C.c_int64, C.POINTER(C.c_int32), C.c_int64]
+        L.ibm_load_surface.restype = C.c_int
+        L.ibm_load_surface.argtypes = [vp, _dp, C.c_int64, C.POINTER(C.c_int32), C.c_int64, _dp, _dp, _dp, vp,
+                                       C.c_size_t]
+        L.step.restype = C.c_int
+        L.step.argtypes = [vp, C.c_int64]
+        L.lbm_fluid_step.restype = C.c_int
+        L.lbm_fluid_step.argtypes = [vp, C.c_int64]
+        L.query_particle_state.restype = C.c_int
+        L.query_particle_state.argtypes = [vp, C.POINTER(ParticleState)]
+        L.lbm_copy_macro.restype = C.c_int
+        L.lbm_copy_macro.argtypes = [vp, vp]
+        L.lbm_copy_populations.restype = C.c_int
+        L.lbm_copy_populations.argtypes = [vp, vp]
+        L.lbm_destroy.restype = C.c_int
+        L.lbm_destroy.argtypes = [vp]
+        L.turret_last_error.restype = C.c_char_p
+        L.turret_last_error.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _arr(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _aligned_workspace(torch, nbytes, device):
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf.data_ptr() + off
+
+
+class Turret:
+    """One simulation window (+ optional particle) on one GPU.
+
+    bc codes: PERIODIC, NOSLIP (halfway bounce-back), PRESSURE (top only)."""
+
+    def __init__(self, nx, ny, nz, nu, kappa=1.0, g=(0.0, 0.0, 0.0), bc_x=PERIODIC, bc_y=PERIODIC,
+                 bc_bottom=PERIODIC, bc_top=PERIODIC, sponge=0, slide=0, anchor_frac=0.25, storage="f32",
+                 flags=None, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.shape = (nz, ny, nx)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._L = lib()
+        self.win = Window(nx, ny, nz, bc_x, bc_y, bc_bottom, bc_top, sponge, slide, 0, float(anchor_frac))
+        st = STORAGE[storage]
+        nb = self._L.lbm_workspace_bytes(C.byref(self.win), st)
+        if nb == 0:
+            raise TurretError(1, "invalid window")
+        self._ws, ptr = _aligned_workspace(torch, nb, self.device)
+        self._ibm_ws = None
+        g3 = (C.c_double * 3)(*g)
+        ctx = C.c_void_p()
+        rc = self._L.lbm_init(C.byref(ctx), C.byref(self.win), 27, float(nu), float(kappa), g3, st,
+                              C.c_void_p(ptr), C.c_size_t(nb), C.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise TurretError(rc, self._L.turret_last_error(None).decode())
+        self.ctx = ctx
+        if flags:
+            f = Flags(0, 0, 0, 0, 4, 0)
+            for k, v in flags.items():
+                setattr(f, k, int(v))
+            self._check(self._L.lbm_set_flags(self.ctx, C.byref(f)))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TurretError(rc, self._L.turret_last_error(self.ctx).decode())
+
+    def set_fields(self, rho=None, u=None):
+        rp = _arr(rho).ctypes.data_as(_dp) if rho is not None else None
+        ua = _arr(u) if u is not None else None
+        up = ua.ctypes.data_as(_dp) if ua is not None else None
+        self._check(self._L.lbm_set_fields(self.ctx, rp, up))
+
+    def load_surface(self, verts, tris, r0, v0=(0, 0, 0), w0=(0, 0, 0)):
+        V = _arr(verts)
+        T = _arr(tris, np.int32)
+        vp, tp = V.ctypes.data_as(_dp), T.ctypes.data_as(C.POINTER(C.c_int32))
+        nb = self._L.ibm_workspace_bytes(self.ctx, vp, V.shape[0], tp, T.shape[0])
+        if nb == 0:
+            raise TurretError(1, "invalid surface mesh")
+        self._ibm_ws, ptr = _aligned_workspace(self.torch, nb, self.device)
+        r0 = (C.c_double * 3)(*r0)
+        v0 = (C.c_double * 3)(*v0)
+        w0 = (C.c_double * 3)(*w0)
+        self._check(self._L.ibm_load_surface(self.ctx, vp, V.shape[0], tp, T.shape[0], r0, v0, w0,
+                                             C.c_void_p(ptr), C.c_size_t(nb)))
+
+    def step(self, n=1):
+        self._check(self._L.step(self.ctx, int(n)))
+
+    def fluid_step(self, n=1):
+        self._check(self._L.lbm_fluid_step(self.ctx, int(n)))
+
+    def state(self, check=True):
+        s = ParticleState()
+        rc = self._L.query_particle_state(self.ctx, C.byref(s))
+        if check:
+            self._check(rc)
+        return dict(r=np.array(s.r), d=np.array(s.d).reshape(3, 3), v=np.array(s.v), w=np.array(s.w),
+                    F=np.array(s.F), T=np.array(s.T), L=np.array(s.L), origin=np.array(s.origin),
+                    step=int(s.step), status=int(s.status), n_markers=int(s.n_markers), volume=s.volume,
+                    area=s.area, kernels_per_step=int(s.kernels_per_step), rc=rc)
+
+    def macro(self):
+        """(4, nz, ny, nx) float32 tensor: rho, u_x, u_y, u_z of f(t)."""
+        out = self.torch.empty((4,) + self.shape, dtype=self.torch.float32, device=self.device)
+        self._check(self._L.lbm_copy_macro(self.ctx, C.c_void_p(out.data_ptr())))
+        return out
+
+    def populations(self):
+        """(27, nz, ny, nx) float32 tensor: deviations f_i(t) - w_i."""
+        out = self.torch.empty((27,) + self.shape, dtype=self.torch.float32, device=self.device)
+        self._check(self._L.lbm_copy_populations(self.ctx, C.c_void_p(out.data_ptr())))
+        return out
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            self._L.lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+"""GPU parity of the coupled step (collide+stream, 6DOF, stress, force and
+torque, IBM cycles, window slide) with the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2408_15115_gb300 import inputs as I
+
+from cases import TOL_U_F32, gpu_velocity, make_pair, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_state(t, s, tol_f=1e-4, tol_v=1e-5):
+    a, b = t.state(), s.state()
+    scale_f = max(np.abs(b["F"]).max(), 1e-300)
+    assert np.abs(a["F"] - b["F"]).max() / scale_f < tol_f, (a["F"], b["F"])
+    scale_v = max(np.abs(b["v"]).max(), 1e-300)
+    assert np.abs(a["v"] - b["v"]).max() / scale_v < tol_v, (a["v"], b["v"])
+    assert np.abs(a["r"] - b["r"]).max() < 1e-6
+    assert np.array_equal(a["origin"], b["origin"].astype(np.int64))
+    return a, b
+
+
+def test_sphere_in_closed_box_100_steps():
+    # 32x32x64 closed box, sphere d = 8 (252 markers), kappa 2.5, g along -z,
+    # seeded smooth random initial flow of amplitude 0.01
+    shape = (64, 32, 32)
+    V, T = I.sphere(5, 8.0)
+    fields = I.random_state(shape, u_amp=0.01, rho_amp=0.001, kmax=4, seed=1)
+    t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), fields=fields,
+                     particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
+    _compare_state(t, s)
+    t.step(100)
+    s.step(100)
+    u, _ = gpu_velocity(t)
+    err = rel_max(u, s.velocity())
+    assert err < TOL_U_F32, err
+    _compare_state(t, s)
+
+
+def test_tilted_ellipsoid_rotation_and_torque():
+    shape = (48, 40, 40)
+    V, T = I.ellipsoid(6, (6.0, 3.0, 3.0))
+    V = I.rotate(I.rotate(V, "x", 30.0), "z", 20.0)
+    fields = I.random_state(shape, u_amp=0.02, rho_amp=0.001, kmax=3, seed=2)
+    t, s = make_pair(40, 40, 48, 0.04, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=6, fields=fields,
+                     particle=(V, T, (19.7, 20.2, 22.3), (0, 0, -0.01), (0.002, -0.001, 0.003)))
+    t.step(100)
+    s.step(100)
+    a, b = _compare_state(t, s, tol_f=1e-4, tol_v=1e-5)
+    assert np.abs(a["w"] - b["w"]).max() / np.abs(b["w"]).max() < 1e-4
+    assert np.abs(a["T"] - b["T"]).max() / np.abs(b["T"]).max() < 1e-3
+    assert np.abs(a["d"] - b["d"]).max() < 1e-6
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < TOL_U_F32
+
+
+def test_sliding_window_follows_particle():
+    # falling sphere in a periodic column with the ring window; several slides
+    shape = (48, 24, 24)
+    V, T = I.sphere(4, 6.0)
+    t, s = make_pair(24, 24, 48, 0.05, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -2e-4), sponge=6, slide=1, anchor=0.5,
+                     particle=(V, T, (11.6, 12.3, 24.4), (0, 0, -0.08), (0, 0, 0)))
+    t.step(80)
+    s.step(80)
+    a, b = _compare_state(t, s, tol_f=1e-4, tol_v=1e-5)
+    assert b["origin"][2] <= -2  # the window moved (the first slide wraps the ring index)
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < TOL_U_F32
+
+
+def test_determinism_and_graph_equivalence():
+    V, T = I.sphere(4, 6.0)
+    runs = []
+    for flags in ({}, {}, {"no_graph": 1}):
+        t, _ = make_pair(24, 24, 32, 0.05, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=4, flags=flags,
+                         particle=(V, T, (11.6, 12.3, 16.4), (0, 0, 0), (0, 0.001, 0)))
+        t.step(30)
+        runs.append((t.populations().cpu().numpy(), t.state()))
+    for other in runs[1:]:
+        assert np.array_equal(runs[0][0], other[0])
+        assert np.array_equal(runs[0][1]["F"], other[1]["F"])
+
+
+def test_domain_error_is_latched_not_faulted():
+    # a particle driven into the closed bottom face: the device latches EDOMAIN
+    V, T = I.sphere(3, 4.0)
+    t, _ = make_pair(16, 16, 16, 0.05, (1, 1, 1, 1), kappa=2.0, g=(0, 0, 0),
+                     particle=(V, T, (8.0, 8.0, 5.2), (0, 0, -0.3), (0, 0, 0)))
+    t.step(12)
+    st = t.state(check=False)
+    assert st["rc"] == 7 and st["status"] == 7
+
+
+@pytest.mark.slow
+def test_stokes_settling_cfg1_drag_and_velocity_vs_oracle():
+    # the 32x32x64 sphere case for 500 steps: drag and settling velocity <= 0.5%
+    V, T = I.sphere(5, 8.0)
+    O.set_threads(0)
+    t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5),
+                     particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
+    t.step(500)
+    s.step(500)
+    a, b = t.state(), s.state()
+    assert abs(a["F"][2] - b["F"][2]) / abs(b["F"][2]) < 5e-3
+    assert abs(a["v"][2] - b["v"][2]) / abs(b["v"][2]) < 5e-3
