@@ -48,7 +48,8 @@ typedef enum {
     TURRET_ESTATE = 4,    /* call out of order (e.g. step before ibm_load_surface)     */
     TURRET_EDIVERGED = 5, /* non-finite force or torque                                */
     TURRET_ETIMEOUT = 6,  /* a bounded device wait gave up                             */
-    TURRET_EDOMAIN = 7    /* a marker stencil left the window along a closed axis      */
+    TURRET_EDOMAIN = 7,   /* a marker stencil left the window along a closed axis      */
+    TURRET_EOVERFLOW = 8  /* more markers touch one 4^3 support tile than its list holds */
 } turret_status;
 
 typedef enum { TURRET_D3Q27 = 27 } turret_lattice;

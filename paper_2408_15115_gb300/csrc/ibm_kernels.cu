@@ -1,384 +1,489 @@
 // ibm_kernels.cu -- rigid-body update, marker kinematics and the
 // immersed-boundary transfers of the Palabos Turret step (arXiv 2408.15115).
 //
-//   k_particle : FP64 leap-frog 6DOF with the orientation predictor-corrector
-//                (Sec. 2.3), then the vertical window slide; one thread.
-//   k_markers  : X_k = C_m + M^T Xb_k, n_k = M^T nb_k, U_k = v + w x (X_k - C_m)
-//                (Sec. 2.3 end), the 4x4x4 Peskin stencil base of each marker in
-//                support-box coordinates and its 12 one-dimensional weights
-//                (Sec. 2.2), one thread per marker.
-//   k_bin      : for every 8^3 tile of the support box, the markers whose
-//                stencil overlaps it, in marker order (ordered compaction).
-//   k_interp   : I[u](X_k) = sum_x u(x) W(x - X_k), one warp per marker, two
-//                stencil cells per lane, xor-shuffle reduction (deterministic);
-//                mode 0 also interpolates sigma and forms dS sigma.n and the
-//                torque arm product for the surface force (Sec. 2.2 end).
-//   k_spread   : S[h](x) = sum_k h_k W(x - X_k) dS_k as a gather: one block
-//                per tile, each cell sums its tile's candidate list in marker
-//                order -- no atomics, bitwise reproducible.
-//   k_reduce_ft: F = sum_k f_k, T = sum_k t_k in FP64, fixed-order block
-//                partials and a last-block final sum.
+//   k_particle_markers : FP64 leap-frog 6DOF with the orientation
+//                predictor-corrector (Sec. 2.3) and the vertical window slide,
+//                spread over the lanes of warp 0 of every block (GB300 has
+//                little FP64 throughput, so the path is short, lane-parallel
+//                and free of division); then, in the same launch, the marker kinematics
+//                X_k = C_m + M^T Xb_k, n_k = M^T nb_k, U_k = v + w x (X_k - C_m)
+//                and each marker's 4x4x4 Peskin stencil (Sec. 2.2) in
+//                support-box coordinates.
+//   k_interp0_rows : I[u](X_k) = sum_x u(x) W(x - X_k) for u* and sigma, one
+//                warp per marker, two stencil cells per lane, xor-shuffle sums
+//                (deterministic); forms dS sigma.n and its moment about C_m
+//                for the surface force (Sec. 2.2 end) and row k of the
+//                interaction matrix A of the IBM cycles; one block per marker.
+//   k_cycle    : one IBM cycle as h <- h + r0 - A h (a sparse product, one
+//                warp per marker), equal to spreading h and interpolating
+//                u* + S h without touching the grid.
+//   k_reduce_ft: F and T summed in FP64 in a fixed order (one block); it runs
+//                on its own graph branch, off the critical path of the cycles.
+//   k_spread   : h_imm = S[h](x) = sum_k h_k W(x - X_k) dS_k as a gather: one block
+//                per 4^3 tile of the support box stages the tile's candidate
+//                records (built with the support-box moments, in marker order)
+//                in shared memory; 8 slices of the candidates per cell, added
+//                in slice order -- no atomics, bitwise reproducible.
 #include <math.h>
 
 #include "turret_internal.cuh"
 
 namespace turret {
 
-__device__ __forceinline__ void cross3(const double *a, const double *b, double *c) {
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
+// Peskin 4-point kernel (Sec. 2.2) on its two branches, argument |r|.
+__device__ __forceinline__ float peskin_in(float a) {
+    return 0.125f * (3.0f - 2.0f * a + sqrtf(1.0f + 4.0f * a - 4.0f * a * a));
 }
-
-__global__ void k_particle(Geom g, BodyConst bc, DevState *__restrict__ stp) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    DevState s = *stp;
-    for (int a = 0; a < 3; ++a) {
-        s.v[a] += bc.g_eff[a] + s.F[a] / bc.mass;  // a(t) = g_eff + F(t)/(kappa V)
-        s.r[a] += s.v[a];
-    }
-    double src[3];
-    for (int a = 0; a < 3; ++a) {
-        if (bc.rot_form == 1) {
-            src[a] = s.T[a];
-        } else {
-            s.L[a] += s.T[a];
-            src[a] = s.L[a];
-        }
-    }
-    double sb[3], wb[3], wl[3];
-    for (int i = 0; i < 3; ++i) sb[i] = s.d[3 * i] * src[0] + s.d[3 * i + 1] * src[1] + s.d[3 * i + 2] * src[2];
-    for (int i = 0; i < 3; ++i)
-        wb[i] = (bc.Jinv_b[3 * i] * sb[0] + bc.Jinv_b[3 * i + 1] * sb[1] + bc.Jinv_b[3 * i + 2] * sb[2]) / bc.mass;
-    for (int a = 0; a < 3; ++a) wl[a] = s.d[a] * wb[0] + s.d[3 + a] * wb[1] + s.d[6 + a] * wb[2];
-    for (int a = 0; a < 3; ++a) s.w[a] = (bc.rot_form == 1) ? s.w[a] + wl[a] : wl[a];
-    double dn[9];
-    for (int i = 0; i < 3; ++i) {
-        double c1[3], pred[3], mid[3], c2[3];
-        cross3(s.w, s.d + 3 * i, c1);
-        for (int a = 0; a < 3; ++a) pred[a] = s.d[3 * i + a] + c1[a];
-        for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (s.d[3 * i + a] + pred[a]);
-        cross3(s.w, mid, c2);
-        for (int a = 0; a < 3; ++a) dn[3 * i + a] = s.d[3 * i + a] + c2[a];
-    }
-    for (int k = 0; k < 9; ++k) s.d[k] = dn[k];
-    if (bc.renorm) {
-        for (int i = 0; i < 3; ++i) {
-            for (int j = 0; j < i; ++j) {
-                double pj = 0.0;
-                for (int a = 0; a < 3; ++a) pj += s.d[3 * i + a] * s.d[3 * j + a];
-                for (int a = 0; a < 3; ++a) s.d[3 * i + a] -= pj * s.d[3 * j + a];
-            }
-            const double l = sqrt(s.d[3 * i] * s.d[3 * i] + s.d[3 * i + 1] * s.d[3 * i + 1] + s.d[3 * i + 2] * s.d[3 * i + 2]);
-            for (int a = 0; a < 3; ++a) s.d[3 * i + a] /= l;
-        }
-    }
-    // vertical slide of the ring window: one plane per step at most
-    s.reseed_plane = -1;
-    if (bc.slide) {
-        const double dz = (s.r[2] - (double)s.origin[2]) - bc.anchor_z;
-        if (dz <= -1.0) {
-            s.origin[2] -= 1;
-            s.ring = (s.ring == 0) ? g.nz - 1 : s.ring - 1;
-            s.reseed_plane = s.ring;  // new logical bottom plane
-        } else if (dz >= 1.0) {
-            s.origin[2] += 1;
-            s.ring = (s.ring + 1 == g.nz) ? 0 : s.ring + 1;
-            s.reseed_plane = (s.ring + g.nz - 1) % g.nz;  // new logical top plane
-        }
-    }
-    for (int a = 0; a < 3; ++a) {
-        const double C = s.r[a] - (double)s.origin[a];
-        const double fl = floor(C);
-        s.Ci[a] = (int)fl;
-        s.Cf[a] = C - fl;
-        s.box_lo[a] = s.Ci[a] - bc.rc - 2;
-    }
-    s.step += 1;
-    *stp = s;
-}
-
-// Peskin 4-point kernel (Sec. 2.2) on the two branches, |r| given.
-__device__ __forceinline__ float peskin_in(float a) { return 0.125f * (3.0f - 2.0f * a + sqrtf(1.0f + 4.0f * a - 4.0f * a * a)); }
 __device__ __forceinline__ float peskin_out(float a) {
     return 0.125f * (5.0f - 2.0f * a - sqrtf(fmaxf(0.0f, -7.0f + 12.0f * a - 4.0f * a * a)));
 }
 
-__global__ void k_markers(Geom g, BodyConst bc, BoxGeom box, DevState *st, MarkerArrays m) {
-    const DevState *st_c = st;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= bc.nm) return;
-    const int nm = bc.nm;
-    float d[9], v[3], w[3], cf[3];
-    int ci[3], lo[3];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) d[a] = (float)st_c->d[a];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        v[a] = (float)st_c->v[a];
-        w[a] = (float)st_c->w[a];
-        cf[a] = (float)st_c->Cf[a];
-        ci[a] = st_c->Ci[a];
-        lo[a] = st_c->box_lo[a];
+constexpr int PM_THREADS = 128;
+
+// Every block recomputes the (tiny) rigid-body update from slot `slot` in
+// warp 0 -- identical inputs, identical FP64 results -- and block 0 stores it
+// in the other slot, so the marker work spreads over many SMs with no
+// grid-wide wait.
+__global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyConst bc, BoxGeom box, DevState *st,
+                                                                  int slot, int advance, MarkerArrays m) {
+    __shared__ BodySlot S;  // the body at the markers' time level
+    __shared__ double s_F[3], s_T[3], s_src[3], s_sb[3], s_wb[3], s_mid[9], s_dn[9];
+    __shared__ float f_d[9], f_v[3], f_w[3], f_cf[3];
+    __shared__ int i_ci[3], i_lo[3];
+    const int tid = threadIdx.x;
+    const int so = advance ? (slot ^ 1) : slot;  // slot of the markers' time level
+    if (tid < 32) {
+        const int lane = tid;
+        {
+            const int *gsrc = reinterpret_cast<const int *>(&st->s[slot]);
+            int *sdst = reinterpret_cast<int *>(&S);
+            for (int q = lane; q < (int)(sizeof(BodySlot) / 4); q += 32) sdst[q] = gsrc[q];
+            if (lane < 3) {
+                s_F[lane] = st->F[lane];
+                s_T[lane] = st->T[lane];
+            }
+        }
+        __syncwarp();
+        if (advance) {
+            // ---- 6DOF, Sec. 2.3 (dt = 1, rho_f = 1, m = kappa V) ------------------
+            if (lane < 3) {
+                S.v[lane] += bc.g_eff[lane] + s_F[lane] * bc.inv_mass;  // v(t+1/2)
+                S.r[lane] += S.v[lane];                                 // r(t+1)
+                if (bc.rot_form == 1) {
+                    s_src[lane] = s_T[lane];
+                } else {
+                    S.L[lane] += s_T[lane];  // L(t+1/2) = L(t-1/2) + T(t)
+                    s_src[lane] = S.L[lane];
+                }
+            }
+            __syncwarp();
+            if (lane < 3)  // body-frame components M src (M has rows d_i)
+                s_sb[lane] = S.d[3 * lane] * s_src[0] + S.d[3 * lane + 1] * s_src[1] + S.d[3 * lane + 2] * s_src[2];
+            __syncwarp();
+            if (lane < 3)  // (J/m)^-1 / m, a host constant
+                s_wb[lane] = bc.Jinv_b[3 * lane] * s_sb[0] + bc.Jinv_b[3 * lane + 1] * s_sb[1] +
+                             bc.Jinv_b[3 * lane + 2] * s_sb[2];
+            __syncwarp();
+            if (lane < 3) {  // back to the lab frame: M^T wb
+                const double wl = S.d[lane] * s_wb[0] + S.d[3 + lane] * s_wb[1] + S.d[6 + lane] * s_wb[2];
+                S.w[lane] = (bc.rot_form == 1) ? S.w[lane] + wl : wl;
+            }
+            __syncwarp();
+            // d_i^pred = d_i + w x d_i;  d_i(t+1) = d_i + w x (d_i + d_i^pred) / 2
+            const int i = lane / 3, a = lane % 3, a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+            if (lane < 9) s_mid[lane] = S.d[lane] + 0.5 * (S.w[a1] * S.d[3 * i + a2] - S.w[a2] * S.d[3 * i + a1]);
+            __syncwarp();
+            if (lane < 9) s_dn[lane] = S.d[lane] + (S.w[a1] * s_mid[3 * i + a2] - S.w[a2] * s_mid[3 * i + a1]);
+            __syncwarp();
+            if (lane == 0) {
+                for (int k = 0; k < 9; ++k) S.d[k] = s_dn[k];
+                if (bc.renorm) {  // modified Gram-Schmidt of d_0, d_1, d_2
+                    for (int q = 0; q < 3; ++q) {
+                        for (int j = 0; j < q; ++j) {
+                            double pj = 0.0;
+                            for (int c = 0; c < 3; ++c) pj += S.d[3 * q + c] * S.d[3 * j + c];
+                            for (int c = 0; c < 3; ++c) S.d[3 * q + c] -= pj * S.d[3 * j + c];
+                        }
+                        const double il = rsqrt(S.d[3 * q] * S.d[3 * q] + S.d[3 * q + 1] * S.d[3 * q + 1] +
+                                                S.d[3 * q + 2] * S.d[3 * q + 2]);
+                        for (int c = 0; c < 3; ++c) S.d[3 * q + c] *= il;
+                    }
+                }
+                // vertical slide of the ring window: one plane per step at most
+                int ring = S.ring;
+                int reseed = -1;
+                if (bc.slide) {
+                    const double dz = (S.r[2] - (double)S.origin[2]) - bc.anchor_z;
+                    if (dz <= -1.0) {
+                        S.origin[2] -= 1;
+                        ring = (ring == 0) ? g.nz - 1 : ring - 1;
+                        reseed = ring;  // new logical bottom plane
+                    } else if (dz >= 1.0) {
+                        S.origin[2] += 1;
+                        ring = (ring + 1 == g.nz) ? 0 : ring + 1;
+                        reseed = (ring == 0) ? g.nz - 1 : ring - 1;  // new logical top plane
+                    }
+                }
+                for (int c = 0; c < 3; ++c) {
+                    const double C = S.r[c] - (double)S.origin[c];
+                    const double fl = floor(C);
+                    S.Ci[c] = (int)fl;
+                    S.Cf[c] = C - fl;
+                    S.box_lo[c] = (int)fl - bc.rc - 2;
+                }
+                S.ring = ring;
+                S.reseed = reseed;
+                S.step += 1;
+            }
+            __syncwarp();
+            if (blockIdx.x == 0) {
+                int *gdst = reinterpret_cast<int *>(&st->s[so]);
+                const int *ssrc = reinterpret_cast<const int *>(&S);
+                for (int q = lane; q < (int)(sizeof(BodySlot) / 4); q += 32) gdst[q] = ssrc[q];
+            }
+        }
+        if (lane < 9) f_d[lane] = (float)S.d[lane];
+        if (lane < 3) {
+            f_v[lane] = (float)S.v[lane];
+            f_w[lane] = (float)S.w[lane];
+            f_cf[lane] = (float)S.Cf[lane];
+            i_ci[lane] = S.Ci[lane];
+            i_lo[lane] = S.box_lo[lane];
+        }
     }
+    __syncthreads();
+    // ---- markers ---------------------------------------------------------------
+    const int nm = bc.nm;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
+    const int B[3] = {box.Bx, box.By, box.Bz};
+    const int k = blockIdx.x * PM_THREADS + tid;
+    if (k >= nm) return;
+    bool bad = false;
     const float xb[3] = {m.Xb[k], m.Xb[nm + k], m.Xb[2 * nm + k]};
     const float nbv[3] = {m.nb[k], m.nb[nm + k], m.nb[2 * nm + k]};
     float arm[3], nn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        arm[a] = d[a] * xb[0] + d[3 + a] * xb[1] + d[6 + a] * xb[2];
-        nn[a] = d[a] * nbv[0] + d[3 + a] * nbv[1] + d[6 + a] * nbv[2];
+        arm[a] = f_d[a] * xb[0] + f_d[3 + a] * xb[1] + f_d[6 + a] * xb[2];
+        nn[a] = f_d[a] * nbv[0] + f_d[3 + a] * nbv[1] + f_d[6 + a] * nbv[2];
     }
-    const float U[3] = {v[0] + (w[1] * arm[2] - w[2] * arm[1]), v[1] + (w[2] * arm[0] - w[0] * arm[2]),
-                        v[2] + (w[0] * arm[1] - w[1] * arm[0])};
-    const int n[3] = {g.nx, g.ny, g.nz};
-    const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
-    const int B[3] = {box.Bx, box.By, box.Bz};
-    bool bad = false;
+    const float U[3] = {f_v[0] + (f_w[1] * arm[2] - f_w[2] * arm[1]), f_v[1] + (f_w[2] * arm[0] - f_w[0] * arm[2]),
+                        f_v[2] + (f_w[0] * arm[1] - f_w[1] * arm[0])};
+    MRec r;
+    int bbv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float xr = cf[a] + arm[a];  // marker position relative to Ci
+        const float xr = f_cf[a] + arm[a];  // marker position relative to Ci
         const float fl = floorf(xr);
-        const float t = xr - fl;          // in [0, 1)
-        int base_rel = (int)fl - 1;       // stencil cells base_rel .. base_rel + 3
-        int bbv = ci[a] + base_rel - lo[a];
+        const float t = xr - fl;            // in [0, 1)
+        int base_rel = (int)fl - 1;         // stencil cells base_rel .. base_rel + 3
+        int bv = i_ci[a] + base_rel - i_lo[a];
         float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
         // a non-finite or out-of-box position must never index memory: park the
         // stencil at the box origin with zero weights and latch the status
-        if (!isfinite(xr) || bbv < 0 || bbv > B[a] - 4) {
-            bbv = 0;
-            base_rel = lo[a] - ci[a];
+        if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
+            bv = 0;
+            base_rel = i_lo[a] - i_ci[a];
             w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;
             bad = true;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) m.wgt[(4 * a + q) * nm + k] = w4[q];
-        m.bb[a * nm + k] = bbv;
-        const int abs_base = ci[a] + base_rel;
+        const int abs_base = i_ci[a] + base_rel;
         if (!per[a] && (abs_base < 0 || abs_base + 3 > n[a] - 1)) bad = true;
+        bbv[a] = bv;
+        float *dstw = (a == 0) ? r.wx : (a == 1) ? r.wy : r.wz;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dstw[q] = w4[q];
         m.U[a * nm + k] = U[a];
         m.n[a * nm + k] = nn[a];
         m.arm[a * nm + k] = arm[a];
     }
+    r.base = bbv[0] | (bbv[1] << 10) | (bbv[2] << 20);
+    r.hdS[0] = r.hdS[1] = r.hdS[2] = 0.0f;
+    m.rec[k] = r;
+    m.base[k] = r.base;
     if (bad) atomicCAS(&st->status, 0, STAT_DOMAIN);  // the first latched error wins
 }
 
-__global__ void __launch_bounds__(256) k_bin(BoxGeom box, int nm, const int *__restrict__ bb,
-                                             int *__restrict__ tile_list, int *__restrict__ tile_count, int cap) {
-    const int tile = blockIdx.x;
-    const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
-    const int t0[3] = {8 * tx, 8 * ty, 8 * tz};
-    __shared__ int wcount[8];
-    __shared__ int total;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) total = 0;
-    __syncthreads();
-    for (int chunk = 0; chunk < nm; chunk += 256) {
-        const int k = chunk + tid;
-        bool hit = false;
-        if (k < nm) {
-            hit = true;
+__device__ __forceinline__ float pick4(const float w[4], int i) {
+    return i == 0 ? w[0] : (i == 1 ? w[1] : (i == 2 ? w[2] : w[3]));
+}
+
+// Overlap of two 1-D 4-point stencils whose bases differ by d (|d| <= 3):
+// sum_c wk[c - bk] wj[c - bj] over the common cells.
+__device__ __forceinline__ float overlap4(const float wk[4], const float wj[4], int d) {
+    float o = 0.0f;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const int b = bb[a * nm + k];
-                hit = hit && (b <= t0[a] + 7) && (b + 3 >= t0[a]);
+    for (int i = 0; i < 4; ++i) {
+        const int ii = i - d;
+        if (ii >= 0 && ii < 4) o = fmaf(wk[i], pick4(wj, ii), o);
+    }
+    return o;
+}
+
+// Step l = 0 of Sec. 2.2 plus the operator of steps l = 1..3 in matrix form.
+// Interpolating u* + S[h] at X_k gives I[u*]_k + sum_j A_kj h_j with
+// A_kj = dS_j sum_x W(x - X_k) W(x - X_j); the Peskin weight is a tensor
+// product, so A_kj = dS_j Ox Oy Oz with one 4-point overlap per axis.
+// One block per marker k:
+//   warp 0: interpolation of u* and sigma (two stencil cells per lane,
+//           xor-shuffle sums), h^0 = U - I[u*], the traction dS sigma.n and
+//           its moment about C_m;
+//   all   : row k of A from the candidate list of the tile holding k's stencil
+//           base, one candidate per thread, block-wide ordered compaction in
+//           list (= marker) order: reproducible.
+constexpr int ROWS_THREADS = 256;
+constexpr int ROWS_WARPS = ROWS_THREADS / 32;
+
+__global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
+                                                                const int *__restrict__ wlist,
+                                                                const int *__restrict__ wcount, int cap,
+                                                                DevState *st) {
+    __shared__ int wc[ROWS_WARPS];
+    const int k = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const MRec rk = m.rec[k];
+    const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
+    if (warp == 0) {
+        const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
+        const float wxy = pick4(rk.wx, i) * pick4(rk.wy, j);
+        const float w0 = wxy * (kz ? rk.wz[1] : rk.wz[0]);
+        const float w1 = wxy * (kz ? rk.wz[3] : rk.wz[2]);
+        const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
+        const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
+        const size_t N = box.nbox;
+        float acc[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = w0 * ba.u[c * N + c0] + w1 * ba.u[c * N + c1];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
+#pragma unroll
+        for (int c = 0; c < 9; ++c)
+#pragma unroll
+            for (int q = 16; q > 0; q >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], q);
+        if (lane == 0) {
+            // l = 0: h_k = U_k - I[u*](X_k); traction dS sigma(X_k) n_k and its moment
+            const float dS = m.dS[k];
+            for (int c = 0; c < 3; ++c) {
+                const float h = m.U[c * nm + k] - acc[c];
+                m.r0[c * nm + k] = h;
+                m.hl[c * nm + k] = h;
+                m.rec[k].hdS[c] = h * dS;
+            }
+            const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
+            const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k];
+            const float f0 = dS * (sxx * nx + sxy * ny + sxz * nz);
+            const float f1 = dS * (sxy * nx + syy * ny + syz * nz);
+            const float f2 = dS * (sxz * nx + syz * ny + szz * nz);
+            const float r0 = m.arm[k], r1 = m.arm[nm + k], r2 = m.arm[2 * nm + k];
+            m.ft[k] = f0;
+            m.ft[nm + k] = f1;
+            m.ft[2 * nm + k] = f2;
+            m.ft[3 * nm + k] = r1 * f2 - r2 * f1;
+            m.ft[4 * nm + k] = r2 * f0 - r0 * f2;
+            m.ft[5 * nm + k] = r0 * f1 - r1 * f0;
+        }
+    }
+    // ---- row k of A -----------------------------------------------------------
+    const int tile = (bx / TILE) + box.tx * ((by / TILE) + box.ty * (bz / TILE));
+    const int cnt = wcount[tile];
+    const int *list = wlist + (size_t)tile * cap;
+    float *arow = m.aval + (size_t)k * ROWCAP;
+    int *irow = m.aidx + (size_t)k * ROWCAP;
+    int len = 0;
+    for (int base = 0; base < cnt; base += ROWS_THREADS) {
+        const int ii = base + tid;
+        bool hit = false;
+        float a = 0.0f;
+        int j = 0;
+        if (ii < cnt) {
+            j = __ldg(list + ii);
+            const MRec rj = m.rec[j];
+            const int dx = (rj.base & 1023) - bx, dy = ((rj.base >> 10) & 1023) - by, dz = ((rj.base >> 20) & 1023) - bz;
+            if (dx >= -3 && dx <= 3 && dy >= -3 && dy <= 3 && dz >= -3 && dz <= 3) {
+                a = m.dS[j] * overlap4(rk.wx, rj.wx, dx) * overlap4(rk.wy, rj.wy, dy) * overlap4(rk.wz, rj.wz, dz);
+                hit = true;
             }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) wcount[warp] = __popc(bal);
+        if (lane == 0) wc[warp] = __popc(bal);
         __syncthreads();
-        int off = total;
-        for (int w = 0; w < warp; ++w) off += wcount[w];
+        int off = len;
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < ROWS_WARPS; ++w) {
+            if (w < warp) off += wc[w];
+            tot += wc[w];
+        }
         if (hit) {
             const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            if (pos < cap) tile_list[(size_t)tile * cap + pos] = k;
+            if (pos < ROWCAP) {
+                arow[pos] = a;
+                irow[pos] = j;
+            }
         }
-        __syncthreads();
-        if (tid == 0) {
-            int s = 0;
-            for (int w = 0; w < 8; ++w) s += wcount[w];
-            total += s;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) tile_count[tile] = total < cap ? total : cap;
-}
-
-__global__ void __launch_bounds__(128) k_interp(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba, int mode) {
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= nm) return;
-    const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
-    const int bx = m.bb[k], by = m.bb[nm + k], bz = m.bb[2 * nm + k];
-    const float wxy = m.wgt[i * nm + k] * m.wgt[(4 + j) * nm + k];
-    const float w0 = wxy * m.wgt[(8 + kz) * nm + k];
-    const float w1 = wxy * m.wgt[(10 + kz) * nm + k];
-    const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
-    const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
-    const size_t N = box.nbox;
-    float acc[9];
-    const int nv = (mode == 0) ? 9 : 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float a0 = ba.u[c * N + c0], a1 = ba.u[c * N + c1];
-        if (mode != 0) {
-            a0 += ba.h[c * N + c0];
-            a1 += ba.h[c * N + c1];
-        }
-        acc[c] = w0 * a0 + w1 * a1;
-    }
-    if (mode == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
-    }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        if (c >= nv) break;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    }
-    if (lane != 0) return;
-    if (mode == 0) {
-        // l = 0: h_k = U_k - I[u*](X_k); surface traction dS sigma(X_k) n_k
-        for (int c = 0; c < 3; ++c) m.hl[c * nm + k] = m.U[c * nm + k] - acc[c];
-        const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
-        const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k], dS = m.dS[k];
-        const float f[3] = {dS * (sxx * nx + sxy * ny + sxz * nz), dS * (sxy * nx + syy * ny + syz * nz),
-                            dS * (sxz * nx + syz * ny + szz * nz)};
-        const float r[3] = {m.arm[k], m.arm[nm + k], m.arm[2 * nm + k]};
-        m.ft[k] = f[0];
-        m.ft[nm + k] = f[1];
-        m.ft[2 * nm + k] = f[2];
-        m.ft[3 * nm + k] = r[1] * f[2] - r[2] * f[1];
-        m.ft[4 * nm + k] = r[2] * f[0] - r[0] * f[2];
-        m.ft[5 * nm + k] = r[0] * f[1] - r[1] * f[0];
-    } else {
-        // l = 4: h_k <- h_k + U_k - I[u* + S h](X_k)
-        for (int c = 0; c < 3; ++c) m.hl[c * nm + k] += m.U[c * nm + k] - acc[c];
-    }
-}
-
-__global__ void __launch_bounds__(256) k_reduce_ft(int nm, const float *__restrict__ ft, double *partials,
-                                                   DevState *st) {
-    __shared__ double sh[6][256];
-    __shared__ bool last;
-    const int tid = threadIdx.x, b = blockIdx.x;
-    const int chunk = (nm + REDUCE_BLOCKS - 1) / REDUCE_BLOCKS;
-    const int k0 = b * chunk, k1 = min(nm, k0 + chunk);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = k0 + tid; k < k1; k += 256)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += (double)ft[c * nm + k];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sh[c][tid] = acc[c];
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (tid < s)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) sh[c][tid] += sh[c][tid + s];
+        len += tot;
         __syncthreads();
     }
     if (tid == 0) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) partials[6 * b + c] = sh[c][0];
-        __threadfence();
-        const unsigned ticket = atomicAdd(&st->counter, 1u);
-        last = (ticket == REDUCE_BLOCKS - 1);
+        m.alen[k] = len < ROWCAP ? len : ROWCAP;
+        if (len > ROWCAP) atomicCAS(&st->status, 0, STAT_OVERFLOW);
     }
-    __syncthreads();
-    if (!last || tid != 0) return;
-    __threadfence();
-    double tot[6] = {0, 0, 0, 0, 0, 0};
-    for (int bb = 0; bb < REDUCE_BLOCKS; ++bb)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) tot[c] += __ldcg(partials + 6 * bb + c);
-    bool finite = true;
-    for (int c = 0; c < 3; ++c) {
-        st->F[c] = tot[c];
-        st->T[c] = tot[3 + c];
-        finite = finite && isfinite(tot[c]) && isfinite(tot[3 + c]);
-    }
-    if (!finite) atomicCAS(&st->status, 0, STAT_DIVERGED);
-    st->counter = 0;
 }
 
-__global__ void __launch_bounds__(512) k_spread(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
-                                                const int *__restrict__ tile_list, const int *__restrict__ tile_count,
-                                                int cap) {
-    constexpr int CH = 256;
-    __shared__ int sb[3][CH];
-    __shared__ float sw[12][CH];
-    __shared__ float sh[3][CH];
-    const int tile = blockIdx.x;
-    const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
-    const int tid = threadIdx.x;
-    const int cx = 8 * tx + (tid & 7), cy = 8 * ty + ((tid >> 3) & 7), cz = 8 * tz + (tid >> 6);
-    const int cnt = tile_count[tile];
+// One cycle of steps l = 1..4 (Sec. 2.2) in matrix form:
+//   h_out_k = h_in_k + U_k - I[u* + S h_in](X_k) = h_in_k + r0_k - sum_j A_kj h_in_j.
+// One warp per marker, entries of the row in order per lane, xor-shuffle sum.
+// The last cycle also stores h dS for the spreading of h_imm.
+__global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArrays m, const float *__restrict__ h_in,
+                                                             float *__restrict__ h_out, int last) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.x * INTERP_WARPS + warp;
+    if (k >= nm) return;
+    const int len = m.alen[k];
+    const float *arow = m.aval + (size_t)k * ROWCAP;
+    const int *irow = m.aidx + (size_t)k * ROWCAP;
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    for (int base = 0; base < cnt; base += CH) {
-        if (tid < CH && base + tid < cnt) {
-            const int k = tile_list[(size_t)tile * cap + base + tid];
+    for (int e = lane; e < len; e += 32) {
+        const float a = arow[e];
+        const int j = irow[e];
+        ax = fmaf(a, h_in[j], ax);
+        ay = fmaf(a, h_in[nm + j], ay);
+        az = fmaf(a, h_in[2 * nm + j], az);
+    }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) sb[a][tid] = m.bb[a * nm + k];
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (lane == 0) {
+        const float acc[3] = {ax, ay, az};
+        const float dS = m.dS[k];
+        for (int c = 0; c < 3; ++c) {
+            const float h = h_in[c * nm + k] + (m.r0[c * nm + k] - acc[c]);
+            h_out[c * nm + k] = h;
+            if (last) m.rec[k].hdS[c] = h * dS;
+        }
+    }
+}
+
+// F = sum_k dS sigma.n, T = sum_k arm x (dS sigma.n) in FP64: warp c sums
+// component c, lane l the markers l, l+32, ... in order, then an xor tree.
+__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st) {
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int k = lane; k < nm; k += 32) a += (double)ft[c * nm + k];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) sw[q][tid] = m.wgt[q * nm + k];
-            const float dS = m.dS[k];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+        if (c < 3) st->F[c] = a; else st->T[c - 3] = a;
+        if (!isfinite(a)) atomicCAS(&st->status, 0, STAT_DIVERGED);
+    }
+}
+
+constexpr int SPREAD_SLICES = 8;                               // candidate slices per tile
+constexpr int SPREAD_THREADS = TILE * TILE * TILE * SPREAD_SLICES;  // 64 cells x 8 slices
+constexpr int SPREAD_STAGE = 256;
+
+// h_imm(x) = S[h](x) = sum_k W(x - X_k) h_k dS_k on the support box.  One block
+// per 4^3 tile: the tile's candidate records are staged in shared memory as
+// structure of arrays; thread (cell c, slice q) sums slice q of each staged
+// chunk for cell c; the 8 slice sums are added in slice order (reproducible).
+__global__ void __launch_bounds__(SPREAD_THREADS) k_spread(BoxGeom box, const MRec *__restrict__ rec, BoxArrays ba,
+                                                           const int *__restrict__ tile_list,
+                                                           const int *__restrict__ tile_count, int cap) {
+    constexpr int TC = TILE * TILE * TILE;
+    __shared__ int sbase[SPREAD_STAGE];
+    __shared__ float sw[12][SPREAD_STAGE];
+    __shared__ float sh[3][SPREAD_STAGE];
+    __shared__ float part[SPREAD_SLICES][3][TC];
+    const int tile = blockIdx.x;
+    const int cnt = tile_count[tile];
+    const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
+    const int tid = threadIdx.x, c = tid % TC, q = tid / TC;
+    const int cx = TILE * tx + c % TILE, cy = TILE * ty + (c / TILE) % TILE, cz = TILE * tz + c / (TILE * TILE);
+    const int *list = tile_list + (size_t)tile * cap;
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    for (int base = 0; base < cnt; base += SPREAD_STAGE) {
+        const int n = min(SPREAD_STAGE, cnt - base);
+        if (tid < n) {
+            const MRec r = rec[__ldg(list + base + tid)];
+            sbase[tid] = r.base;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) sh[a][tid] = m.hl[a * nm + k] * dS;
+            for (int e = 0; e < 4; ++e) {
+                sw[e][tid] = r.wx[e];
+                sw[4 + e][tid] = r.wy[e];
+                sw[8 + e][tid] = r.wz[e];
+            }
+            sh[0][tid] = r.hdS[0];
+            sh[1][tid] = r.hdS[1];
+            sh[2][tid] = r.hdS[2];
         }
         __syncthreads();
-        const int nloc = min(CH, cnt - base);
-        for (int jj = 0; jj < nloc; ++jj) {
-            const int dx = cx - sb[0][jj], dy = cy - sb[1][jj], dz = cz - sb[2][jj];
+        const int j0 = (n * q) / SPREAD_SLICES, j1 = (n * (q + 1)) / SPREAD_SLICES;
+        for (int jj = j0; jj < j1; ++jj) {
+            const int pb = sbase[jj];
+            const int dx = cx - (pb & 1023), dy = cy - ((pb >> 10) & 1023), dz = cz - ((pb >> 20) & 1023);
             if ((unsigned)dx < 4u && (unsigned)dy < 4u && (unsigned)dz < 4u) {
                 const float wv = sw[dx][jj] * sw[4 + dy][jj] * sw[8 + dz][jj];
-                ax += wv * sh[0][jj];
-                ay += wv * sh[1][jj];
-                az += wv * sh[2][jj];
+                ax = fmaf(wv, sh[0][jj], ax);
+                ay = fmaf(wv, sh[1][jj], ay);
+                az = fmaf(wv, sh[2][jj], az);
             }
         }
         __syncthreads();
     }
-    if (cx < box.Bx && cy < box.By && cz < box.Bz) {
-        const size_t c = ((size_t)cz * box.By + cy) * box.Bx + cx;
-        ba.h[c] = ax;
-        ba.h[box.nbox + c] = ay;
-        ba.h[2 * box.nbox + c] = az;
+    part[q][0][c] = ax;
+    part[q][1][c] = ay;
+    part[q][2][c] = az;
+    __syncthreads();
+    if (tid < TC) {
+        float hx = 0.0f, hy = 0.0f, hz = 0.0f;
+#pragma unroll
+        for (int w = 0; w < SPREAD_SLICES; ++w) {  // fixed slice order: reproducible
+            hx += part[w][0][tid];
+            hy += part[w][1][tid];
+            hz += part[w][2][tid];
+        }
+        if (cx < box.Bx && cy < box.By && cz < box.Bz) {
+            const size_t b = ((size_t)cz * box.By + cy) * box.Bx + cx;
+            ba.h[b] = hx;
+            ba.h[box.nbox + b] = hy;
+            ba.h[2 * box.nbox + b] = hz;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-cudaError_t launch_particle(const Geom &g, const BodyConst &bc, DevState *st, cudaStream_t s) {
-    k_particle<<<1, 32, 0, s>>>(g, bc, st);
+cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st, int slot,
+                                    int advance, MarkerArrays m, cudaStream_t s) {
+    k_particle_markers<<<(bc.nm + PM_THREADS - 1) / PM_THREADS, PM_THREADS, 0, s>>>(g, bc, box, st, slot, advance, m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_markers(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st, MarkerArrays m,
-                           cudaStream_t s) {
-    k_markers<<<(bc.nm + 127) / 128, 128, 0, s>>>(g, bc, box, st, m);
+cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
+                           const int *tile_count, int cap, DevState *st, cudaStream_t s) {
+    const int ntiles = box.tx * box.ty * box.tz;  // list 1 (rows of A) follows list 0
+    k_interp0_rows<<<nm, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
+                                               tile_count + ntiles, cap, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const BoxGeom &box, int nm, const int *bb, int *tile_list, int *tile_count, int cap,
-                       cudaStream_t s) {
-    k_bin<<<box.tx * box.ty * box.tz, 256, 0, s>>>(box, nm, bb, tile_list, tile_count, cap);
+cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, int last, cudaStream_t s) {
+    k_cycle<<<(nm + INTERP_WARPS - 1) / INTERP_WARPS, 32 * INTERP_WARPS, 0, s>>>(nm, m, h_in, h_out, last);
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, int mode, cudaStream_t s) {
-    const long long threads = (long long)nm * 32;
-    k_interp<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(box, nm, m, ba, mode);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_ft(int nm, MarkerArrays m, double *partials, DevState *st, cudaStream_t s) {
-    k_reduce_ft<<<REDUCE_BLOCKS, 256, 0, s>>>(nm, m.ft, partials, st);
+cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, cudaStream_t s) {
+    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
                           const int *tile_count, int cap, cudaStream_t s) {
-    k_spread<<<box.tx * box.ty * box.tz, 512, 0, s>>>(box, nm, m, ba, tile_list, tile_count, cap);
+    (void)nm;
+    k_spread<<<box.tx * box.ty * box.tz, SPREAD_THREADS, 0, s>>>(box, m.rec, ba, tile_list, tile_count, cap);
     return cudaGetLastError();
 }
 

@@ -10,14 +10,15 @@
 //
 // GB300 formulation (not the paper's): both f0 and f1 live in the 27-term
 // tensor-product Hermite basis H_p(xi_x) H_q(xi_y) H_r(xi_z), p,q,r <= 2,
-// which is orthogonal under the D3Q27 weights.  A collision is therefore
-//   moments  : 3 separable passes of 3-point sums over x, y, z  (10 moments)
-//   collision: C_pqr = rho u^p u^q u^r + (1 - 1/tau) a1_pqr, where
-//              a1_pqr = 1/2 sum_ab P1_ab d^2(u^p u^q u^r)/du_a du_b
-//              (the closed form of the recursion: a sum over index pairs)
-//   rebuild  : 3 separable passes of 3x3 transforms with the weighted
-//              basis g_p(xi) = w1(xi) H_p(xi)
-// about 450 FP32 flops per cell.  Populations are stored as deviations
+// which is orthogonal under the D3Q27 weights.  The equilibrium coefficients
+// are the monomials rho u_x^p u_y^q u_z^r and the recursive coefficients are
+// a1_pqr = 1/2 sum_ab P1_ab d^2(u^p u^q u^r)/du_a du_b (the closed form of
+// the recursion: a sum over index pairs), so every term is an outer product
+// of one 3-vector per axis and a collision is
+//   moments : 3 separable passes of 3-point sums over x, y, z (10 moments)
+//   rebuild : per-axis factors X, X', X'' and 9 (y,z) pair terms, then
+//             3 FMAs per population (collide_factored below)
+// about 300 FP32 flops per cell.  Populations are stored as deviations
 // q_i = f_i - w_i (FP32) or q_i / w_i scaled (FP16/BF16); the moments use
 // drho = sum q, so no O(1) term cancels in single precision.
 //
@@ -63,15 +64,17 @@ __device__ __forceinline__ float eqfac_m1(int e, float u) {
 }
 __device__ __forceinline__ float ghost_dev(int i, float ux, float uy, float uz) {
     float a = eqfac_m1(i % 3, ux), b = eqfac_m1((i / 3) % 3, uy), c = eqfac_m1(i / 9, uz);
-    return wq(i) * (a + b + c + a * b + a * c + b * c + a * b * c);
+    return Wq(i) * (a + b + c + a * b + a * c + b * c + a * b * c);  // scaled deviation
 }
 
-// Pull the 27 pre-collision deviations of cell (x, y, zl) from the
+// Pull the 27 pre-collision scaled deviations of cell (x, y, zl) from the
 // post-collision buffer: f_i(x) = f*_i(x - xi_i); no-slip faces bounce back
 // (halfway), the pressure top reads the ghost equilibrium, periodic faces wrap.
+// A source on the plane that just entered the sliding window (reseed >= 0)
+// holds stale data and reads as the rest equilibrium (deviation 0).
 template <int ST>
 __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::T *__restrict__ f, int x, int y,
-                                       int zl, int ring, const float *__restrict__ utop, float q[27]) {
+                                       int zl, int ring, int reseed, const float *__restrict__ utop, float q[27]) {
     int sx[3], sy[3], szp[3], bxf[3], byf[3], bzf[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -86,8 +89,27 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
             else bzf[e] = (g.bc_top == BC_PRESSURE) ? 2 : 1;
         }
         szp[e] = bzf[e] ? 0 : zphys(zs, ring, g.nz);
+        if (bzf[e] == 0 && szp[e] == reseed) bzf[e] = 3;
     }
-    const size_t own = (size_t)zphys(zl, ring, g.nz) * g.plane + (size_t)y * g.nx + x;
+    const int nx = g.nx, plane = (int)g.plane, ncell = (int)g.ncell;
+    if ((bxf[0] | bxf[2] | byf[0] | byf[2] | bzf[0] | bzf[1] | bzf[2]) == 0) {
+        // interior (or periodic) cell: 27 plain loads, 32-bit offsets
+#pragma unroll
+        for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+            for (int ey = 0; ey < 3; ++ey) {
+                const int row = szp[ez] * plane + sy[ey] * nx;
+#pragma unroll
+                for (int ex = 0; ex < 3; ++ex) {
+                    const int i = ex + 3 * ey + 9 * ez;
+                    q[i] = Codec<ST>::load(f + i * ncell + row + sx[ex], i);
+                }
+            }
+        return;
+    }
+    const int zo = zphys(zl, ring, g.nz);
+    const int own = zo * plane + y * nx + x;
+    const bool own_rest = (zo == reseed);
 #pragma unroll
     for (int ez = 0; ez < 3; ++ez)
 #pragma unroll
@@ -96,19 +118,21 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
             for (int ex = 0; ex < 3; ++ex) {
                 const int i = ex + 3 * ey + 9 * ez;
                 if (bxf[ex] == 1 || byf[ey] == 1 || bzf[ez] == 1) {
-                    q[i] = Codec<ST>::load(f + (size_t)(26 - i) * g.ncell + own, 26 - i);
+                    q[i] = own_rest ? 0.0f : Codec<ST>::load(f + (26 - i) * ncell + own, 26 - i);
+                } else if (bzf[ez] == 3) {
+                    q[i] = 0.0f;
                 } else if (bzf[ez] == 2) {
-                    const size_t c = (size_t)sy[ey] * g.nx + sx[ex];
-                    q[i] = ghost_dev(i, __ldg(utop + c), __ldg(utop + g.plane + c), __ldg(utop + 2 * g.plane + c));
+                    const int c = sy[ey] * nx + sx[ex];
+                    q[i] = ghost_dev(i, __ldg(utop + c), __ldg(utop + plane + c), __ldg(utop + 2 * plane + c));
                 } else {
-                    q[i] = Codec<ST>::load(
-                        f + (size_t)i * g.ncell + (size_t)szp[ez] * g.plane + (size_t)sy[ey] * g.nx + sx[ex], i);
+                    q[i] = Codec<ST>::load(f + i * ncell + szp[ez] * plane + sy[ey] * nx + sx[ex], i);
                 }
             }
 }
 
-// Raw moments of the deviations up to second order: drho = sum q,
-// j = sum xi q, Pi'_ab = sum xi_a xi_b q, by three separable 3-point passes.
+// Raw moments of the scaled deviations up to second order (all times 216):
+// drho = sum s, j = sum xi s, Pi'_ab = sum xi_a xi_b s, by three separable
+// 3-point passes.
 struct Mom {
     float drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
@@ -147,18 +171,19 @@ __device__ __forceinline__ Mom moments27(const float q[27]) {
     return m;
 }
 
-// Macroscopic quantities from the deviation moments:
-//   rho = 1 + drho, u = j / rho,
-//   P1 = Pi - rho (I/3 + u u) = Pi' - drho I / 3 - j u^T.
+// Macroscopic quantities from the scaled moments (the tilde quantities are
+// 216 times the physical ones):
+//   drho = drho~ / 216, rho = 1 + drho, u = j~ / (216 + drho~),
+//   P1~ = Pi'~ - drho~ I / 3 - j~ u^T   (= 216 [Pi - rho (I/3 + u u)]).
 struct Macro {
-    float drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
+    float drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;  // P: scaled by 216
 };
 
 __device__ __forceinline__ Macro macro_of(const Mom &m) {
     Macro M;
-    M.drho = m.drho;
-    M.rho = 1.0f + m.drho;
-    const float ir = 1.0f / M.rho;
+    M.drho = m.drho * INV_SCALE;
+    M.rho = 1.0f + M.drho;
+    const float ir = 1.0f / (SCALE + m.drho);
     M.ux = m.jx * ir;
     M.uy = m.jy * ir;
     M.uz = m.jz * ir;
@@ -172,78 +197,101 @@ __device__ __forceinline__ Macro macro_of(const Mom &m) {
     return M;
 }
 
-// Post-collision Hermite coefficients C[p + 3q + 9r] (deviation: C_000 - 1).
-// forced: equilibrium part (1-w) rho m(u) + w rho m(u + tau h)  (scheme 0) or
-// rho m(u + tau h) (scheme 1), m = monomial u_x^p u_y^q u_z^r.
-__device__ __forceinline__ void collide_coeffs(const Macro &M, float omega, float tau, bool forced, float hx,
-                                               float hy, float hz, int scheme, float C[27]) {
-    const float px[3] = {1.0f, M.ux, M.ux * M.ux};
-    const float py[3] = {1.0f, M.uy, M.uy * M.uy};
-    const float pz[3] = {1.0f, M.uz, M.uz * M.uz};
-    float ce[27];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int p = 0; p < 3; ++p) ce[p + 3 * q + 9 * r] = M.rho * px[p] * py[q] * pz[r];
-    if (forced) {
-        const float vx = M.ux + tau * hx, vy = M.uy + tau * hy, vz = M.uz + tau * hz;
-        const float qx[3] = {1.0f, vx, vx * vx};
-        const float qy[3] = {1.0f, vy, vy * vy};
-        const float qz[3] = {1.0f, vz, vz * vz};
-        const float a = (scheme == 1) ? 0.0f : (1.0f - omega);
-        const float b = (scheme == 1) ? 1.0f : omega;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-#pragma unroll
-                for (int p = 0; p < 3; ++p) {
-                    const int k = p + 3 * q + 9 * r;
-                    ce[k] = a * ce[k] + b * (M.rho * qx[p] * qy[q] * qz[r]);
-                }
-    }
-    const float om1 = 1.0f - omega;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                // a1_pqr: half the P1-weighted Hessian of the monomial u^p u^q u^r
-                float a1 = 0.0f;
-                if (p == 2) a1 += M.Pxx * py[q] * pz[r];
-                if (q == 2) a1 += M.Pyy * px[p] * pz[r];
-                if (r == 2) a1 += M.Pzz * px[p] * py[q];
-                if (p > 0 && q > 0) a1 += (float)(p * q) * M.Pxy * px[p - 1] * py[q - 1] * pz[r];
-                if (p > 0 && r > 0) a1 += (float)(p * r) * M.Pxz * px[p - 1] * py[q] * pz[r - 1];
-                if (q > 0 && r > 0) a1 += (float)(q * r) * M.Pyz * px[p] * py[q - 1] * pz[r - 1];
-                const int k = p + 3 * q + 9 * r;
-                C[k] = ce[k] + om1 * a1;
-            }
-    C[0] = M.drho;  // rho - 1: only deviations are stored
+// Per-axis factors of the collision.  With m(u) = prod_a u_a^{p_a} and the
+// weighted basis g_p(xi) = w1(xi) H_p(xi), every term of the post-collision
+// Hermite expansion is an outer product of one 3-vector per axis, so each
+// population is rebuilt directly from per-axis vectors (here scaled by 6 so
+// that the weights 6 w1 = (1, 4, 1) are exact):
+//   X(e)   = 6 sum_p u^p g_p(e)      = W1(e) (1 + a(e)),  a = (-3u+3u^2, -3u^2/2, 3u+3u^2)
+//   X'(e)  = 6 sum_p p u^(p-1) g_p(e) = (6u - 3, -12u, 6u + 3)
+//   X''(e) = 6 sum_p p(p-1) u^(p-2) g_p(e) = (6, -12, 6)
+// and, for P' = (1 - 1/tau) P1 (P1 the physical tensor),
+//   s_i = 216 (f*_i - w_i) = [rho X Y Z - W_i] + X'' [P'xx/2 Y Z]
+//         + X [P'yy/2 Y'' Z + P'zz/2 Y Z'' + P'yz Y' Z'] + X' [P'xy Y' Z + P'xz Y Z'],
+// the bracketed equilibrium deviation evaluated as W_i (rho E + drho) with
+// E = (1+a_x)(1+a_y)(1+a_z) - 1 expanded so no O(1) term cancels.
+struct AxisF {
+    float a[3], X[3], Xp[3];
+};
+
+__device__ __forceinline__ AxisF axis_of(float u) {
+    AxisF f;
+    const float u2 = u * u;
+    f.a[0] = 3.0f * (u2 - u);
+    f.a[1] = -1.5f * u2;
+    f.a[2] = 3.0f * (u2 + u);
+    f.X[0] = 1.0f + f.a[0];
+    f.X[1] = 4.0f * (1.0f + f.a[1]);
+    f.X[2] = 1.0f + f.a[2];
+    f.Xp[0] = 6.0f * u - 3.0f;
+    f.Xp[1] = -12.0f * u;
+    f.Xp[2] = 6.0f * u + 3.0f;
+    return f;
 }
 
-// Rebuild q_i = sum_pqr C_pqr g_p(xi_x) g_q(xi_y) g_r(xi_z) in place, with the
-// weighted 1-D basis g(-1) = (1/6, -1/2, 1/2), g(0) = (2/3, 0, -1), g(+1) = (1/6, 1/2, 1/2).
-__device__ __forceinline__ void tri(float &c0, float &c1, float &c2) {
-    const float t = c0 * (1.0f / 6.0f) + 0.5f * c2;
-    const float s = 0.5f * c1;
-    const float mid = c0 * (2.0f / 3.0f) - c2;
-    c0 = t - s;
-    c1 = mid;
-    c2 = t + s;
+// Scaled equilibrium deviation 216 (f0_i(rho, u) - w_i), times c, into s.
+__device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
+                                           float drho, float c, float s[27], bool first) {
+    float sxy[9];
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = fmaf(fx.a[ex], fy.a[ey], fx.a[ex] + fy.a[ey]);
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = k + 9 * ez;
+            const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
+            const float v = (c * Wq(i)) * fmaf(E, rho, drho);
+            s[i] = first ? v : s[i] + v;
+        }
 }
-__device__ __forceinline__ void rebuild27(float C[27]) {
+
+// Post-collision scaled deviations s_i = 216 (f*_i - w_i) of one cell.
+// forced: equilibrium part (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
+// f0(u + tau h) (scheme 1), both reducing to f0(u) at h = 0.
+__device__ __forceinline__ void collide_factored(const Macro &M, float omega, float tau, bool forced, float hx,
+                                                 float hy, float hz, int scheme, float s[27]) {
+    const AxisF fx = axis_of(M.ux), fy = axis_of(M.uy), fz = axis_of(M.uz);
+    if (!forced) {
+        add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f, s, true);
+    } else {
+        const AxisF vx = axis_of(M.ux + tau * hx), vy = axis_of(M.uy + tau * hy), vz = axis_of(M.uz + tau * hz);
+        if (scheme == 1) {
+            add_eq_dev(vx, vy, vz, M.rho, M.drho, 1.0f, s, true);
+        } else {
+            add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f - omega, s, true);
+            add_eq_dev(vx, vy, vz, M.rho, M.drho, omega, s, false);
+        }
+    }
+    // P' = (1 - 1/tau) P1 with P1 = P1~ / 216
+    const float om1 = (1.0f - omega) * INV_SCALE;
+    const float hxx = 0.5f * om1 * M.Pxx, hyy = 0.5f * om1 * M.Pyy, hzz = 0.5f * om1 * M.Pzz;
+    const float pxy = om1 * M.Pxy, pxz = om1 * M.Pxz, pyz = om1 * M.Pyz;
+    const float Xpp[3] = {6.0f, -12.0f, 6.0f};
+    float cY[3], cZ[3], bY[3], aY[3], bZ[3];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) tri(C[k], C[k + 9], C[k + 18]);  // z: stride 9
+    for (int e = 0; e < 3; ++e) {
+        cY[e] = hyy * Xpp[e];     // P'yy/2 Y''
+        cZ[e] = hzz * Xpp[e];     // P'zz/2 Z''
+        bY[e] = pyz * fy.Xp[e];   // P'yz Y'
+        aY[e] = pxy * fy.Xp[e];   // P'xy Y'
+        bZ[e] = pxz * fz.Xp[e];   // P'xz Z'
+    }
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+    for (int ez = 0; ez < 3; ++ez)
 #pragma unroll
-        for (int p = 0; p < 3; ++p) tri(C[p + 9 * r], C[p + 3 + 9 * r], C[p + 6 + 9 * r]);  // y: stride 3
+        for (int ey = 0; ey < 3; ++ey) {
+            const float G0 = hxx * (fy.X[ey] * fz.X[ez]);
+            const float G1 = fmaf(cY[ey], fz.X[ez], fmaf(fy.X[ey], cZ[ez], bY[ey] * fz.Xp[ez]));
+            const float G2 = fmaf(aY[ey], fz.X[ez], fy.X[ey] * bZ[ez]);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) tri(C[3 * k], C[3 * k + 1], C[3 * k + 2]);  // x: stride 1
+            for (int ex = 0; ex < 3; ++ex) {
+                const int i = ex + 3 * ey + 9 * ez;
+                s[i] = fmaf(Xpp[ex], G0, fmaf(fx.X[ex], G1, fmaf(fx.Xp[ex], G2, s[i])));
+            }
+        }
 }
 
 // Wrapped offset of window coordinate c from box origin lo along one axis.
@@ -257,29 +305,61 @@ __device__ __forceinline__ int box_rel(int c, int lo, int n, bool periodic) {
 }
 
 // ---------------------------------------------------------------------------
-// K1: fused collide + stream over every cell of the window.
+// K1: fused collide + stream.  REGION_ALL: every cell; REGION_FAR: every cell
+// outside the near region (support box grown by NEAR_MARGIN cells);
+// REGION_NEAR: the near region only (grid over its extent).  The far and near
+// launches together cover the window once.
 template <int ST, bool BOX>
 __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename Codec<ST>::T *__restrict__ src,
                                                         typename Codec<ST>::T *__restrict__ dst,
                                                         const float *__restrict__ utop_in,
-                                                        float *__restrict__ utop_out,
-                                                        const DevState *__restrict__ st,
-                                                        const float *__restrict__ hbox, BoxGeom box) {
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * 4 + threadIdx.y;
-    const int zl = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
-    const int ring = st->ring;
+                                                        float *__restrict__ utop_out, DevState *st, int slot,
+                                                        int slot_out, const float *__restrict__ hbox, BoxGeom box,
+                                                        int region) {
+    if (slot_out >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+        threadIdx.y == 0) {
+        // carry the body and window to the next time level (no entering plane there)
+        st->s[slot_out] = st->s[slot];
+        st->s[slot_out].reseed = -1;
+    }
+    int x, y, zl;
+    const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
+    if (region == REGION_NEAR) {
+        // grid over the near region; map to window cells, skip cells outside closed faces
+        const int rx = blockIdx.x * 32 + threadIdx.x, ry = blockIdx.y * 4 + threadIdx.y, rz = blockIdx.z;
+        if (rx >= box.Bx + 2 * NEAR_MARGIN || ry >= box.By + 2 * NEAR_MARGIN) return;
+        x = st->s[slot].box_lo[0] - NEAR_MARGIN + rx;
+        y = st->s[slot].box_lo[1] - NEAR_MARGIN + ry;
+        zl = st->s[slot].box_lo[2] - NEAR_MARGIN + rz;
+        if (perx) { x %= g.nx; if (x < 0) x += g.nx; } else if (x < 0 || x >= g.nx) return;
+        if (pery) { y %= g.ny; if (y < 0) y += g.ny; } else if (y < 0 || y >= g.ny) return;
+        if (perz) { zl %= g.nz; if (zl < 0) zl += g.nz; } else if (zl < 0 || zl >= g.nz) return;
+    } else {
+        x = blockIdx.x * 32 + threadIdx.x;
+        y = blockIdx.y * 4 + threadIdx.y;
+        zl = blockIdx.z;
+        if (x >= g.nx || y >= g.ny) return;
+        if (region == REGION_FAR) {
+            const int rx = box_rel(x, st->s[slot].box_lo[0] - NEAR_MARGIN, g.nx, perx);
+            const int ry = box_rel(y, st->s[slot].box_lo[1] - NEAR_MARGIN, g.ny, pery);
+            const int rz = box_rel(zl, st->s[slot].box_lo[2] - NEAR_MARGIN, g.nz, perz);
+            if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
+                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN) &&
+                (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN))
+                return;
+        }
+    }
+    const int ring = st->s[slot].ring;
     float q[27];
-    pull27<ST>(g, src, x, y, zl, ring, utop_in, q);
+    pull27<ST>(g, src, x, y, zl, ring, st->s[slot].reseed, utop_in, q);
     const float tau = tau_of(g, zl);
     const float omega = 1.0f / tau;
     bool forced = false;
     float hx = 0.0f, hy = 0.0f, hz = 0.0f;
-    if (BOX) {
-        const int rx = box_rel(x, st->box_lo[0], g.nx, g.bc_x == BC_PERIODIC);
-        const int ry = box_rel(y, st->box_lo[1], g.ny, g.bc_y == BC_PERIODIC);
-        const int rz = box_rel(zl, st->box_lo[2], g.nz, g.bc_bottom == BC_PERIODIC);
+    if (BOX && region != REGION_FAR) {
+        const int rx = box_rel(x, st->s[slot].box_lo[0], g.nx, perx);
+        const int ry = box_rel(y, st->s[slot].box_lo[1], g.ny, pery);
+        const int rz = box_rel(zl, st->s[slot].box_lo[2], g.nz, perz);
         if ((unsigned)rx < (unsigned)box.Bx && (unsigned)ry < (unsigned)box.By && (unsigned)rz < (unsigned)box.Bz) {
             const size_t b = ((size_t)rz * box.By + ry) * box.Bx + rx;
             hx = __ldg(hbox + b);
@@ -295,12 +375,11 @@ __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename C
         utop_out[g.plane + c] = M.uy;
         utop_out[2 * g.plane + c] = M.uz;
     }
-    float C[27];
-    collide_coeffs(M, omega, tau, forced, hx, hy, hz, g.force_scheme, C);
-    rebuild27(C);
-    const size_t own = (size_t)zphys(zl, ring, g.nz) * g.plane + (size_t)y * g.nx + x;
+    collide_factored(M, omega, tau, forced, hx, hy, hz, g.force_scheme, q);
+    const int own = zphys(zl, ring, g.nz) * (int)g.plane + y * g.nx + x;
+    const int ncell = (int)g.ncell;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + own, C[i], i);
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i], i);
 }
 
 // Equilibrium of given (rho - 1, u) fields (doubles, window order) as the
@@ -310,19 +389,17 @@ __global__ void k_init_equilibrium(Geom g, typename Codec<ST>::T *__restrict__ d
                                    const double *__restrict__ u, float *__restrict__ utop) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
-    const float dr = drho ? (float)drho[c] : 0.0f;
     Macro M;
-    M.drho = dr;
+    M.drho = drho ? (float)drho[c] : 0.0f;
     M.rho = (float)(1.0 + (drho ? drho[c] : 0.0));
     M.ux = u ? (float)u[3 * c] : 0.0f;
     M.uy = u ? (float)u[3 * c + 1] : 0.0f;
     M.uz = u ? (float)u[3 * c + 2] : 0.0f;
     M.Pxx = M.Pyy = M.Pzz = M.Pxy = M.Pxz = M.Pyz = 0.0f;
-    float C[27];
-    collide_coeffs(M, 1.0f, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, C);
-    rebuild27(C);
+    float q[27];
+    collide_factored(M, 1.0f, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
 #pragma unroll
-    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + c, C[i], i);
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + c, q[i], i);
     const long long z = c / g.plane;
     if (z == g.nz - 1) {
         const long long p = c - z * g.plane;
@@ -336,17 +413,17 @@ __global__ void k_init_equilibrium(Geom g, typename Codec<ST>::T *__restrict__ d
 template <int ST>
 __global__ void __launch_bounds__(128) k_macro(Geom g, const typename Codec<ST>::T *__restrict__ src,
                                                const float *__restrict__ utop_in, const DevState *__restrict__ st,
-                                               float *__restrict__ out, int pops) {
+                                               int slot, float *__restrict__ out, int pops) {
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 4 + threadIdx.y;
     const int zl = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     float q[27];
-    pull27<ST>(g, src, x, y, zl, st->ring, utop_in, q);
+    pull27<ST>(g, src, x, y, zl, st->s[slot].ring, st->s[slot].reseed, utop_in, q);
     const size_t c = ((size_t)zl * g.ny + y) * g.nx + x;
     if (pops) {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) out[(size_t)i * g.ncell + c] = q[i];
+        for (int i = 0; i < 27; ++i) out[(size_t)i * g.ncell + c] = q[i] * INV_SCALE;
         return;
     }
     const Macro M = macro_of(moments27(q));
@@ -356,30 +433,86 @@ __global__ void __launch_bounds__(128) k_macro(Geom g, const typename Codec<ST>:
     out[3 * g.ncell + c] = M.uz;
 }
 
-// Window slide: the plane that enters the ring is reset to the rest state.
-template <int ST>
-__global__ void k_reseed(Geom g, typename Codec<ST>::T *__restrict__ dst, const DevState *__restrict__ st) {
-    const int p = st->reseed_plane;
-    if (p < 0) return;
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.plane * 27) return;
-    const long long i = c / g.plane, xy = c - i * g.plane;
-    Codec<ST>::store(dst + (size_t)i * g.ncell + (size_t)p * g.plane + xy, 0.0f, (int)i);
-}
+// K2 + binning, one launch.  Blocks [0, nmom): u* and the stress of Eq. 10,
+// sigma = -p I + (1/(2 tau) - 1) P1 with p = c_s^2 (rho - 1), at every
+// support-box cell, from f(t+1) pulled from the post-collision buffer (box
+// cells outside a closed face get zeros).  Blocks [nmom, nmom + ntiles): for
+// one TILE^3 tile of the box, two lists in marker order (ordered compaction
+// with warp ballots; no atomics): list 0, the markers whose 4x4x4 stencil
+// overlaps the tile (spreading); list 1, those whose stencil overlaps the
+// stencil of any marker based in the tile (rows of A).
+constexpr int MB_THREADS = 256;
 
-// K2: u* and the stress of Eq. 10, sigma = -p I + (1/(2 tau) - 1) P1 with
-// p = c_s^2 (rho - 1), at every support-box cell, from f(t+1) pulled from
-// the post-collision buffer.  Box cells outside a closed face get zeros.
 template <int ST>
-__global__ void k_box_moments(Geom g, const typename Codec<ST>::T *__restrict__ src,
-                              const float *__restrict__ utop_in, const DevState *__restrict__ st, BoxGeom box,
-                              BoxArrays ba) {
+__global__ void __launch_bounds__(MB_THREADS) k_box_moments_bin(Geom g, const typename Codec<ST>::T *__restrict__ src,
+                                                                const float *__restrict__ utop_in,
+                                                                const DevState *__restrict__ st, int slot, BoxGeom box,
+                                                                BoxArrays ba, int nmom, int nm,
+                                                                const int *__restrict__ mbase,
+                                                                int *__restrict__ tile_list,
+                                                                int *__restrict__ tile_count, int cap, DevState *stw) {
+    if ((int)blockIdx.x >= nmom) {
+        constexpr int NW = MB_THREADS / 32;
+        const int tile = blockIdx.x - nmom;
+        const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
+        const int t0[3] = {TILE * tx, TILE * ty, TILE * tz};
+        __shared__ int wcount[2][NW];
+        __shared__ int total[2];
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        if (tid < 2) total[tid] = 0;
+        int pb = (tid < nm) ? __ldg(mbase + tid) : 0;
+        __syncthreads();
+        for (int chunk = 0; chunk < nm; chunk += MB_THREADS) {
+            const int k = chunk + tid;
+            const int nxt = (k + MB_THREADS < nm) ? __ldg(mbase + k + MB_THREADS) : 0;  // prefetch
+            bool hit[2] = {false, false};
+            if (k < nm) {
+                const int b[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
+                hit[0] = hit[1] = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const bool lo = b[a] + 3 >= t0[a];
+                    hit[0] = hit[0] && lo && (b[a] <= t0[a] + TILE - 1);  // stencil overlaps the tile
+                    hit[1] = hit[1] && lo && (b[a] <= t0[a] + TILE + 2);  // ... or a stencil based in it
+                }
+            }
+            unsigned bal[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                bal[l] = __ballot_sync(0xffffffffu, hit[l]);
+                if (lane == 0) wcount[l][warp] = __popc(bal[l]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                int off = total[l];
+                for (int w = 0; w < warp; ++w) off += wcount[l][w];
+                if (hit[l]) {
+                    const int pos = off + __popc(bal[l] & ((1u << lane) - 1u));
+                    if (pos < cap) tile_list[((size_t)l * (box.tx * box.ty * box.tz) + tile) * cap + pos] = k;
+                }
+            }
+            __syncthreads();
+            if (tid < 2) {
+                int sum = 0;
+                for (int w = 0; w < NW; ++w) sum += wcount[tid][w];
+                total[tid] += sum;
+            }
+            __syncthreads();
+            pb = nxt;
+        }
+        if (tid < 2) {
+            tile_count[tid * (box.tx * box.ty * box.tz) + tile] = total[tid] < cap ? total[tid] : cap;
+            if (total[tid] > cap) atomicCAS(&stw->status, 0, STAT_OVERFLOW);
+        }
+        return;
+    }
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= box.nbox) return;
     const int bx = (int)(b % box.Bx);
     const int by = (int)((b / box.Bx) % box.By);
     const int bz = (int)(b / ((long long)box.Bx * box.By));
-    int c[3] = {st->box_lo[0] + bx, st->box_lo[1] + by, st->box_lo[2] + bz};
+    int c[3] = {st->s[slot].box_lo[0] + bx, st->s[slot].box_lo[1] + by, st->s[slot].box_lo[2] + bz};
     const int n[3] = {g.nx, g.ny, g.nz};
     const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
     bool inside = true;
@@ -400,10 +533,10 @@ __global__ void k_box_moments(Geom g, const typename Codec<ST>::T *__restrict__ 
         return;
     }
     float q[27];
-    pull27<ST>(g, src, c[0], c[1], c[2], st->ring, utop_in, q);
+    pull27<ST>(g, src, c[0], c[1], c[2], st->s[slot].ring, st->s[slot].reseed, utop_in, q);
     const Macro M = macro_of(moments27(q));
     const float tau = tau_of(g, c[2]);
-    const float k2 = 0.5f / tau - 1.0f;
+    const float k2 = (0.5f / tau - 1.0f) * INV_SCALE;  // P1 = P1~ / 216
     const float p = M.drho * (1.0f / 3.0f);
     ba.u[b] = M.ux;
     ba.u[box.nbox + b] = M.uy;
@@ -419,28 +552,33 @@ __global__ void k_box_moments(Geom g, const typename Codec<ST>::T *__restrict__ 
 // ---------------------------------------------------------------------------
 // Launchers.
 static dim3 cell_grid(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz); }
+static dim3 near_grid(const BoxGeom &b) {
+    const int ex = b.Bx + 2 * NEAR_MARGIN, ey = b.By + 2 * NEAR_MARGIN, ez = b.Bz + 2 * NEAR_MARGIN;
+    return dim3((ex + 31) / 32, (ey + 3) / 4, ez);
+}
 
 template <int ST>
 static cudaError_t collide_t(const Geom &g, const void *src, void *dst, const float *utop_in, float *utop_out,
-                             const DevState *st, const float *hbox, const BoxGeom &box, bool has_box,
-                             cudaStream_t s) {
+                             DevState *st, int slot, int slot_out, const float *hbox, const BoxGeom &box,
+                             bool has_box, int region, cudaStream_t s) {
     using T = typename Codec<ST>::T;
+    const dim3 grid = (region == REGION_NEAR) ? near_grid(box) : cell_grid(g);
     if (has_box)
-        k_collide_stream<ST, true><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in,
-                                                                        utop_out, st, hbox, box);
+        k_collide_stream<ST, true><<<grid, dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st,
+                                                                slot, slot_out, hbox, box, region);
     else
-        k_collide_stream<ST, false><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in,
-                                                                         utop_out, st, hbox, box);
+        k_collide_stream<ST, false><<<grid, dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st,
+                                                                 slot, slot_out, hbox, box, region);
     return cudaGetLastError();
 }
 
 cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
-                                  float *utop_out, const DevState *st, const float *hbox, const BoxGeom &box,
-                                  bool has_box, cudaStream_t s) {
+                                  float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
+                                  const BoxGeom &box, bool has_box, int region, cudaStream_t s) {
     switch (storage) {
-        case ST_F32: return collide_t<ST_F32>(g, src, dst, utop_in, utop_out, st, hbox, box, has_box, s);
-        case ST_F16: return collide_t<ST_F16>(g, src, dst, utop_in, utop_out, st, hbox, box, has_box, s);
-        default: return collide_t<ST_BF16>(g, src, dst, utop_in, utop_out, st, hbox, box, has_box, s);
+        case ST_F32: return collide_t<ST_F32>(g, src, dst, utop_in, utop_out, st, slot, slot_out, hbox, box, has_box, region, s);
+        case ST_F16: return collide_t<ST_F16>(g, src, dst, utop_in, utop_out, st, slot, slot_out, hbox, box, has_box, region, s);
+        default: return collide_t<ST_BF16>(g, src, dst, utop_in, utop_out, st, slot, slot_out, hbox, box, has_box, region, s);
     }
 }
 
@@ -456,32 +594,25 @@ cudaError_t launch_init_equilibrium(const Geom &g, int storage, void *dst, const
 }
 
 cudaError_t launch_macro(const Geom &g, int storage, const void *src, const float *utop_in, const DevState *st,
-                         float *out, bool pops, cudaStream_t s) {
+                         int slot, float *out, bool pops, cudaStream_t s) {
     switch (storage) {
-        case ST_F32: k_macro<ST_F32><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const float *)src, utop_in, st, out, pops); break;
-        case ST_F16: k_macro<ST_F16><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const __half *)src, utop_in, st, out, pops); break;
-        default: k_macro<ST_BF16><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, out, pops); break;
+        case ST_F32: k_macro<ST_F32><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const float *)src, utop_in, st, slot, out, pops); break;
+        case ST_F16: k_macro<ST_F16><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const __half *)src, utop_in, st, slot, out, pops); break;
+        default: k_macro<ST_BF16><<<cell_grid(g), dim3(32, 4), 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, slot, out, pops); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_reseed(const Geom &g, int storage, void *dst, const DevState *st, cudaStream_t s) {
-    const unsigned nb = (unsigned)((g.plane * 27 + 255) / 256);
+cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
+                                   const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
+                                   const int *mbase, int *tile_list, int *tile_count, int cap, DevState *stw,
+                                   cudaStream_t s) {
+    const int nmom = (int)((box.nbox + MB_THREADS - 1) / MB_THREADS);
+    const unsigned nb = (unsigned)(nmom + box.tx * box.ty * box.tz);
     switch (storage) {
-        case ST_F32: k_reseed<ST_F32><<<nb, 256, 0, s>>>(g, (float *)dst, st); break;
-        case ST_F16: k_reseed<ST_F16><<<nb, 256, 0, s>>>(g, (__half *)dst, st); break;
-        default: k_reseed<ST_BF16><<<nb, 256, 0, s>>>(g, (__nv_bfloat16 *)dst, st); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_box_moments(const Geom &g, int storage, const void *src, const float *utop_in,
-                               const DevState *st, const BoxGeom &box, BoxArrays ba, cudaStream_t s) {
-    const unsigned nb = (unsigned)((box.nbox + 127) / 128);
-    switch (storage) {
-        case ST_F32: k_box_moments<ST_F32><<<nb, 128, 0, s>>>(g, (const float *)src, utop_in, st, box, ba); break;
-        case ST_F16: k_box_moments<ST_F16><<<nb, 128, 0, s>>>(g, (const __half *)src, utop_in, st, box, ba); break;
-        default: k_box_moments<ST_BF16><<<nb, 128, 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, box, ba); break;
+        case ST_F32: k_box_moments_bin<ST_F32><<<nb, MB_THREADS, 0, s>>>(g, (const float *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
+        case ST_F16: k_box_moments_bin<ST_F16><<<nb, MB_THREADS, 0, s>>>(g, (const __half *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
+        default: k_box_moments_bin<ST_BF16><<<nb, MB_THREADS, 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
     }
     return cudaGetLastError();
 }

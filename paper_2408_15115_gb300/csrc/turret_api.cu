@@ -2,6 +2,21 @@
 // context creation over caller-owned device workspaces, surface loading with
 // host FP64 mesh properties, and the per-step launch sequence captured as one
 // CUDA graph per ping-pong parity.
+//
+// Step graph (time t -> t+1, parity p = t % 2), when the particle's near
+// region fits the window:
+//
+//   caller stream: --fork--> collide+stream, far cells ------------------> join
+//   side stream  :       \-> collide+stream, near cells -> particle update
+//                           + markers -> support moments + tile lists
+//                           -> interpolation + rows of A -> (h <- h + r0 - A h)
+//                           x (n-1) -> spread h_imm(t+1) ---------------------^
+//   aux stream   :                         \-> F, T (FP64) ---------------^
+//
+// The near region (support box grown by two cells) contains every cell the
+// next support-box pull reads, so the immersed-boundary chain only waits for
+// the small near launch and runs concurrently with the bulk of the window
+// (the side stream has the highest priority).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -21,15 +36,18 @@ struct turret_ctx {
     turret_flags flags;
     int storage;
     double nu, tau0, kappa, g[3];
-    cudaStream_t stream;
+    cudaStream_t stream;  // caller's stream
+    cudaStream_t side;    // internal high-priority stream of the immersed-boundary chain
+    cudaStream_t aux;     // internal stream of the FP64 force/torque reduction
+    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done;
     Geom geom;
     // fluid workspace
     void *f[2];
     float *utop[2];
     DevState *dstate;
-    double *scratch_d;  // lbm_set_fields staging (aliases the idle population buffer)
     // particle
     bool has_particle;
+    bool split;  // near/far collide+stream with the chain on the side stream
     int nm;
     BodyConst body;
     BoxGeom box;
@@ -37,7 +55,6 @@ struct turret_ctx {
     BoxArrays ba;
     int *tile_list, *tile_count;
     int cap;
-    double *partials;
     double vol, area;
     DevState host_state;
     DevState *pinned;  // page-locked staging of the device state for queries
@@ -60,10 +77,16 @@ static turret_status cuda_fail(turret_ctx *c, cudaError_t e, const char *where) 
     return fail(c, TURRET_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(call, where)                                  \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+#define CK(call, where)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where);  \
+    } while (0)
+
+#define CE(call)                                \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return e_;       \
     } while (0)
 
 // Sequential 256-byte-aligned carving of a caller workspace (or size count).
@@ -86,6 +109,7 @@ static bool valid_window(const turret_window *w) {
     if (w->sponge_cells < 0 || w->sponge_cells > w->nz) return false;
     if (w->slide && (w->bc_bottom == TURRET_BC_PERIODIC)) return false;
     if (w->slide && !(w->anchor_frac > 0.0 && w->anchor_frac < 1.0)) return false;
+    if (w->nz > 65535) return false;
     if ((long long)w->nx * w->ny * w->nz > (1LL << 31) / 27) return false;
     return true;
 }
@@ -107,6 +131,20 @@ extern "C" size_t lbm_workspace_bytes(const turret_window *win, turret_storage s
     return cv.off + 256;
 }
 
+static void release(turret_ctx *c) {
+    if (!c) return;
+    for (int k = 0; k < 2; ++k)
+        if (c->graph_ready[k]) cudaGraphExecDestroy(c->graph[k]);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_red) cudaEventDestroy(c->ev_red);
+    if (c->ev_red_done) cudaEventDestroy(c->ev_red_done);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+}
+
 extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, turret_lattice lat, double nu,
                                   double rho_ratio, const double g[3], turret_storage st, void *ws,
                                   size_t ws_bytes, void *stream) {
@@ -125,6 +163,10 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     if (((uintptr_t)ws & 255) != 0) return fail(c, TURRET_EINVAL, "workspace must be 256-byte aligned");
 
     c = new turret_ctx();
+    c->side = c->aux = nullptr;
+    c->ev_fork = c->ev_join = c->ev_red = c->ev_red_done = nullptr;
+    c->pinned = nullptr;
+    c->graph_ready[0] = c->graph_ready[1] = false;
     c->win = *win;
     memset(&c->flags, 0, sizeof c->flags);
     c->flags.ibm_cycles = 4;
@@ -144,34 +186,37 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     G.force_scheme = 0;
     Carver cv{(char *)ws, 0};
     carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate);
-    c->scratch_d = (double *)c->f[1];
     c->has_particle = false;
+    c->split = false;
     c->step = 0;
-    c->graph_ready[0] = c->graph_ready[1] = false;
     if (cudaMallocHost((void **)&c->pinned, sizeof(DevState)) != cudaSuccess) {
         c->pinned = nullptr;  // queries then stage through pageable memory
         cudaGetLastError();
     }
+    int lo_prio = 0, hi_prio = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, hi_prio);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red_done, cudaEventDisableTiming);
     // fluid at rest: all deviations zero, ghost velocity zero, window state reset
-    for (int k = 0; k < 2; ++k) {
-        cudaError_t e = cudaMemsetAsync(c->f[k], 0, 27 * (size_t)G.ncell * storage_bytes(c->storage), c->stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(c->f[k], 0, 27 * (size_t)G.ncell * storage_bytes(c->storage), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->utop[k], 0, 3 * (size_t)G.plane * sizeof(float), c->stream);
-        if (e != cudaSuccess) {
-            cuda_fail(nullptr, e, "lbm_init memset");
-            if (c->pinned) cudaFreeHost(c->pinned);
-            delete c;
-            return TURRET_ECUDA;
-        }
     }
     memset(&c->host_state, 0, sizeof(DevState));
-    for (int i = 0; i < 9; ++i) c->host_state.d[i] = (i % 4 == 0) ? 1.0 : 0.0;
-    c->host_state.reseed_plane = -1;
-    cudaError_t e = cudaMemcpyAsync(c->dstate, &c->host_state, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
+    for (int k = 0; k < 2; ++k) {
+        for (int i = 0; i < 9; ++i) c->host_state.s[k].d[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        c->host_state.s[k].reseed = -1;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->dstate, &c->host_state, sizeof(DevState), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        cuda_fail(nullptr, e, "lbm_init state upload");
-        if (c->pinned) cudaFreeHost(c->pinned);
-        delete c;
+        cuda_fail(nullptr, e, "lbm_init");
+        release(c);
         return TURRET_ECUDA;
     }
     *out = c;
@@ -202,7 +247,7 @@ extern "C" turret_status lbm_set_fields(turret_ctx *c, const double *rho, const 
     if (c->has_particle) return fail(c, TURRET_ESTATE, "fields must be set before ibm_load_surface");
     const size_t n = (size_t)c->geom.ncell;
     const int p = (int)(c->step & 1);
-    double *dr = (double *)c->f[1 - p];  // the idle buffer holds >= 32 bytes per cell
+    double *dr = (double *)c->f[1 - p];  // the idle buffer holds >= 54 bytes per cell
     double *du = dr + n;
     std::vector<double> h(n);
     if (rho) {
@@ -312,7 +357,10 @@ struct IbmLayout {
     int nm, cap, rc;
 };
 
-static bool ibm_layout(const turret_ctx *c, const MeshProps &mp, const double *V, int64_t nv, IbmLayout &L) {
+// Support box: every marker lies within rc = ceil(bounding radius) of C_m,
+// so all 4x4x4 stencils fit a cube of 2 rc + 6 cells placed at floor(C) - rc - 2.
+static bool ibm_layout(const MeshProps &mp, const double *V, int64_t nv, IbmLayout &L) {
+    if (nv <= 0 || nv >= (1 << 24)) return false;
     double rb = 0.0;
     for (int64_t k = 0; k < nv; ++k) {
         double s = 0.0;
@@ -322,12 +370,11 @@ static bool ibm_layout(const turret_ctx *c, const MeshProps &mp, const double *V
     L.rc = (int)ceil(rb + 1e-6);
     const int B = 2 * L.rc + 6;
     L.box.Bx = L.box.By = L.box.Bz = B;
-    L.box.tx = L.box.ty = L.box.tz = (B + 7) / 8;
+    L.box.tx = L.box.ty = L.box.tz = (B + TILE - 1) / TILE;
     L.box.nbox = (long long)B * B * B;
     L.nm = (int)nv;
-    L.cap = (int)nv;
-    (void)c;
-    return nv > 0 && nv < (1 << 24);
+    L.cap = (int)(nv < MAX_CANDIDATES ? nv : MAX_CANDIDATES);
+    return B <= 1024;
 }
 
 static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
@@ -337,26 +384,29 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     m.Xb = (const float *)cv.take(3 * nm * 4);
     m.nb = (const float *)cv.take(3 * nm * 4);
     m.dS = (const float *)cv.take(nm * 4);
-    m.bb = (int *)cv.take(3 * nm * 4);
-    m.wgt = (float *)cv.take(12 * nm * 4);
+    m.rec = (MRec *)cv.take(nm * sizeof(MRec));
+    m.base = (int *)cv.take(nm * 4);
+    m.ft = (float *)cv.take(6 * nm * 4);
     m.U = (float *)cv.take(3 * nm * 4);
     m.n = (float *)cv.take(3 * nm * 4);
     m.arm = (float *)cv.take(3 * nm * 4);
     m.hl = (float *)cv.take(3 * nm * 4);
-    m.ft = (float *)cv.take(6 * nm * 4);
+    m.r0 = (float *)cv.take(3 * nm * 4);
+    m.hb = (float *)cv.take(3 * nm * 4);
+    m.aval = (float *)cv.take(nm * (size_t)ROWCAP * 4);
+    m.aidx = (int *)cv.take(nm * (size_t)ROWCAP * 4);
+    m.alen = (int *)cv.take(nm * 4);
     BoxArrays ba;
     ba.u = (float *)cv.take(3 * nb * 4);
     ba.s = (float *)cv.take(6 * nb * 4);
     ba.h = (float *)cv.take(3 * nb * 4);
-    int *tl = (int *)cv.take(ntiles * (size_t)L.cap * 4);
-    int *tc = (int *)cv.take(ntiles * 4);
-    double *part = (double *)cv.take(REDUCE_BLOCKS * 6 * sizeof(double));
+    int *tl = (int *)cv.take(2 * ntiles * (size_t)L.cap * 4);  // spreading list, rows-of-A list
+    int *tc = (int *)cv.take(2 * ntiles * 4);
     if (c) {
         c->mk = m;
         c->ba = ba;
         c->tile_list = tl;
         c->tile_count = tc;
-        c->partials = part;
     }
     return cv.off + 256;
 }
@@ -367,43 +417,71 @@ extern "C" size_t ibm_workspace_bytes(const turret_ctx *c, const double *V, int6
     MeshProps mp;
     if (!mesh_props(V, nv, T, nt, mp)) return 0;
     IbmLayout L;
-    if (!ibm_layout(c, mp, V, nv, L)) return 0;
+    if (!ibm_layout(mp, V, nv, L)) return 0;
     Carver cv{nullptr, 0};
     return carve_ibm(cv, L, nullptr);
 }
 
-// Events (3) and (4) of Table 1 at time t: markers at the current particle
-// state, u* and sigma on the support box from f(t) = pull(f*(t-1)), surface
-// force and torque, n IBM cycles -> h_imm(t).
-static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float *utop_in) {
-    cudaError_t e;
+// Events (2)-(4) of Table 1.  advance = 1: particle update t -> t+1 from
+// window slot `slot` (markers land in slot^1), then u* and sigma on the
+// support box from f(t+1) = pull(f*(t)) together with the tile candidate
+// lists, the surface force and torque, and n IBM cycles -> h_imm(t+1).
+// advance = 0: the same at the current time level (slot `slot`) without
+// moving the particle (set-up of t = 0).
+static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float *utop_in, int slot, int advance,
+                                    cudaStream_t s) {
     const int nm = c->nm;
-    if ((e = launch_markers(c->geom, c->body, c->box, c->dstate, c->mk, c->stream)) != cudaSuccess) return e;
-    if ((e = launch_box_moments(c->geom, c->storage, fsrc, utop_in, c->dstate, c->box, c->ba, c->stream)) !=
-        cudaSuccess)
-        return e;
-    if ((e = launch_bin(c->box, nm, c->mk.bb, c->tile_list, c->tile_count, c->cap, c->stream)) != cudaSuccess)
-        return e;
-    if ((e = launch_interp(c->box, nm, c->mk, c->ba, 0, c->stream)) != cudaSuccess) return e;
-    if ((e = launch_reduce_ft(nm, c->mk, c->partials, c->dstate, c->stream)) != cudaSuccess) return e;
-    for (int cyc = 1; cyc < c->flags.ibm_cycles; ++cyc) {
-        if ((e = launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->stream)) !=
-            cudaSuccess)
-            return e;
-        if ((e = launch_interp(c->box, nm, c->mk, c->ba, 1, c->stream)) != cudaSuccess) return e;
+    const int so = advance ? (slot ^ 1) : slot;
+    const bool branch = (s == c->side);  // reduce F, T on the aux branch
+    CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, slot, advance, c->mk, s));
+    CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base,
+                              c->tile_list, c->tile_count, c->cap, c->dstate, s));
+    CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, s));
+    if (branch) {
+        CE(cudaEventRecord(c->ev_red, s));
+        CE(cudaStreamWaitEvent(c->aux, c->ev_red, 0));
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, c->aux));
+        CE(cudaEventRecord(c->ev_red_done, c->aux));
+    } else {
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, s));
     }
-    return launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->stream);
+    // cycles 1 .. n-1 read r0, then alternate so that the last one writes hl
+    const int C = c->flags.ibm_cycles - 1;
+    const float *src = c->mk.r0;
+    for (int cyc = 1; cyc <= C; ++cyc) {
+        float *dst = ((C - cyc) % 2 == 0) ? c->mk.hl : c->mk.hb;
+        CE(launch_cycle(nm, c->mk, src, dst, cyc == C, s));
+        src = dst;
+    }
+    CE(launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, s));
+    if (branch) CE(cudaStreamWaitEvent(s, c->ev_red_done, 0));
+    return cudaSuccess;
 }
 
 // One step from parity p: f[p] holds f*(t-1), f[1-p] receives f*(t).
 static cudaError_t enqueue_step(turret_ctx *c, int p) {
-    cudaError_t e = launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p],
-                                          c->dstate, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle,
-                                          c->stream);
-    if (e != cudaSuccess || !c->has_particle) return e;
-    if ((e = launch_particle(c->geom, c->body, c->dstate, c->stream)) != cudaSuccess) return e;
-    if ((e = launch_reseed(c->geom, c->storage, c->f[1 - p], c->dstate, c->stream)) != cudaSuccess) return e;
-    return enqueue_coupling(c, c->f[1 - p], c->utop[p]);
+    const Geom &G = c->geom;
+    if (!c->has_particle)
+        return launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
+                                     1 - p, nullptr, c->box, false, REGION_ALL, c->stream);
+    cudaStream_t chain = c->split ? c->side : c->stream;
+    if (c->split) {
+        CE(cudaEventRecord(c->ev_fork, c->stream));
+        CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
+                                 c->ba.h, c->box, true, REGION_FAR, c->stream));
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
+                                 c->ba.h, c->box, true, REGION_NEAR, c->side));
+    } else {
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
+                                 c->ba.h, c->box, true, REGION_ALL, c->stream));
+    }
+    CE(enqueue_coupling(c, c->f[1 - p], c->utop[p], p, 1, chain));
+    if (c->split) {
+        CE(cudaEventRecord(c->ev_join, c->side));
+        CE(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    }
+    return cudaSuccess;
 }
 
 extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_t nv, const int32_t *T, int64_t nt,
@@ -416,12 +494,15 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     if (!mesh_props(V, nv, T, nt, mp))
         return fail(c, TURRET_EINVAL, "surface is not a closed, outward-oriented triangle mesh");
     IbmLayout L;
-    if (!ibm_layout(c, mp, V, nv, L)) return fail(c, TURRET_EINVAL, "too many markers");
+    if (!ibm_layout(mp, V, nv, L)) return fail(c, TURRET_EINVAL, "too many markers or too large a surface");
     const int n[3] = {c->win.nx, c->win.ny, c->win.nz};
     const bool per[3] = {c->win.bc_x == 0, c->win.bc_y == 0, c->win.bc_bottom == 0};
-    for (int a = 0; a < 3; ++a)
+    bool split = true;
+    for (int a = 0; a < 3; ++a) {
         if (per[a] && L.box.Bx > n[a])
             return fail(c, TURRET_EINVAL, "support box wider than the window along a periodic axis");
+        if (per[a] && L.box.Bx + 2 * NEAR_MARGIN > n[a]) split = false;
+    }
     // every marker stencil must start inside the window along closed axes
     for (int64_t k = 0; k < nv; ++k)
         for (int a = 0; a < 3; ++a) {
@@ -444,11 +525,13 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     c->box = L.box;
     c->vol = mp.vol;
     c->area = mp.area;
+    c->split = split;
     BodyConst &B = c->body;
     B.vol = mp.vol;
     B.kappa = c->kappa;
     B.mass = c->kappa * mp.vol;
-    for (int i = 0; i < 9; ++i) B.Jinv_b[i] = Jinv[i];
+    B.inv_mass = 1.0 / B.mass;
+    for (int i = 0; i < 9; ++i) B.Jinv_b[i] = Jinv[i] * B.inv_mass;
     for (int a = 0; a < 3; ++a) B.g_eff[a] = (c->flags.gravity == 1 ? 1.0 : 1.0 - 1.0 / c->kappa) * c->g[a];
     B.anchor_z = c->win.anchor_frac * c->win.nz;
     B.rot_form = c->flags.rot_form;
@@ -474,12 +557,14 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     // rigid-body state at t: r(t), d = I, v(t-1/2) = v0, w(t-1/2) = w0, L = J w0
     CK(cudaMemcpyAsync(&c->host_state, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state");
     CK(cudaStreamSynchronize(c->stream), "load sync");
-    DevState &S = c->host_state;
+    DevState &D = c->host_state;
+    const int t = (int)(c->step & 1);
+    BodySlot &S = D.s[t];
     for (int a = 0; a < 3; ++a) {
         S.r[a] = r0[a] + (double)S.origin[a];
         S.v[a] = v0[a];
         S.w[a] = w0[a];
-        S.F[a] = S.T[a] = 0.0;
+        D.F[a] = D.T[a] = 0.0;
         S.L[a] = B.mass * (mp.Jm[3 * a] * w0[0] + mp.Jm[3 * a + 1] * w0[1] + mp.Jm[3 * a + 2] * w0[2]);
         const double C = r0[a];
         S.Ci[a] = (int)floor(C);
@@ -488,16 +573,41 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     }
     for (int i = 0; i < 9; ++i) S.d[i] = (i % 4 == 0) ? 1.0 : 0.0;
     S.step = c->step;
-    S.reseed_plane = -1;
-    S.status = 0;
-    S.counter = 0;
-    CK(cudaMemcpyAsync(c->dstate, &S, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "state upload");
+    D.status = 0;
+    D.counter = 0;
+    CK(cudaMemcpyAsync(c->dstate, &D, sizeof(DevState), cudaMemcpyHostToDevice, c->stream), "state upload");
     c->has_particle = true;
     drop_graphs(c);
-    const int t = (int)(c->step & 1);
-    CK(enqueue_coupling(c, c->f[t], c->utop[1 - t]), "initial coupling");
+    CK(enqueue_coupling(c, c->f[t], c->utop[1 - t], t, 0, c->stream), "initial coupling");
     CK(cudaStreamSynchronize(c->stream), "initial coupling sync");
     return TURRET_OK;
+}
+
+// Stream priorities are not part of a captured graph: mark the bulk
+// collide+stream node low and every other kernel node (the immersed-boundary
+// chain on the critical path) high, so the chain's blocks are dispatched
+// first whenever an SM frees up.
+static void set_node_priorities(const turret_ctx *c, cudaGraph_t gr) {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return;
+    size_t n = 0;
+    if (cudaGraphGetNodes(gr, nullptr, &n) != cudaSuccess || n == 0) return;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(gr, nodes.data(), &n) != cudaSuccess) return;
+    const dim3 bulk((c->geom.nx + 31) / 32, (c->geom.ny + 3) / 4, c->geom.nz);
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        const bool is_bulk = kp.gridDim.x == bulk.x && kp.gridDim.y == bulk.y && kp.gridDim.z == bulk.z &&
+                             kp.blockDim.x == 32 && kp.blockDim.y == 4;
+        cudaLaunchAttributeValue v;
+        memset(&v, 0, sizeof v);
+        v.priority = is_bulk ? lo : hi;
+        cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v);
+    }
+    cudaGetLastError();  // priorities are a hint; never fail a step on them
 }
 
 extern "C" turret_status step(turret_ctx *c, int64_t n) {
@@ -512,9 +622,13 @@ extern "C" turret_status step(turret_ctx *c, int64_t n) {
                 CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
                 cudaError_t e = enqueue_step(c, p);
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
-                if (e != cudaSuccess) return cuda_fail(c, e, "capture enqueue");
+                if (e != cudaSuccess) {
+                    if (e2 == cudaSuccess) cudaGraphDestroy(gr);
+                    return cuda_fail(c, e, "capture enqueue");
+                }
                 CK(e2, "end capture");
-                e = cudaGraphInstantiate(&c->graph[p], gr, 0);
+                set_node_priorities(c, gr);
+                e = cudaGraphInstantiateWithFlags(&c->graph[p], gr, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(gr);
                 CK(e, "graph instantiate");
                 c->graph_ready[p] = true;
@@ -533,8 +647,9 @@ extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
     for (int64_t k = 0; k < n; ++k) {
         const int p = (int)(c->step & 1);
-        CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
-                                 c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle, c->stream),
+        CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
+                                 1 - p, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle, REGION_ALL,
+                                 c->stream),
            "fluid step");
         c->step++;
     }
@@ -543,39 +658,42 @@ extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
 
 extern "C" turret_status query_particle_state(turret_ctx *c, turret_particle_state *out) {
     if (!c || !out) return fail(c, TURRET_EINVAL, "NULL argument");
-    DevState S;
-    DevState *dst = c->pinned ? c->pinned : &S;
+    DevState D;
+    DevState *dst = c->pinned ? c->pinned : &D;
     CK(cudaMemcpyAsync(dst, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "query");
     CK(cudaStreamSynchronize(c->stream), "query sync");
-    if (c->pinned) S = *c->pinned;
+    if (c->pinned) D = *c->pinned;
+    const BodySlot &S = D.s[c->step & 1];  // the body at the current time level
     memset(out, 0, sizeof *out);
     for (int a = 0; a < 3; ++a) {
         out->r[a] = S.r[a];
         out->v[a] = S.v[a];
         out->w[a] = S.w[a];
-        out->F[a] = S.F[a];
-        out->T[a] = S.T[a];
+        out->F[a] = D.F[a];
+        out->T[a] = D.T[a];
         out->L[a] = S.L[a];
         out->origin[a] = S.origin[a];
     }
     for (int i = 0; i < 9; ++i) out->d[i] = S.d[i];
     out->step = c->has_particle ? S.step : c->step;
-    out->status = S.status;
+    out->status = D.status;
     out->n_markers = c->has_particle ? c->nm : 0;
     out->volume = c->has_particle ? c->vol : 0.0;
     out->area = c->has_particle ? c->area : 0.0;
-    // enqueue_step: collide+stream, particle, reseed; enqueue_coupling: markers,
-    // box moments, bin, interp, reduce, (spread + interp) per extra cycle, spread
-    out->kernels_per_step = c->has_particle ? 3 + 6 + 2 * (c->flags.ibm_cycles - 1) : 1;
-    if (S.status == STAT_DOMAIN) return fail(c, TURRET_EDOMAIN, "a marker stencil left the window");
-    if (S.status == STAT_DIVERGED) return fail(c, TURRET_EDIVERGED, "non-finite force or torque");
+    // collide+stream (1, or far + near), particle + markers, moments + tile
+    // lists, interpolation + rows of A, F/T reduction, one product per extra
+    // cycle, spread of h_imm
+    out->kernels_per_step = c->has_particle ? (c->split ? 2 : 1) + 5 + (c->flags.ibm_cycles - 1) : 1;
+    if (D.status == STAT_DOMAIN) return fail(c, TURRET_EDOMAIN, "a marker stencil left the window");
+    if (D.status == STAT_DIVERGED) return fail(c, TURRET_EDIVERGED, "non-finite force or torque");
+    if (D.status == STAT_OVERFLOW) return fail(c, TURRET_EOVERFLOW, "a support tile overflowed its marker list");
     return TURRET_OK;
 }
 
 static turret_status copy_fields(turret_ctx *c, float *dev_out, bool pops) {
     if (!c || !dev_out) return fail(c, TURRET_EINVAL, "NULL argument");
     const int p = (int)(c->step & 1);
-    CK(launch_macro(c->geom, c->storage, c->f[p], c->utop[1 - p], c->dstate, dev_out, pops, c->stream), "macro");
+    CK(launch_macro(c->geom, c->storage, c->f[p], c->utop[1 - p], c->dstate, p, dev_out, pops, c->stream), "macro");
     CK(cudaStreamSynchronize(c->stream), "macro sync");
     return TURRET_OK;
 }
@@ -586,9 +704,9 @@ extern "C" turret_status lbm_copy_populations(turret_ctx *c, float *dev_out) { r
 extern "C" turret_status lbm_destroy(turret_ctx *c) {
     if (!c) return TURRET_EINVAL;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    drop_graphs(c);
-    if (c->pinned) cudaFreeHost(c->pinned);
-    delete c;
+    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->aux) cudaStreamSynchronize(c->aux);
+    release(c);
     return TURRET_OK;
 }
 

@@ -3,7 +3,8 @@
 //
 // HBM layout
 //   populations : two buffers (ping-pong) of 27 planes [i][z_phys][y][x], each
-//                 holding deviations q_i = f_i - w_i in the storage type;
+//                 holding scaled deviations s_i = 216 (f_i - w_i) in the
+//                 storage type (see Codec below);
 //                 z_phys = (z_logical + ring) mod nz (ring-buffer window).
 //   utop        : two buffers [3][ny][nx] float, velocity of the top plane at
 //                 the last two collisions (constant-pressure ghost).
@@ -22,24 +23,35 @@ namespace turret {
 
 enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_PRESSURE = 2 };
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
-enum { STAT_OK = 0, STAT_DIVERGED = 5, STAT_DOMAIN = 7 };
+enum { STAT_OK = 0, STAT_DIVERGED = 5, STAT_DOMAIN = 7, STAT_OVERFLOW = 8 };
 
 // Rigid body + window state, FP64 (Sec. 2.3), resident in device memory.
-struct DevState {
+// Everything that changes from one time level to the next lives in two slots
+// indexed by the parity of the time level t.  Slot t%2 holds the body at t
+// (r, d at t; v, w, L at t - 1/2) and the window bookkeeping for pulling f(t)
+// from f*(t-1) and for h_imm(t) (ring offset, support-box origin, entering
+// plane).  The particle update t -> t+1 reads slot t%2 and writes slot
+// (t+1)%2, so collide+stream (reading slot t%2) can run concurrently, and
+// every block of the update may recompute it redundantly without racing.
+struct BodySlot {
     double r[3];       // centre of mass, global coordinates
     double d[9];       // rows d_0, d_1, d_2 of the orientation matrix M
     double v[3], w[3]; // at t - 1/2
     double L[3];       // angular momentum at t - 1/2
-    double F[3], T[3]; // hydrodynamic force / torque at t
     double Cf[3];      // centre in window coordinates minus Ci
     long long origin[3];
     long long step;
     int Ci[3];         // floor of the centre in window coordinates
     int box_lo[3];     // window coordinates of support-box cell (0,0,0), unwrapped
     int ring;          // physical plane of logical z = 0
-    int reseed_plane;  // physical plane to reset to rest (-1: none)
+    int reseed;        // physical plane that entered the ring (reads as rest), -1 none
+};
+
+struct DevState {
+    BodySlot s[2];
+    double F[3], T[3];     // hydrodynamic force / torque at the latest time level
     int status;
-    unsigned int counter;  // last-block ticket of the force reduction
+    unsigned int counter;
 };
 
 // Constant per-context parameters of the fluid window.
@@ -55,14 +67,14 @@ struct Geom {
 
 struct BoxGeom {
     int Bx, By, Bz;
-    int tx, ty, tz;   // tiles of 8^3 along each axis
+    int tx, ty, tz;   // tiles of TILE^3 along each axis
     long long nbox;   // Bx * By * Bz
 };
 
 // Rigid-body constants (body frame) and readings.
 struct BodyConst {
-    double vol, kappa, mass;
-    double Jinv_b[9];  // inverse of J/m in the body frame
+    double vol, kappa, mass, inv_mass;
+    double Jinv_b[9];  // inverse of J/m in the body frame, divided by the mass
     double g_eff[3];
     double anchor_z;   // window z the centre is kept near
     int rot_form, renorm, slide;
@@ -70,17 +82,31 @@ struct BodyConst {
     int rc;            // ceil of the bounding radius of the markers about C_m
 };
 
+// Per-marker record read by the transfer kernels (64 bytes, one per marker):
+// packed stencil base in support-box coordinates (x | y << 10 | z << 20), the
+// 12 one-dimensional Peskin weights (x0..3, y0..3, z0..3) and h_k dS_k.
+struct __align__(16) MRec {
+    int base;
+    float wx[4], wy[4], wz[4];
+    float hdS[3];
+};
+
 struct MarkerArrays {
     const float *Xb;   // [3][nm] body-frame offsets from C_m
     const float *nb;   // [3][nm] body-frame normals
     const float *dS;   // [nm]
-    int *bb;           // [3][nm] stencil base (cell of weight index 0) in box coordinates
-    float *wgt;        // [12][nm] Peskin weights along x (4), y (4), z (4)
+    MRec *rec;         // [nm] stencil records
+    int *base;         // [nm] packed stencil bases (copy of rec[k].base, coalesced for binning)
+    float *ft;         // [6][nm] dS sigma.n and its moment about C_m
     float *U;          // [3][nm] prescribed velocity
     float *n;          // [3][nm] lab-frame normal
     float *arm;        // [3][nm] X_k - C_m
-    float *hl;         // [3][nm] Lagrangian IBM force
-    float *ft;         // [6][nm] dS sigma.n and arm x (dS sigma.n)
+    float *hl;         // [3][nm] Lagrangian IBM force (the last cycle's result)
+    float *r0;         // [3][nm] U_k - I[u*](X_k): the force of step l = 0
+    float *hb;         // [3][nm] second buffer of the cycles
+    float *aval;       // [nm][ROWCAP] A_kj = dS_j sum_x W(x - X_k) W(x - X_j)
+    int *aidx;         // [nm][ROWCAP] column j of each entry, in marker order
+    int *alen;         // [nm] entries per row
 };
 
 struct BoxArrays {
@@ -91,63 +117,87 @@ struct BoxArrays {
 
 // ---------------------------------------------------------------------------
 // D3Q27 index i = ex + 3 ey + 9 ez with e = xi + 1 in {0,1,2}; opposite 26 - i.
-// Tensor-product weights w = w1(x) w1(y) w1(z), w1 = (1/6, 2/3, 1/6).
-__host__ __device__ constexpr float w1f(int e) { return e == 1 ? (2.0f / 3.0f) : (1.0f / 6.0f); }
-__host__ __device__ constexpr float wq(int i) { return w1f(i % 3) * w1f((i / 3) % 3) * w1f(i / 9); }
+// Tensor-product weights w_i = w1(x) w1(y) w1(z), w1 = (1/6, 2/3, 1/6).
+//
+// Populations are carried as scaled deviations s_i = 216 (f_i - w_i).  The
+// scaled weights W_i = 216 w_i = W1(x) W1(y) W1(z), W1 = (1, 4, 1), are the
+// exact integers 1, 4, 16, 64, so every equilibrium is formed without weight
+// rounding and the collision conserves mass and momentum to round-off
+// (float weights 1/216, 1/54, ... would bias the momentum by ~1e-7 per step).
+constexpr float SCALE = 216.0f;
+constexpr float INV_SCALE = 1.0f / 216.0f;
+__host__ __device__ constexpr float W1(int e) { return e == 1 ? 4.0f : 1.0f; }
+__host__ __device__ constexpr float Wq(int i) { return W1(i % 3) * W1((i / 3) % 3) * W1(i / 9); }
 
-// Storage codec for the deviation q_i (FP32 arithmetic in every case).
+// Storage codec for the scaled deviation s_i (FP32 arithmetic in every case).
+//   FP32: s_i as is.
+//   FP16: s_i / W_i * 16 = (f_i - w_i) / w_i * 16, which keeps corner
+//         populations out of subnormals; BF16: s_i / W_i.  All scalings are
+//         exact powers of two or exact integers.
 template <int ST> struct Codec;
 template <> struct Codec<ST_F32> {
     using T = float;
     static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
-    static __device__ __forceinline__ void store(T *p, float q, int) { *p = q; }
+    static __device__ __forceinline__ void store(T *p, float s, int) { *p = s; }
 };
-// FP16: q * 16 / w_i keeps corner populations (w = 1/216) out of subnormals.
 template <> struct Codec<ST_F16> {
     using T = __half;
     static __device__ __forceinline__ float load(const T *p, int i) {
-        return __half2float(__ldg(p)) * (wq(i) * 0.0625f);
+        return __half2float(__ldg(p)) * (Wq(i) * 0.0625f);
     }
-    static __device__ __forceinline__ void store(T *p, float q, int i) {
-        *p = __float2half_rn(q * (16.0f / wq(i)));
+    static __device__ __forceinline__ void store(T *p, float s, int i) {
+        *p = __float2half_rn(s * (16.0f / Wq(i)));
     }
 };
 template <> struct Codec<ST_BF16> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float load(const T *p, int i) {
-        return __bfloat162float(__ldg(p)) * wq(i);
-    }
-    static __device__ __forceinline__ void store(T *p, float q, int i) {
-        *p = __float2bfloat16_rn(q * (1.0f / wq(i)));
-    }
+    static __device__ __forceinline__ float load(const T *p, int i) { return __bfloat162float(__ldg(p)) * Wq(i); }
+    static __device__ __forceinline__ void store(T *p, float s, int i) { *p = __float2bfloat16_rn(s * (1.0f / Wq(i))); }
 };
 
 inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 
 // ---------------------------------------------------------------------------
 // Launchers (lbm_kernels.cu).
+// Collide+stream region: all cells, the cells outside the near region around
+// the particle (support box grown by NEAR_MARGIN), or the near region only.
+enum { REGION_ALL = 0, REGION_FAR = 1, REGION_NEAR = 2 };
+constexpr int NEAR_MARGIN = 2;
+// slot_out >= 0: the kernel also copies the window slot to slot_out (with no
+// entering plane) for a following step that has no particle update.
 cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
-                                  float *utop_out, const DevState *st, const float *hbox, const BoxGeom &box,
-                                  bool has_box, cudaStream_t s);
+                                  float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
+                                  const BoxGeom &box, bool has_box, int region, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const Geom &g, int storage, void *dst, const double *drho, const double *u,
                                     float *utop, cudaStream_t s);
 cudaError_t launch_macro(const Geom &g, int storage, const void *src, const float *utop_in, const DevState *st,
-                         float *out, bool pops, cudaStream_t s);
-cudaError_t launch_reseed(const Geom &g, int storage, void *dst, const DevState *st, cudaStream_t s);
-cudaError_t launch_box_moments(const Geom &g, int storage, const void *src, const float *utop_in,
-                               const DevState *st, const BoxGeom &box, BoxArrays ba, cudaStream_t s);
+                         int slot, float *out, bool pops, cudaStream_t s);
+// Support-box moments (u*, sigma) and the tile candidate lists, one launch.
+cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
+                                   const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
+                                   const int *mbase, int *tile_list, int *tile_count, int cap, DevState *stw,
+                                   cudaStream_t s);
 
 // Launchers (ibm_kernels.cu).
-cudaError_t launch_particle(const Geom &g, const BodyConst &bc, DevState *st, cudaStream_t s);
-cudaError_t launch_markers(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st, MarkerArrays m,
-                           cudaStream_t s);
-cudaError_t launch_bin(const BoxGeom &box, int nm, const int *bb, int *tile_list, int *tile_count, int cap,
-                       cudaStream_t s);
-cudaError_t launch_interp(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, int mode, cudaStream_t s);
-cudaError_t launch_reduce_ft(int nm, MarkerArrays m, double *partials, DevState *st, cudaStream_t s);
+// Rigid-body update t -> t+1 (advance = 1; reads window slot `slot`, writes
+// slot^1) and the marker kinematics for the resulting state, one launch; with
+// advance = 0 only the markers of the current state (window slot `slot`).
+cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st, int slot,
+                                    int advance, MarkerArrays m, cudaStream_t s);
+// l = 0 interpolation of u* and sigma, the surface traction per marker, and
+// the row k of the interaction matrix A (one warp per marker).
+cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
+                           const int *tile_count, int cap, DevState *st, cudaStream_t s);
+// One IBM cycle in matrix form: h_out = h_in + r0 - A h_in (= steps l = 1..4).
+cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, int last, cudaStream_t s);
+// F = sum_k f_k, T = sum_k t_k in FP64, fixed order, into the device state.
+cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, cudaStream_t s);
 cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
                           const int *tile_count, int cap, cudaStream_t s);
 
-constexpr int REDUCE_BLOCKS = 32;
+constexpr int TILE = 4;          // support-box tiles of TILE^3 cells (spreading)
+constexpr int INTERP_WARPS = 8;  // markers per interpolation block
+constexpr int MAX_CANDIDATES = 2048;  // markers listed per support tile
+constexpr int ROWCAP = 512;           // entries per row of A
 
 }  // namespace turret
