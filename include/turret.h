@@ -183,6 +183,26 @@ TURRET_API turret_status lbm_copy_macro(turret_ctx *c, float *dev_out);
  * i = (xi_x+1) + 3 (xi_y+1) + 9 (xi_z+1).  Waits.                           */
 TURRET_API turret_status lbm_copy_populations(turret_ctx *c, float *dev_out);
 
+/* ---- standalone operator ------------------------------------------------------ */
+
+/* Bytes of device workspace ibm_spread needs (0 for invalid sizes).         */
+TURRET_API size_t ibm_spread_workspace_bytes(int32_t nx, int32_t ny, int32_t nz, int64_t n_markers);
+
+/* The spreading step of the immersed-boundary method (Sec. 2.2, step l = 1)
+ * on an nx x ny x nz grid with cell centres at integer coordinates:
+ *   field(x) = sum_k h_k W(x - X_k) dS_k,  W the 3-D Peskin 4-point kernel.
+ * X: device [3][n_markers] floats (all x, then all y, then all z); h: device
+ * [3][n_markers] floats; dS: device [n_markers] floats; field: device
+ * [3][nz][ny][nx] floats, overwritten.  Every marker's 4x4x4 stencil
+ * (floor(X) - 1 .. floor(X) + 2 per axis) must lie inside the grid
+ * (TURRET_EDOMAIN otherwise; such markers contribute nothing).  Grid sides
+ * 4..1023.  workspace: >= ibm_spread_workspace_bytes, 256-byte aligned.
+ * Enqueued on `stream`; waits for it and returns the status.  Bitwise
+ * reproducible (fixed summation order, no atomics).                        */
+TURRET_API turret_status ibm_spread(const float *X, const float *h, const float *dS, int64_t n_markers, int32_t nx,
+                                    int32_t ny, int32_t nz, float *field, void *workspace, size_t workspace_bytes,
+                                    void *stream);
+
 /* Releases the context (not the caller's workspaces).                       */
 TURRET_API turret_status lbm_destroy(turret_ctx *c);
 

@@ -83,6 +83,10 @@ def lib():
         L.lbm_copy_populations.argtypes = [vp, vp]
         L.lbm_destroy.restype = C.c_int
         L.lbm_destroy.argtypes = [vp]
+        L.ibm_spread_workspace_bytes.restype = C.c_size_t
+        L.ibm_spread_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int64]
+        L.ibm_spread.restype = C.c_int
+        L.ibm_spread.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_size_t, vp]
         L.turret_last_error.restype = C.c_char_p
         L.turret_last_error.argtypes = [vp]
         _lib = L
@@ -97,6 +101,28 @@ def _aligned_workspace(torch, nbytes, device):
     buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
     off = (-buf.data_ptr()) % 256
     return buf, buf.data_ptr() + off
+
+
+def ibm_spread(X, h, dS, shape, stream=None):
+    """S[h](x) = sum_k h_k W(x - X_k) dS_k on a (nz, ny, nx) grid (Sec. 2.2, step l = 1).
+
+    X, h: float32 CUDA tensors (3, n); dS: (n,); returns a (3, nz, ny, nx) tensor."""
+    import torch
+    L = lib()
+    nz, ny, nx = shape
+    n = X.shape[1]
+    dev = X.device
+    out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev)
+    nb = L.ibm_spread_workspace_bytes(nx, ny, nz, n)
+    if nb == 0:
+        raise TurretError(1, "invalid spread sizes")
+    ws, ptr = _aligned_workspace(torch, nb, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = L.ibm_spread(C.c_void_p(X.data_ptr()), C.c_void_p(h.data_ptr()), C.c_void_p(dS.data_ptr()), n, nx, ny, nz,
+                      C.c_void_p(out.data_ptr()), C.c_void_p(ptr), C.c_size_t(nb), C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise TurretError(rc, "ibm_spread failed")
+    return out
 
 
 class Turret:
