@@ -260,3 +260,42 @@ def test_pressure_top_ghost_is_rest_equilibrium_for_fluid_at_rest():
     s.fluid_step(5)
     xi, w = O.lattice()
     assert np.abs(s.f() - w).max() < 1e-15
+
+
+def test_pressure_top_keeps_uniform_tangential_flow():
+    # reading of the constant-pressure top (Sec. 2.5): ghost = f0(rho = 1, u of the
+    # top plane).  A uniform tangential flow at rest density is then an exact fixed
+    # point; a ghost at rest (u = 0) or a bounce-back top would shear it.
+    nz, ny, nx = 8, 4, 5
+    u = np.zeros((nz, ny, nx, 3))
+    u[..., 0] = 0.03
+    u[..., 1] = -0.01
+    for top in (2, 1):
+        s = O.Sim(nx, ny, nz, tau=0.7, bc_bottom=0, bc_top=top)
+        s.init_fields(np.ones((nz, ny, nx)), u)
+        s.fluid_step(20)
+        dev = np.abs(s.velocity() - u).max()
+        if top == 2:
+            assert dev < 1e-15
+        else:
+            assert dev > 1e-4
+
+
+def test_sponge_raises_viscosity_towards_the_top():
+    # a shear wave u_x(y) decays faster inside the sponge (tau -> 1 at the top) than
+    # below it; with tau0 = 1 the sponge changes nothing
+    nz, ny, nx = 12, 16, 2
+    y = np.arange(ny)
+    u = np.zeros((nz, ny, nx, 3))
+    u[..., 0] = 1e-3 * np.sin(2 * np.pi * y / ny)[None, :, None]
+    s = O.Sim(nx, ny, nz, tau=0.55, bc_bottom=0, bc_top=2, sponge=6)
+    s.init_fields(np.ones((nz, ny, nx)), u)
+    s.fluid_step(30)
+    amp = np.abs(s.velocity()[..., 0]).max(axis=(1, 2))
+    assert amp[-1] < 0.8 * amp[0]
+    s1 = O.Sim(nx, ny, nz, tau=1.0, bc_bottom=0, bc_top=2, sponge=6)
+    s2 = O.Sim(nx, ny, nz, tau=1.0, bc_bottom=0, bc_top=2, sponge=0)
+    for q in (s1, s2):
+        q.init_fields(np.ones((nz, ny, nx)), u)
+        q.fluid_step(10)
+    assert np.array_equal(s1.velocity(), s2.velocity())
