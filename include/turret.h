@@ -203,6 +203,22 @@ TURRET_API turret_status ibm_spread(const float *X, const float *h, const float 
                                     int32_t ny, int32_t nz, float *field, void *workspace, size_t workspace_bytes,
                                     void *stream);
 
+/* ibm_spread without a workspace, for callers that cannot allocate device
+ * memory (a host framework whose pool owns the device, a plugin given no
+ * allocator, a real-time loop that forbids allocation after start-up).  The
+ * paper has no counterpart; this is a deployment variant of ibm_spread with
+ * the same arguments minus the workspace and the same results.  Scratch comes
+ * from a fixed 8 MiB array in the library's device image, held by every GPU
+ * that loads the library until the process exits; sizes whose
+ * ibm_spread_workspace_bytes exceed it return TURRET_ENOMEM.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make it before any stream capture.  All calls on a device
+ * share the one array: calls whose GPU work overlaps (other streams, other
+ * threads) race and must be serialised by the caller.  Waits for `stream`.  */
+TURRET_API turret_status ibm_spread_noalloc(const float *X, const float *h, const float *dS, int64_t n_markers,
+                                            int32_t nx, int32_t ny, int32_t nz, float *field, void *stream);
+
 /* Releases the context (not the caller's workspaces).                       */
 TURRET_API turret_status lbm_destroy(turret_ctx *c);
 

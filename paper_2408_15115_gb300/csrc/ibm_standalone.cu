@@ -8,6 +8,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/turret.h"
 #include "turret_internal.cuh"
 
@@ -183,3 +185,43 @@ extern "C" turret_status ibm_spread(const float *X, const float *h, const float 
     return run_spread(X, h, dS, n_markers, nx, ny, nz, field, (char *)workspace, L, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------
+// ibm_spread for callers that cannot allocate device memory.
+//
+// Some callers of this library may not call cudaMalloc at all: code that runs
+// under a host framework whose memory pool owns the whole device, plugins that
+// get no allocator from their host, and real-time loops that forbid
+// allocation (and its implicit synchronisation) after start-up.  For them this
+// entry point takes its scratch from a fixed array in the library's device
+// image instead of a caller workspace.  The array is NOALLOC_SCRATCH_BYTES
+// (8 MiB) and is held by every GPU that loads the library until the process
+// exits.  The address of the array is a device address only on the device:
+// host code obtains it once per device with cudaGetSymbolAddress (on the
+// first call made with that device current) and passes it to the kernels.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+extern "C" turret_status ibm_spread_noalloc(const float *X, const float *h, const float *dS, int64_t n_markers,
+                                            int32_t nx, int32_t ny, int32_t nz, float *field, void *stream) {
+    SpreadLayout L;
+    if (!X || !h || !dS || !field || !spread_layout(nx, ny, nz, n_markers, L)) return TURRET_EINVAL;
+    if (L.bytes > NOALLOC_SCRATCH_BYTES) return TURRET_ENOMEM;  // beyond the fixed scratch
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return TURRET_ECUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TURRET_ECUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // run_spread clears the error word first; records, lists and counts are
+    // fully rewritten by every call
+    return run_spread(X, h, dS, n_markers, nx, ny, nz, field, (char *)scratch, L, (cudaStream_t)stream);
+}

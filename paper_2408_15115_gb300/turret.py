@@ -87,6 +87,8 @@ def lib():
         L.ibm_spread_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int64]
         L.ibm_spread.restype = C.c_int
         L.ibm_spread.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_size_t, vp]
+        L.ibm_spread_noalloc.restype = C.c_int
+        L.ibm_spread_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp]
         L.turret_last_error.restype = C.c_char_p
         L.turret_last_error.argtypes = [vp]
         _lib = L
