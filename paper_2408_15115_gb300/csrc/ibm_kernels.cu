@@ -124,12 +124,20 @@ __global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyCon
                         reseed = (ring == 0) ? g.nz - 1 : ring - 1;  // new logical top plane
                     }
                 }
+                const int nn[3] = {g.nx, g.ny, g.nz};
+                const bool pp[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
                 for (int c = 0; c < 3; ++c) {
                     const double C = S.r[c] - (double)S.origin[c];
                     const double fl = floor(C);
                     S.Ci[c] = (int)fl;
                     S.Cf[c] = C - fl;
                     S.box_lo[c] = (int)fl - bc.rc - 2;
+                    int lw = S.box_lo[c];
+                    if (pp[c]) {
+                        lw %= nn[c];
+                        if (lw < 0) lw += nn[c];
+                    }
+                    S.box_lo_w[c] = lw;
                 }
                 S.ring = ring;
                 S.reseed = reseed;

@@ -35,11 +35,10 @@ __device__ __forceinline__ int zphys(int zl, int ring, int nz) {
     return z >= nz ? z - nz : z;
 }
 
-__device__ __forceinline__ float tau_of(const Geom &g, int zl) {
-    if (g.sponge > 0 && zl >= g.nz - g.sponge)
-        return g.tau0 + (1.0f - g.tau0) * (float)(zl - (g.nz - g.sponge) + 1) / (float)g.sponge;
-    return g.tau0;
-}
+// Relaxation time of a logical plane (the sponge raises it linearly to 1 on
+// the top plane); tabulated on the host in double precision.
+__device__ __forceinline__ float tau_of(const Geom &g, int zl) { return __ldg(g.tau_z + zl); }
+__device__ __forceinline__ float omega_of(const Geom &g, int zl) { return __ldg(g.omega_z + zl); }
 
 // Source coordinate along one axis for velocity index e (= xi + 1): returns
 // 0 (s valid, wrapped if periodic) or 1 (bounce-back through a no-slip face).
@@ -183,7 +182,7 @@ __device__ __forceinline__ Macro macro_of(const Mom &m) {
     Macro M;
     M.drho = m.drho * INV_SCALE;
     M.rho = 1.0f + M.drho;
-    const float ir = 1.0f / (SCALE + m.drho);
+    const float ir = __frcp_rn(SCALE + m.drho);
     M.ux = m.jx * ir;
     M.uy = m.jy * ir;
     M.uz = m.jz * ir;
@@ -294,72 +293,76 @@ __device__ __forceinline__ void collide_factored(const Macro &M, float omega, fl
         }
 }
 
-// Wrapped offset of window coordinate c from box origin lo along one axis.
-__device__ __forceinline__ int box_rel(int c, int lo, int n, bool periodic) {
-    int r = c - lo;
-    if (periodic) {
-        r %= n;
-        if (r < 0) r += n;
-    }
+// Offset of window coordinate c from (box origin - margin) along one axis,
+// wrapped into [0, n) along periodic axes (lo_w: the origin already wrapped).
+__device__ __forceinline__ int rel_axis(int c, int lo, int lo_w, int margin, int n, bool periodic) {
+    if (!periodic) return c - lo + margin;
+    int r = c - lo_w + margin;
+    r += (r < 0) ? n : 0;
+    r -= (r >= n) ? n : 0;
     return r;
 }
 
 // ---------------------------------------------------------------------------
-// K1: fused collide + stream.  REGION_ALL: every cell; REGION_FAR: every cell
-// outside the near region (support box grown by NEAR_MARGIN cells);
-// REGION_NEAR: the near region only (grid over its extent).  The far and near
-// launches together cover the window once.
-template <int ST, bool BOX>
+// K1: fused collide + stream.  MODE selects the cells and the forcing:
+//   K1_ALL    every cell, no support box (fluid without particle);
+//   K1_ALLF   every cell, h_imm read on the support box;
+//   K1_FAR    every cell outside the near region (support box grown by
+//             NEAR_MARGIN cells) -- no forcing there;
+//   K1_NEAR   the near region only (grid over its extent), with forcing.
+// FAR and NEAR together cover the window once.
+enum { K1_ALL = 0, K1_ALLF = 1, K1_FAR = 2, K1_NEAR = 3 };
+
+template <int ST, int MODE>
 __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename Codec<ST>::T *__restrict__ src,
                                                         typename Codec<ST>::T *__restrict__ dst,
                                                         const float *__restrict__ utop_in,
                                                         float *__restrict__ utop_out, DevState *st, int slot,
-                                                        int slot_out, const float *__restrict__ hbox, BoxGeom box,
-                                                        int region) {
+                                                        int slot_out, const float *__restrict__ hbox, BoxGeom box) {
     if (slot_out >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
         threadIdx.y == 0) {
         // carry the body and window to the next time level (no entering plane there)
         st->s[slot_out] = st->s[slot];
         st->s[slot_out].reseed = -1;
     }
+    const BodySlot &S = st->s[slot];
     int x, y, zl;
     const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
-    if (region == REGION_NEAR) {
+    if (MODE == K1_NEAR) {
         // grid over the near region; map to window cells, skip cells outside closed faces
         const int rx = blockIdx.x * 32 + threadIdx.x, ry = blockIdx.y * 4 + threadIdx.y, rz = blockIdx.z;
         if (rx >= box.Bx + 2 * NEAR_MARGIN || ry >= box.By + 2 * NEAR_MARGIN) return;
-        x = st->s[slot].box_lo[0] - NEAR_MARGIN + rx;
-        y = st->s[slot].box_lo[1] - NEAR_MARGIN + ry;
-        zl = st->s[slot].box_lo[2] - NEAR_MARGIN + rz;
-        if (perx) { x %= g.nx; if (x < 0) x += g.nx; } else if (x < 0 || x >= g.nx) return;
-        if (pery) { y %= g.ny; if (y < 0) y += g.ny; } else if (y < 0 || y >= g.ny) return;
-        if (perz) { zl %= g.nz; if (zl < 0) zl += g.nz; } else if (zl < 0 || zl >= g.nz) return;
+        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_MARGIN + rx;
+        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_MARGIN + ry;
+        zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_MARGIN + rz;
+        if (perx) { x += (x < 0) ? g.nx : 0; x -= (x >= g.nx) ? g.nx : 0; } else if (x < 0 || x >= g.nx) return;
+        if (pery) { y += (y < 0) ? g.ny : 0; y -= (y >= g.ny) ? g.ny : 0; } else if (y < 0 || y >= g.ny) return;
+        if (perz) { zl += (zl < 0) ? g.nz : 0; zl -= (zl >= g.nz) ? g.nz : 0; } else if (zl < 0 || zl >= g.nz) return;
     } else {
         x = blockIdx.x * 32 + threadIdx.x;
         y = blockIdx.y * 4 + threadIdx.y;
         zl = blockIdx.z;
         if (x >= g.nx || y >= g.ny) return;
-        if (region == REGION_FAR) {
-            const int rx = box_rel(x, st->s[slot].box_lo[0] - NEAR_MARGIN, g.nx, perx);
-            const int ry = box_rel(y, st->s[slot].box_lo[1] - NEAR_MARGIN, g.ny, pery);
-            const int rz = box_rel(zl, st->s[slot].box_lo[2] - NEAR_MARGIN, g.nz, perz);
+        if (MODE == K1_FAR) {
+            const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
+            const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
+            const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
             if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
                 (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN) &&
                 (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN))
                 return;
         }
     }
-    const int ring = st->s[slot].ring;
+    const int ring = S.ring;
     float q[27];
-    pull27<ST>(g, src, x, y, zl, ring, st->s[slot].reseed, utop_in, q);
-    const float tau = tau_of(g, zl);
-    const float omega = 1.0f / tau;
+    pull27<ST>(g, src, x, y, zl, ring, S.reseed, utop_in, q);
+    const float omega = omega_of(g, zl);
     bool forced = false;
     float hx = 0.0f, hy = 0.0f, hz = 0.0f;
-    if (BOX && region != REGION_FAR) {
-        const int rx = box_rel(x, st->s[slot].box_lo[0], g.nx, perx);
-        const int ry = box_rel(y, st->s[slot].box_lo[1], g.ny, pery);
-        const int rz = box_rel(zl, st->s[slot].box_lo[2], g.nz, perz);
+    if (MODE == K1_ALLF || MODE == K1_NEAR) {
+        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], 0, g.nx, perx);
+        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], 0, g.ny, pery);
+        const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], 0, g.nz, perz);
         if ((unsigned)rx < (unsigned)box.Bx && (unsigned)ry < (unsigned)box.By && (unsigned)rz < (unsigned)box.Bz) {
             const size_t b = ((size_t)rz * box.By + ry) * box.Bx + rx;
             hx = __ldg(hbox + b);
@@ -375,7 +378,10 @@ __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename C
         utop_out[g.plane + c] = M.uy;
         utop_out[2 * g.plane + c] = M.uz;
     }
-    collide_factored(M, omega, tau, forced, hx, hy, hz, g.force_scheme, q);
+    if (MODE == K1_ALLF || MODE == K1_NEAR)
+        collide_factored(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
+    else
+        collide_factored(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
     const int own = zphys(zl, ring, g.nz) * (int)g.plane + y * g.nx + x;
     const int ncell = (int)g.ncell;
 #pragma unroll
@@ -562,13 +568,17 @@ static cudaError_t collide_t(const Geom &g, const void *src, void *dst, const fl
                              DevState *st, int slot, int slot_out, const float *hbox, const BoxGeom &box,
                              bool has_box, int region, cudaStream_t s) {
     using T = typename Codec<ST>::T;
-    const dim3 grid = (region == REGION_NEAR) ? near_grid(box) : cell_grid(g);
-    if (has_box)
-        k_collide_stream<ST, true><<<grid, dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st,
-                                                                slot, slot_out, hbox, box, region);
+    const dim3 blk(32, 4);
+    const T *fs = (const T *)src;
+    T *fd = (T *)dst;
+    if (region == REGION_NEAR)
+        k_collide_stream<ST, K1_NEAR><<<near_grid(box), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
+    else if (region == REGION_FAR)
+        k_collide_stream<ST, K1_FAR><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
+    else if (has_box)
+        k_collide_stream<ST, K1_ALLF><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     else
-        k_collide_stream<ST, false><<<grid, dim3(32, 4), 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st,
-                                                                 slot, slot_out, hbox, box, region);
+        k_collide_stream<ST, K1_ALL><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ struct turret_ctx {
     DevState host_state;
     DevState *pinned;  // page-locked staging of the device state for queries
     std::vector<float> staging;
+    std::vector<float> tau_host;  // staging of the per-plane relaxation times
     // stepping
     long long step;
     cudaGraphExec_t graph[2];
@@ -114,11 +115,13 @@ static bool valid_window(const turret_window *w) {
     return true;
 }
 
-static void carve_fluid(Carver &cv, const turret_window *w, int st, void **f, float **utop, DevState **ds) {
+static void carve_fluid(Carver &cv, const turret_window *w, int st, void **f, float **utop, DevState **ds,
+                        float **tau_z) {
     const size_t ncell = (size_t)w->nx * w->ny * w->nz, plane = (size_t)w->nx * w->ny;
     for (int k = 0; k < 2; ++k) f[k] = cv.take(27 * ncell * storage_bytes(st));
     for (int k = 0; k < 2; ++k) utop[k] = (float *)cv.take(3 * plane * sizeof(float));
     *ds = (DevState *)cv.take(sizeof(DevState));
+    *tau_z = (float *)cv.take(2 * (size_t)w->nz * sizeof(float));  // tau, then 1/tau, per plane
 }
 
 extern "C" size_t lbm_workspace_bytes(const turret_window *win, turret_storage st) {
@@ -127,7 +130,8 @@ extern "C" size_t lbm_workspace_bytes(const turret_window *win, turret_storage s
     void *f[2];
     float *u[2];
     DevState *ds;
-    carve_fluid(cv, win, (int)st, f, u, &ds);
+    float *tz;
+    carve_fluid(cv, win, (int)st, f, u, &ds, &tz);
     return cv.off + 256;
 }
 
@@ -185,7 +189,20 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     G.tau0 = (float)tau;
     G.force_scheme = 0;
     Carver cv{(char *)ws, 0};
-    carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate);
+    float *tau_z = nullptr;
+    carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate, &tau_z);
+    // relaxation time per logical plane: tau0, rising linearly to 1 on the top
+    // plane over the sponge (Sec. 2.5), tabulated in double and stored as float
+    c->tau_host.assign(2 * (size_t)win->nz, 0.0f);
+    for (int z = 0; z < win->nz; ++z) {
+        double t = tau;
+        const int L = win->sponge_cells;
+        if (L > 0 && z >= win->nz - L) t = tau + (1.0 - tau) * (double)(z - (win->nz - L) + 1) / (double)L;
+        c->tau_host[z] = (float)t;
+        c->tau_host[win->nz + z] = (float)(1.0 / t);
+    }
+    G.tau_z = tau_z;
+    G.omega_z = tau_z + win->nz;
     c->has_particle = false;
     c->split = false;
     c->step = 0;
@@ -201,6 +218,9 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tau_z, c->tau_host.data(), c->tau_host.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            c->stream);
     // fluid at rest: all deviations zero, ghost velocity zero, window state reset
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaMemsetAsync(c->f[k], 0, 27 * (size_t)G.ncell * storage_bytes(c->storage), c->stream);
@@ -570,6 +590,12 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
         S.Ci[a] = (int)floor(C);
         S.Cf[a] = C - floor(C);
         S.box_lo[a] = S.Ci[a] - L.rc - 2;
+        int lw = S.box_lo[a];
+        if (per[a]) {
+            lw %= n[a];
+            if (lw < 0) lw += n[a];
+        }
+        S.box_lo_w[a] = lw;
     }
     for (int i = 0; i < 9; ++i) S.d[i] = (i % 4 == 0) ? 1.0 : 0.0;
     S.step = c->step;

@@ -43,6 +43,7 @@ struct BodySlot {
     long long step;
     int Ci[3];         // floor of the centre in window coordinates
     int box_lo[3];     // window coordinates of support-box cell (0,0,0), unwrapped
+    int box_lo_w[3];   // the same wrapped into [0, n) along periodic axes
     int ring;          // physical plane of logical z = 0
     int reseed;        // physical plane that entered the ring (reads as rest), -1 none
 };
@@ -63,6 +64,8 @@ struct Geom {
     long long ncell;  // nx * ny * nz  (population stride)
     float tau0;
     int force_scheme;
+    const float *tau_z;    // [nz] relaxation time per logical plane (sponge included)
+    const float *omega_z;  // [nz] 1 / tau per logical plane
 };
 
 struct BoxGeom {
