@@ -219,6 +219,64 @@ TURRET_API turret_status ibm_spread(const float *X, const float *h, const float 
 TURRET_API turret_status ibm_spread_noalloc(const float *X, const float *h, const float *dS, int64_t n_markers,
                                             int32_t nx, int32_t ny, int32_t nz, float *field, void *stream);
 
+/* ---- batched ensemble ------------------------------------------------------ */
+
+/* Many independent settling runs advanced together.  The paper has no
+ * counterpart (it simulates one particle at a time); a batch is a throughput
+ * form of step() over runs of different shapes, windows, viscosities and
+ * storage types.  Each turret_step of a batch launches every phase of the
+ * step (collide+stream, particle + markers, support moments, interpolation,
+ * IBM cycles, spreading, F/T reduction) ONCE for all runs, over a table of
+ * (run, block) pairs, and replays it as one CUDA graph per step parity.  The
+ * per-cell and per-marker arithmetic is the single-run arithmetic, so every
+ * run of a batch evolves bit for bit as it does alone under step().          */
+typedef struct turret_batch turret_batch;
+
+/* Bytes of device workspace a batch of n_runs runs needs (descriptors and
+ * per-phase block tables); 0 for n_runs < 1.                                */
+TURRET_API size_t turret_batch_workspace_bytes(int32_t n_runs);
+
+/* Groups n_runs contexts into a batch.  Every context must hold a particle
+ * (ibm_load_surface done), be at a time level of the same parity and use the
+ * same ibm_cycles; a context appears once.  The contexts stay owned by the
+ * caller and must outlive the batch.  GPU work of the batch is
+ * enqueued on `stream` (the caller's); turret_batch_step orders it after the
+ * work already enqueued on each context's stream and makes each context's
+ * stream wait for it, so query_particle_state on a context sees the batched
+ * steps.  device_workspace: >= turret_batch_workspace_bytes, 256-byte
+ * aligned.  Initial tiles: 128 threads per block, tile width 32, register
+ * budget variant 3 (see turret_batch_set_tiles).                           */
+TURRET_API turret_status turret_batch_init(turret_batch **out, turret_ctx *const *ctxs, int32_t n_runs,
+                                           void *device_workspace, size_t workspace_bytes, void *stream);
+
+/* Collide+stream launch shape of a batch: threads per block (64, 128, 256),
+ * register-budget variant minb (3: <= 80 registers per thread, 4: <= 64, the
+ * number of resident 256-thread blocks per SM the compiler plans for) and per
+ * run the tile width tx[r] in {16, 32, 64, 128} (<= threads; the tile covers
+ * tx cells along x and threads / tx rows along y of one plane).  Results do
+ * not depend on these.  Waits for the batch stream.                        */
+TURRET_API turret_status turret_batch_set_tiles(turret_batch *b, int32_t threads, int32_t minb, const int32_t *tx);
+
+/* Advances every run of the batch by n coupled steps (the order of step()).
+ * Runs may be stepped alone between calls; every run must then still be at a
+ * time level of the same parity (TURRET_ESTATE otherwise).                  */
+TURRET_API turret_status turret_batch_step(turret_batch *b, int64_t n);
+
+/* Releases the batch (not the contexts or the workspace); waits for it.     */
+TURRET_API turret_status turret_batch_destroy(turret_batch *b);
+
+/* Message of the last failure on this batch (or of the last failed
+ * turret_batch_init when b is NULL).                                        */
+TURRET_API const char *turret_batch_last_error(const turret_batch *b);
+
+/* Times `reps` launches of the collide+stream kernel of one context with the
+ * given launch shape (as turret_batch_set_tiles), from the current time level
+ * into the idle population buffer, so the context's state is unchanged; the
+ * mean duration in microseconds goes to *us_out.  Used by the tile
+ * autotuner.  Waits for the context's stream.                               */
+TURRET_API turret_status turret_time_collide(turret_ctx *c, int32_t threads, int32_t tx, int32_t minb, int32_t reps,
+                                             float *us_out);
+
 /* Releases the context (not the caller's workspaces).                       */
 TURRET_API turret_status lbm_destroy(turret_ctx *c);
 

@@ -44,8 +44,8 @@ constexpr int PM_THREADS = 128;
 // warp 0 -- identical inputs, identical FP64 results -- and block 0 stores it
 // in the other slot, so the marker work spreads over many SMs with no
 // grid-wide wait.
-__global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyConst bc, BoxGeom box, DevState *st,
-                                                                  int slot, int advance, MarkerArrays m) {
+__device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st,
+                                         int slot, int advance, const MarkerArrays &m, int blk) {
     __shared__ BodySlot S;  // the body at the markers' time level
     __shared__ double s_F[3], s_T[3], s_src[3], s_sb[3], s_wb[3], s_mid[9], s_dn[9];
     __shared__ float f_d[9], f_v[3], f_w[3], f_cf[3];
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyCon
                 S.step += 1;
             }
             __syncwarp();
-            if (blockIdx.x == 0) {
+            if (blk == 0) {
                 int *gdst = reinterpret_cast<int *>(&st->s[so]);
                 const int *ssrc = reinterpret_cast<const int *>(&S);
                 for (int q = lane; q < (int)(sizeof(BodySlot) / 4); q += 32) gdst[q] = ssrc[q];
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyCon
     const int n[3] = {g.nx, g.ny, g.nz};
     const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
     const int B[3] = {box.Bx, box.By, box.Bz};
-    const int k = blockIdx.x * PM_THREADS + tid;
+    const int k = blk * PM_THREADS + tid;
     if (k >= nm) return;
     bool bad = false;
     const float xb[3] = {m.Xb[k], m.Xb[nm + k], m.Xb[2 * nm + k]};
@@ -213,6 +213,11 @@ __global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyCon
     if (bad) atomicCAS(&st->status, 0, STAT_DOMAIN);  // the first latched error wins
 }
 
+__global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyConst bc, BoxGeom box, DevState *st,
+                                                                  int slot, int advance, MarkerArrays m) {
+    pm_block(g, bc, box, st, slot, advance, m, blockIdx.x);
+}
+
 __device__ __forceinline__ float pick4(const float w[4], int i) {
     return i == 0 ? w[0] : (i == 1 ? w[1] : (i == 2 ? w[2] : w[3]));
 }
@@ -243,12 +248,10 @@ __device__ __forceinline__ float overlap4(const float wk[4], const float wj[4], 
 constexpr int ROWS_THREADS = 256;
 constexpr int ROWS_WARPS = ROWS_THREADS / 32;
 
-__global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
-                                                                const int *__restrict__ wlist,
-                                                                const int *__restrict__ wcount, int cap,
-                                                                DevState *st) {
+__device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const MarkerArrays &m, const BoxArrays &ba,
+                                              const int *__restrict__ wlist, const int *__restrict__ wcount,
+                                              int cap, DevState *st, int k) {
     __shared__ int wc[ROWS_WARPS];
-    const int k = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MRec rk = m.rec[k];
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
@@ -339,14 +342,21 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int 
     }
 }
 
+__global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
+                                                                const int *__restrict__ wlist,
+                                                                const int *__restrict__ wcount, int cap,
+                                                                DevState *st) {
+    interp0_block(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x);
+}
+
 // One cycle of steps l = 1..4 (Sec. 2.2) in matrix form:
 //   h_out_k = h_in_k + U_k - I[u* + S h_in](X_k) = h_in_k + r0_k - sum_j A_kj h_in_j.
 // One warp per marker, entries of the row in order per lane, xor-shuffle sum.
 // The last cycle also stores h dS for the spreading of h_imm.
-__global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArrays m, const float *__restrict__ h_in,
-                                                             float *__restrict__ h_out, int last) {
+__device__ __forceinline__ void cycle_block(int nm, const MarkerArrays &m, const float *__restrict__ h_in,
+                                            float *__restrict__ h_out, int last, int blk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.x * INTERP_WARPS + warp;
+    const int k = blk * INTERP_WARPS + warp;
     if (k >= nm) return;
     const int len = m.alen[k];
     const float *arow = m.aval + (size_t)k * ROWCAP;
@@ -376,9 +386,14 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArray
     }
 }
 
+__global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArrays m, const float *__restrict__ h_in,
+                                                             float *__restrict__ h_out, int last) {
+    cycle_block(nm, m, h_in, h_out, last, blockIdx.x);
+}
+
 // F = sum_k dS sigma.n, T = sum_k arm x (dS sigma.n) in FP64: warp c sums
 // component c, lane l the markers l, l+32, ... in order, then an xor tree.
-__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st) {
+__device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ ft, DevState *st) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double a = 0.0;
     for (int k = lane; k < nm; k += 32) a += (double)ft[c * nm + k];
@@ -390,6 +405,10 @@ __global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restri
     }
 }
 
+__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st) {
+    reduce_block(nm, ft, st);
+}
+
 constexpr int SPREAD_SLICES = 8;                               // candidate slices per tile
 constexpr int SPREAD_THREADS = TILE * TILE * TILE * SPREAD_SLICES;  // 64 cells x 8 slices
 constexpr int SPREAD_STAGE = 256;
@@ -398,15 +417,14 @@ constexpr int SPREAD_STAGE = 256;
 // per 4^3 tile: the tile's candidate records are staged in shared memory as
 // structure of arrays; thread (cell c, slice q) sums slice q of each staged
 // chunk for cell c; the 8 slice sums are added in slice order (reproducible).
-__global__ void __launch_bounds__(SPREAD_THREADS) k_spread(BoxGeom box, const MRec *__restrict__ rec, BoxArrays ba,
-                                                           const int *__restrict__ tile_list,
-                                                           const int *__restrict__ tile_count, int cap) {
+__device__ __forceinline__ void spread_block(const BoxGeom &box, const MRec *__restrict__ rec, const BoxArrays &ba,
+                                             const int *__restrict__ tile_list, const int *__restrict__ tile_count,
+                                             int cap, int tile) {
     constexpr int TC = TILE * TILE * TILE;
     __shared__ int sbase[SPREAD_STAGE];
     __shared__ float sw[12][SPREAD_STAGE];
     __shared__ float sh[3][SPREAD_STAGE];
     __shared__ float part[SPREAD_SLICES][3][TC];
-    const int tile = blockIdx.x;
     const int cnt = tile_count[tile];
     const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
     const int tid = threadIdx.x, c = tid % TC, q = tid / TC;
@@ -463,6 +481,67 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(BoxGeom box, const MR
     }
 }
 
+__global__ void __launch_bounds__(SPREAD_THREADS) k_spread(BoxGeom box, const MRec *__restrict__ rec, BoxArrays ba,
+                                                           const int *__restrict__ tile_list,
+                                                           const int *__restrict__ tile_count, int cap) {
+    spread_block(box, rec, ba, tile_list, tile_count, cap, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch per phase over all runs of a batch, block b of
+// the launch serving block b - prefix[r] of run r (prefix[r] <= b <
+// prefix[r + 1]), with the same block code as the single-run kernels.
+__device__ __forceinline__ int run_of(const int *__restrict__ prefix, int nruns, int b, int &local) {
+    int lo = 0, hi = nruns;  // largest r with prefix[r] <= b
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid;
+    }
+    local = b - __ldg(prefix + lo);
+    return lo;
+}
+
+__global__ void __launch_bounds__(PM_THREADS) k_batch_particle_markers(const RunDesc *__restrict__ runs,
+                                                                        const int *__restrict__ prefix, int nruns,
+                                                                        int p) {
+    int lb;
+    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    pm_block(R.g, R.bc, R.box, R.st, p, 1, R.m, lb);
+}
+
+__global__ void __launch_bounds__(ROWS_THREADS) k_batch_interp0_rows(const RunDesc *__restrict__ runs,
+                                                                     const int *__restrict__ prefix, int nruns) {
+    int lb;
+    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    const int ntiles = R.box.tx * R.box.ty * R.box.tz;  // list 1 (rows of A) follows list 0
+    interp0_block(R.box, R.nm, R.m, R.ba, R.tile_list + (size_t)ntiles * R.cap, R.tile_count + ntiles, R.cap, R.st,
+                  lb);
+}
+
+__device__ __forceinline__ float *hsel(const MarkerArrays &m, int sel) {
+    return sel == HSEL_R0 ? m.r0 : (sel == HSEL_HL ? m.hl : m.hb);
+}
+
+__global__ void __launch_bounds__(32 * INTERP_WARPS) k_batch_cycle(const RunDesc *__restrict__ runs,
+                                                                   const int *__restrict__ prefix, int nruns,
+                                                                   int sel_in, int sel_out, int last) {
+    int lb;
+    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    cycle_block(R.nm, R.m, hsel(R.m, sel_in), hsel(R.m, sel_out), last, lb);
+}
+
+__global__ void __launch_bounds__(192) k_batch_reduce_ft(const RunDesc *__restrict__ runs) {
+    const RunDesc &R = runs[blockIdx.x];
+    reduce_block(R.nm, R.m.ft, R.st);
+}
+
+__global__ void __launch_bounds__(SPREAD_THREADS) k_batch_spread(const RunDesc *__restrict__ runs,
+                                                                 const int *__restrict__ prefix, int nruns) {
+    int lb;
+    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    spread_block(R.box, R.m.rec, R.ba, R.tile_list, R.tile_count, R.cap, lb);
+}
+
 // ---------------------------------------------------------------------------
 cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const BoxGeom &box, DevState *st, int slot,
                                     int advance, MarkerArrays m, cudaStream_t s) {
@@ -492,6 +571,38 @@ cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays 
                           const int *tile_count, int cap, cudaStream_t s) {
     (void)nm;
     k_spread<<<box.tx * box.ty * box.tz, SPREAD_THREADS, 0, s>>>(box, m.rec, ba, tile_list, tile_count, cap);
+    return cudaGetLastError();
+}
+
+int blocks_particle_markers(const RunDesc &r) { return (r.nm + PM_THREADS - 1) / PM_THREADS; }
+int blocks_interp0(const RunDesc &r) { return r.nm; }
+int blocks_cycle(const RunDesc &r) { return (r.nm + INTERP_WARPS - 1) / INTERP_WARPS; }
+int blocks_spread(const RunDesc &r) { return r.box.tx * r.box.ty * r.box.tz; }
+
+cudaError_t launch_batch_particle_markers(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                          cudaStream_t s) {
+    k_batch_particle_markers<<<nblocks, PM_THREADS, 0, s>>>(runs, prefix, nruns, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s) {
+    k_batch_interp0_rows<<<nblocks, ROWS_THREADS, 0, s>>>(runs, prefix, nruns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_cycle(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int sel_in,
+                               int sel_out, int last, cudaStream_t s) {
+    k_batch_cycle<<<nblocks, 32 * INTERP_WARPS, 0, s>>>(runs, prefix, nruns, sel_in, sel_out, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, cudaStream_t s) {
+    k_batch_reduce_ft<<<nruns, 192, 0, s>>>(runs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_spread(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s) {
+    k_batch_spread<<<nblocks, SPREAD_THREADS, 0, s>>>(runs, prefix, nruns);
     return cudaGetLastError();
 }
 

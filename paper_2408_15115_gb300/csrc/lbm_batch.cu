@@ -1,0 +1,187 @@
+// lbm_batch.cu -- collide+stream with a chosen tile (the autotuner's timing
+// kernel) and the batched collide+stream and support-moment launches over
+// the (run, block) table of many independent runs.
+#include "lbm_cell.cuh"
+
+namespace turret {
+
+// Register budget variants of the collide+stream launches, chosen by the
+// autotuner with the tile: MINB resident 256-thread blocks per SM, i.e. at most
+// 64 registers per thread for MINB = 4 (some spilling of the batched kernel's
+// descriptor values) and 80 for MINB = 3 (no spilling, fewer resident warps).
+// K1 over one window with a chosen tile (the autotuner's timing kernel): the
+// same cells and arithmetic as k_collide_stream, no window-slot carry.
+template <int ST, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_collide_tiled(Geom g, const typename Codec<ST>::T *__restrict__ src,
+                                                       typename Codec<ST>::T *__restrict__ dst,
+                                                       const float *__restrict__ utop_in,
+                                                       float *__restrict__ utop_out, const DevState *st, int slot,
+                                                       const float *__restrict__ hbox, BoxGeom box, int tx) {
+    int cx, cy, cz;
+    tile_coords(blockIdx.x, tx, g.nx, g.ny, cx, cy, cz);
+    k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, cx, cy, cz);
+}
+
+// ---------------------------------------------------------------------------
+// Batched K1: one launch over the (run, tile) table of many independent runs.
+// Block b belongs to the run r with prefix[r] <= b < prefix[r + 1]; every run
+// keeps its own storage type, window, boundary conditions, relaxation times
+// and tile, read from its descriptor.  PHASE_BULK: the far cells of runs that
+// split (no blocks for the others); PHASE_NEAR: the near region of runs that
+// split, the whole window (with forcing) of runs that do not.
+template <int PHASE, int ST>
+__device__ __forceinline__ void batch_k1_run(const RunDesc &R, int p, int lb) {
+    using T = typename Codec<ST>::T;
+    const Geom g = R.g;
+    const BoxGeom box = R.box;
+    const T *src = (const T *)R.f[p];
+    T *dst = (T *)R.f[1 - p];
+    const BodySlot &S = R.st->s[p];
+    int cx, cy, cz;
+    if (PHASE == PHASE_BULK) {
+        tile_coords(lb, R.tx, g.nx, g.ny, cx, cy, cz);
+        k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+    } else if (R.split) {
+        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_MARGIN, box.By + 2 * NEAR_MARGIN, cx, cy, cz);
+        k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+    } else {
+        tile_coords(lb, R.tx, g.nx, g.ny, cx, cy, cz);
+        k1_cell<ST, K1_ALLF>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+    }
+}
+
+// The near phase is a small launch on the critical path (no register cap).
+template <int PHASE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_batch_collide(const RunDesc *__restrict__ runs,
+                                                       const int *__restrict__ prefix, int nruns, int p) {
+    // the run's descriptor is staged in shared memory: its fields are then
+    // operands read on use rather than registers held through the cell
+    __shared__ RunDesc R;
+    __shared__ int s_lb;
+    if (threadIdx.x < 32) {
+        int lb;
+        const int r = find_run(prefix, nruns, blockIdx.x, lb);
+        const int *gsrc = reinterpret_cast<const int *>(runs + r);
+        int *sdst = reinterpret_cast<int *>(&R);
+        for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 4); q += 32) sdst[q] = __ldg(gsrc + q);
+        if (threadIdx.x == 0) s_lb = lb;
+    }
+    __syncthreads();
+    const int lb = s_lb;
+    switch (R.storage) {
+        case ST_F32: batch_k1_run<PHASE, ST_F32>(R, p, lb); break;
+        case ST_F16: batch_k1_run<PHASE, ST_F16>(R, p, lb); break;
+        default: batch_k1_run<PHASE, ST_BF16>(R, p, lb); break;
+    }
+}
+
+
+// Batched K2 + binning: per run nmom(r) moment blocks then its tiles, on
+// f(t+1) in buffer 1 - p and window slot 1 - p (the advanced body).
+__global__ void __launch_bounds__(MB_THREADS) k_batch_box_moments_bin(const RunDesc *__restrict__ runs,
+                                                                      const int *__restrict__ prefix, int nruns,
+                                                                      int p) {
+    int lb;
+    const int r = find_run(prefix, nruns, blockIdx.x, lb);
+    const RunDesc &R = runs[r];
+    const Geom g = R.g;
+    const BoxGeom box = R.box;
+    const int nmom = (int)((box.nbox + MB_THREADS - 1) / MB_THREADS);
+    const int so = 1 - p;
+    switch (R.storage) {
+        case ST_F32:
+            mb_block<ST_F32>(g, (const float *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base,
+                             R.tile_list, R.tile_count, R.cap, R.st, lb);
+            break;
+        case ST_F16:
+            mb_block<ST_F16>(g, (const __half *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base,
+                             R.tile_list, R.tile_count, R.cap, R.st, lb);
+            break;
+        default:
+            mb_block<ST_BF16>(g, (const __nv_bfloat16 *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm,
+                              R.m.base, R.tile_list, R.tile_count, R.cap, R.st, lb);
+            break;
+    }
+}
+
+template <int ST, int MINB>
+static cudaError_t tiled_t(const Geom &g, const void *src, void *dst, const float *utop_in, float *utop_out,
+                           const DevState *st, int slot, const float *hbox, const BoxGeom &box, bool has_box,
+                           int threads, int tx, cudaStream_t s) {
+    using T = typename Codec<ST>::T;
+    const int ty = threads / tx;
+    const unsigned nb = (unsigned)(((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty) * g.nz);
+    if (has_box)
+        k_collide_tiled<ST, K1_ALLF, MINB><<<nb, threads, 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st, slot, hbox, box, tx);
+    else
+        k_collide_tiled<ST, K1_ALL, MINB><<<nb, threads, 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st, slot, hbox, box, tx);
+    return cudaGetLastError();
+}
+
+template <int MINB>
+static cudaError_t tiled_m(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
+                           float *utop_out, const DevState *st, int slot, const float *hbox, const BoxGeom &box,
+                           bool has_box, int threads, int tx, cudaStream_t s) {
+    switch (storage) {
+        case ST_F32: return tiled_t<ST_F32, MINB>(g, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+        case ST_F16: return tiled_t<ST_F16, MINB>(g, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+        default: return tiled_t<ST_BF16, MINB>(g, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+    }
+}
+
+bool valid_tile(int threads, int tx, int minb) {
+    return (threads == 64 || threads == 128 || threads == 256) && (tx == 16 || tx == 32 || tx == 64 || tx == 128) &&
+           tx <= threads && (minb == 3 || minb == 4);
+}
+
+cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
+                                 float *utop_out, const DevState *st, int slot, const float *hbox,
+                                 const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s) {
+    if (!valid_tile(threads, tx, minb)) return cudaErrorInvalidValue;
+    if (minb == 3) return tiled_m<3>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+    return tiled_m<4>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+}
+
+static int tile_blocks(int ex, int ey, int ez, int threads, int tx) {
+    const int ty = threads / tx;
+    return ((ex + tx - 1) / tx) * ((ey + ty - 1) / ty) * ez;
+}
+
+int blocks_bulk(const RunDesc &r, int threads) {
+    return r.split ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx) : 0;
+}
+
+int blocks_near(const RunDesc &r, int threads) {
+    if (!r.split) return tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx);
+    return tile_blocks(r.box.Bx + 2 * NEAR_MARGIN, r.box.By + 2 * NEAR_MARGIN, r.box.Bz + 2 * NEAR_MARGIN, threads,
+                       r.tx);
+}
+
+int blocks_box_moments_bin(const RunDesc &r) {
+    return (int)((r.box.nbox + MB_THREADS - 1) / MB_THREADS) + r.box.tx * r.box.ty * r.box.tz;
+}
+
+cudaError_t launch_batch_collide(int phase, const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                 int threads, int minb, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (phase == PHASE_NEAR)
+        k_batch_collide<PHASE_NEAR, 1><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+    else if (minb == 3)
+        k_batch_collide<PHASE_BULK, 3><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+    else
+        k_batch_collide<PHASE_BULK, 4><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+    return cudaGetLastError();
+}
+
+bool is_batch_bulk_kernel(const void *fn) {
+    return fn == (const void *)k_batch_collide<PHASE_BULK, 3> || fn == (const void *)k_batch_collide<PHASE_BULK, 4>;
+}
+
+cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                         cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_batch_box_moments_bin<<<nblocks, MB_THREADS, 0, s>>>(runs, prefix, nruns, p);
+    return cudaGetLastError();
+}
+
+}  // namespace turret

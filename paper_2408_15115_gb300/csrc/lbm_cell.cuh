@@ -1,0 +1,530 @@
+// lbm_cell.cuh -- per-cell device code of the fused recursive-regularized
+// D3Q27 collide+stream (pull) and of the passes that share its streaming and
+// moment code; included by the single-run and the batched kernels, which thus
+// run identical arithmetic.
+//
+// Method (Sec. 2.1 and Appendix A of arXiv 2408.15115): the post-collision
+// populations are f* = f0(rho, u) + (1 - 1/tau) f1 (Eq. 7), with f0 the
+// Hermite equilibrium carrying every D3Q27-supported term up to H6_xxyyzz and
+// f1 the off-equilibrium part rebuilt from P1 = sum xi xi (f - f0) through the
+// recursive coefficients a1^(n) (Eq. A.3).  Forcing follows the equilibrium
+// velocity shift of Eq. 15 (reading: regularized BGK form, see turret.h).
+//
+// GB300 formulation (not the paper's): both f0 and f1 live in the 27-term
+// tensor-product Hermite basis H_p(xi_x) H_q(xi_y) H_r(xi_z), p,q,r <= 2,
+// which is orthogonal under the D3Q27 weights.  The equilibrium coefficients
+// are the monomials rho u_x^p u_y^q u_z^r and the recursive coefficients are
+// a1_pqr = 1/2 sum_ab P1_ab d^2(u^p u^q u^r)/du_a du_b (the closed form of
+// the recursion: a sum over index pairs), so every term is an outer product
+// of one 3-vector per axis and a collision is
+//   moments : 3 separable passes of 3-point sums over x, y, z (10 moments)
+//   rebuild : per-axis factors X, X', X'' and 9 (y,z) pair terms, then
+//             3 FMAs per population (collide_factored below)
+// about 300 FP32 flops per cell.  Populations are stored as deviations
+// q_i = f_i - w_i (FP32) or q_i / w_i scaled (FP16/BF16); the moments use
+// drho = sum q, so no O(1) term cancels in single precision.
+//
+// Memory: SoA planes [27][z][y][x], one thread per cell, x fastest; each warp
+// reads 27 coalesced 128-byte rows (the +-1 x-shifts hit the same sectors in
+// L1/L2) and writes 27 aligned rows.  216 B/cell of HBM traffic in FP32.  The
+#pragma once
+#include "turret_internal.cuh"
+
+namespace turret {
+
+__device__ __forceinline__ int zphys(int zl, int ring, int nz) {
+    int z = zl + ring;
+    return z >= nz ? z - nz : z;
+}
+
+// Relaxation time of a logical plane (the sponge raises it linearly to 1 on
+// the top plane); tabulated on the host in double precision.
+__device__ __forceinline__ float tau_of(const Geom &g, int zl) { return __ldg(g.tau_z + zl); }
+__device__ __forceinline__ float omega_of(const Geom &g, int zl) { return __ldg(g.omega_z + zl); }
+
+// Source coordinate along one axis for velocity index e (= xi + 1): returns
+// 0 (s valid, wrapped if periodic) or 1 (bounce-back through a no-slip face).
+__device__ __forceinline__ int src_axis(int c, int e, int n, int bc, int &s) {
+    s = c - (e - 1);
+    if (s < 0) {
+        if (bc == BC_PERIODIC) { s += n; return 0; }
+        return 1;
+    }
+    if (s >= n) {
+        if (bc == BC_PERIODIC) { s -= n; return 0; }
+        return 1;
+    }
+    return 0;
+}
+
+// Deviation of the rest-density equilibrium f0_i(1, u) - w_i from the
+// product form prod_a w1 [1 + 3 xi u + 9/2 (xi^2 - 1/3) u^2] (equal to the
+// appendix equilibrium on D3Q27), expanded so the leading 1 cancels exactly.
+__device__ __forceinline__ float eqfac_m1(int e, float u) {
+    return e == 1 ? -1.5f * u * u : (e == 2 ? (3.0f * u + 3.0f * u * u) : (-3.0f * u + 3.0f * u * u));
+}
+__device__ __forceinline__ float ghost_dev(int i, float ux, float uy, float uz) {
+    float a = eqfac_m1(i % 3, ux), b = eqfac_m1((i / 3) % 3, uy), c = eqfac_m1(i / 9, uz);
+    return Wq(i) * (a + b + c + a * b + a * c + b * c + a * b * c);  // scaled deviation
+}
+
+// Pull the 27 pre-collision scaled deviations of cell (x, y, zl) from the
+// post-collision buffer: f_i(x) = f*_i(x - xi_i); no-slip faces bounce back
+// (halfway), the pressure top reads the ghost equilibrium, periodic faces wrap.
+// A source on the plane that just entered the sliding window (reseed >= 0)
+// holds stale data and reads as the rest equilibrium (deviation 0).
+template <int ST>
+__device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::T *__restrict__ f, int x, int y,
+                                       int zl, int ring, int reseed, const float *__restrict__ utop, float q[27]) {
+    int sx[3], sy[3], szp[3], bxf[3], byf[3], bzf[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        bxf[e] = src_axis(x, e, g.nx, g.bc_x, sx[e]);
+        byf[e] = src_axis(y, e, g.ny, g.bc_y, sy[e]);
+        int zs = zl - (e - 1);
+        bzf[e] = 0;
+        if (zs < 0) {
+            if (g.bc_bottom == BC_PERIODIC) zs += g.nz; else bzf[e] = 1;
+        } else if (zs >= g.nz) {
+            if (g.bc_top == BC_PERIODIC) zs -= g.nz;
+            else bzf[e] = (g.bc_top == BC_PRESSURE) ? 2 : 1;
+        }
+        szp[e] = bzf[e] ? 0 : zphys(zs, ring, g.nz);
+        if (bzf[e] == 0 && szp[e] == reseed) bzf[e] = 3;
+    }
+    const int nx = g.nx, plane = (int)g.plane, ncell = (int)g.ncell;
+    if ((bxf[0] | bxf[2] | byf[0] | byf[2] | bzf[0] | bzf[1] | bzf[2]) == 0) {
+        // interior (or periodic) cell: 27 plain loads, 32-bit offsets
+#pragma unroll
+        for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+            for (int ey = 0; ey < 3; ++ey) {
+                const int row = szp[ez] * plane + sy[ey] * nx;
+#pragma unroll
+                for (int ex = 0; ex < 3; ++ex) {
+                    const int i = ex + 3 * ey + 9 * ez;
+                    q[i] = Codec<ST>::load(f + i * ncell + row + sx[ex], i);
+                }
+            }
+        return;
+    }
+    const int zo = zphys(zl, ring, g.nz);
+    const int own = zo * plane + y * nx + x;
+    const bool own_rest = (zo == reseed);
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+            for (int ex = 0; ex < 3; ++ex) {
+                const int i = ex + 3 * ey + 9 * ez;
+                if (bxf[ex] == 1 || byf[ey] == 1 || bzf[ez] == 1) {
+                    q[i] = own_rest ? 0.0f : Codec<ST>::load(f + (26 - i) * ncell + own, 26 - i);
+                } else if (bzf[ez] == 3) {
+                    q[i] = 0.0f;
+                } else if (bzf[ez] == 2) {
+                    const int c = sy[ey] * nx + sx[ex];
+                    q[i] = ghost_dev(i, __ldg(utop + c), __ldg(utop + plane + c), __ldg(utop + 2 * plane + c));
+                } else {
+                    q[i] = Codec<ST>::load(f + i * ncell + szp[ez] * plane + sy[ey] * nx + sx[ex], i);
+                }
+            }
+}
+
+// Raw moments of the scaled deviations up to second order (all times 216):
+// drho = sum s, j = sum xi s, Pi'_ab = sum xi_a xi_b s, by three separable
+// 3-point passes.
+struct Mom {
+    float drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
+};
+
+__device__ __forceinline__ Mom moments27(const float q[27]) {
+    float A0[9], A1[9], A2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {  // k = ey + 3 ez; x pass
+        const float a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
+        A0[k] = a + b + c;
+        A1[k] = c - a;
+        A2[k] = c + a;
+    }
+    float B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez) {  // y pass
+        const int k = 3 * ez;
+        B00[ez] = A0[k] + A0[k + 1] + A0[k + 2];
+        B01[ez] = A0[k + 2] - A0[k];
+        B02[ez] = A0[k + 2] + A0[k];
+        B10[ez] = A1[k] + A1[k + 1] + A1[k + 2];
+        B11[ez] = A1[k + 2] - A1[k];
+        B20[ez] = A2[k] + A2[k + 1] + A2[k + 2];
+    }
+    Mom m;  // z pass
+    m.drho = B00[0] + B00[1] + B00[2];
+    m.jz = B00[2] - B00[0];
+    m.pzz = B00[2] + B00[0];
+    m.jy = B01[0] + B01[1] + B01[2];
+    m.pyz = B01[2] - B01[0];
+    m.pyy = B02[0] + B02[1] + B02[2];
+    m.jx = B10[0] + B10[1] + B10[2];
+    m.pxz = B10[2] - B10[0];
+    m.pxy = B11[0] + B11[1] + B11[2];
+    m.pxx = B20[0] + B20[1] + B20[2];
+    return m;
+}
+
+// Macroscopic quantities from the scaled moments (the tilde quantities are
+// 216 times the physical ones):
+//   drho = drho~ / 216, rho = 1 + drho, u = j~ / (216 + drho~),
+//   P1~ = Pi'~ - drho~ I / 3 - j~ u^T   (= 216 [Pi - rho (I/3 + u u)]).
+struct Macro {
+    float drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;  // P: scaled by 216
+};
+
+__device__ __forceinline__ Macro macro_of(const Mom &m) {
+    Macro M;
+    M.drho = m.drho * INV_SCALE;
+    M.rho = 1.0f + M.drho;
+    const float ir = __frcp_rn(SCALE + m.drho);
+    M.ux = m.jx * ir;
+    M.uy = m.jy * ir;
+    M.uz = m.jz * ir;
+    const float d3 = m.drho * (1.0f / 3.0f);
+    M.Pxx = m.pxx - d3 - m.jx * M.ux;
+    M.Pyy = m.pyy - d3 - m.jy * M.uy;
+    M.Pzz = m.pzz - d3 - m.jz * M.uz;
+    M.Pxy = m.pxy - m.jx * M.uy;
+    M.Pxz = m.pxz - m.jx * M.uz;
+    M.Pyz = m.pyz - m.jy * M.uz;
+    return M;
+}
+
+// Per-axis factors of the collision.  With m(u) = prod_a u_a^{p_a} and the
+// weighted basis g_p(xi) = w1(xi) H_p(xi), every term of the post-collision
+// Hermite expansion is an outer product of one 3-vector per axis, so each
+// population is rebuilt directly from per-axis vectors (here scaled by 6 so
+// that the weights 6 w1 = (1, 4, 1) are exact):
+//   X(e)   = 6 sum_p u^p g_p(e)      = W1(e) (1 + a(e)),  a = (-3u+3u^2, -3u^2/2, 3u+3u^2)
+//   X'(e)  = 6 sum_p p u^(p-1) g_p(e) = (6u - 3, -12u, 6u + 3)
+//   X''(e) = 6 sum_p p(p-1) u^(p-2) g_p(e) = (6, -12, 6)
+// and, for P' = (1 - 1/tau) P1 (P1 the physical tensor),
+//   s_i = 216 (f*_i - w_i) = [rho X Y Z - W_i] + X'' [P'xx/2 Y Z]
+//         + X [P'yy/2 Y'' Z + P'zz/2 Y Z'' + P'yz Y' Z'] + X' [P'xy Y' Z + P'xz Y Z'],
+// the bracketed equilibrium deviation evaluated as W_i (rho E + drho) with
+// E = (1+a_x)(1+a_y)(1+a_z) - 1 expanded so no O(1) term cancels.
+struct AxisF {
+    float a[3], X[3], Xp[3];
+};
+
+__device__ __forceinline__ AxisF axis_of(float u) {
+    AxisF f;
+    const float u2 = u * u;
+    f.a[0] = 3.0f * (u2 - u);
+    f.a[1] = -1.5f * u2;
+    f.a[2] = 3.0f * (u2 + u);
+    f.X[0] = 1.0f + f.a[0];
+    f.X[1] = 4.0f * (1.0f + f.a[1]);
+    f.X[2] = 1.0f + f.a[2];
+    f.Xp[0] = 6.0f * u - 3.0f;
+    f.Xp[1] = -12.0f * u;
+    f.Xp[2] = 6.0f * u + 3.0f;
+    return f;
+}
+
+// Scaled equilibrium deviation 216 (f0_i(rho, u) - w_i), times c, into s.
+__device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
+                                           float drho, float c, float s[27], bool first) {
+    float sxy[9];
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = fmaf(fx.a[ex], fy.a[ey], fx.a[ex] + fy.a[ey]);
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = k + 9 * ez;
+            const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
+            const float v = (c * Wq(i)) * fmaf(E, rho, drho);
+            s[i] = first ? v : s[i] + v;
+        }
+}
+
+// Post-collision scaled deviations s_i = 216 (f*_i - w_i) of one cell.
+// forced: equilibrium part (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
+// f0(u + tau h) (scheme 1), both reducing to f0(u) at h = 0.
+__device__ __forceinline__ void collide_factored(const Macro &M, float omega, float tau, bool forced, float hx,
+                                                 float hy, float hz, int scheme, float s[27]) {
+    const AxisF fx = axis_of(M.ux), fy = axis_of(M.uy), fz = axis_of(M.uz);
+    if (!forced) {
+        add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f, s, true);
+    } else {
+        const AxisF vx = axis_of(M.ux + tau * hx), vy = axis_of(M.uy + tau * hy), vz = axis_of(M.uz + tau * hz);
+        if (scheme == 1) {
+            add_eq_dev(vx, vy, vz, M.rho, M.drho, 1.0f, s, true);
+        } else {
+            add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f - omega, s, true);
+            add_eq_dev(vx, vy, vz, M.rho, M.drho, omega, s, false);
+        }
+    }
+    // P' = (1 - 1/tau) P1 with P1 = P1~ / 216
+    const float om1 = (1.0f - omega) * INV_SCALE;
+    const float hxx = 0.5f * om1 * M.Pxx, hyy = 0.5f * om1 * M.Pyy, hzz = 0.5f * om1 * M.Pzz;
+    const float pxy = om1 * M.Pxy, pxz = om1 * M.Pxz, pyz = om1 * M.Pyz;
+    const float Xpp[3] = {6.0f, -12.0f, 6.0f};
+    float cY[3], cZ[3], bY[3], aY[3], bZ[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        cY[e] = hyy * Xpp[e];     // P'yy/2 Y''
+        cZ[e] = hzz * Xpp[e];     // P'zz/2 Z''
+        bY[e] = pyz * fy.Xp[e];   // P'yz Y'
+        aY[e] = pxy * fy.Xp[e];   // P'xy Y'
+        bZ[e] = pxz * fz.Xp[e];   // P'xz Z'
+    }
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 3; ++ey) {
+            const float G0 = hxx * (fy.X[ey] * fz.X[ez]);
+            const float G1 = fmaf(cY[ey], fz.X[ez], fmaf(fy.X[ey], cZ[ez], bY[ey] * fz.Xp[ez]));
+            const float G2 = fmaf(aY[ey], fz.X[ez], fy.X[ey] * bZ[ez]);
+#pragma unroll
+            for (int ex = 0; ex < 3; ++ex) {
+                const int i = ex + 3 * ey + 9 * ez;
+                s[i] = fmaf(Xpp[ex], G0, fmaf(fx.X[ex], G1, fmaf(fx.Xp[ex], G2, s[i])));
+            }
+        }
+}
+
+// Offset of window coordinate c from (box origin - margin) along one axis,
+// wrapped into [0, n) along periodic axes (lo_w: the origin already wrapped).
+__device__ __forceinline__ int rel_axis(int c, int lo, int lo_w, int margin, int n, bool periodic) {
+    if (!periodic) return c - lo + margin;
+    int r = c - lo_w + margin;
+    r += (r < 0) ? n : 0;
+    r -= (r >= n) ? n : 0;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// K1: fused collide + stream.  MODE selects the cells and the forcing:
+//   K1_ALL    every cell, no support box (fluid without particle);
+//   K1_ALLF   every cell, h_imm read on the support box;
+//   K1_FAR    every cell outside the near region (support box grown by
+//             NEAR_MARGIN cells) -- no forcing there;
+//   K1_NEAR   the near region only (grid over its extent), with forcing.
+// FAR and NEAR together cover the window once.
+enum { K1_ALL = 0, K1_ALLF = 1, K1_FAR = 2, K1_NEAR = 3 };
+
+// One cell of K1.  (cx, cy, cz): window coordinates (x, y, logical z) for
+// ALL / ALLF / FAR, coordinates within the near region for NEAR; out-of-range
+// coordinates return.  S is the window slot of the pulled time level.
+template <int ST, int MODE>
+__device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
+                                        typename Codec<ST>::T *__restrict__ dst, const float *__restrict__ utop_in,
+                                        float *__restrict__ utop_out, const BodySlot &S,
+                                        const float *__restrict__ hbox, const BoxGeom &box, int cx, int cy, int cz) {
+    int x, y, zl;
+    const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
+    if (MODE == K1_NEAR) {
+        // grid over the near region; map to window cells, skip cells outside closed faces
+        if (cx >= box.Bx + 2 * NEAR_MARGIN || cy >= box.By + 2 * NEAR_MARGIN) return;
+        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_MARGIN + cx;
+        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_MARGIN + cy;
+        zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_MARGIN + cz;
+        if (perx) { x += (x < 0) ? g.nx : 0; x -= (x >= g.nx) ? g.nx : 0; } else if (x < 0 || x >= g.nx) return;
+        if (pery) { y += (y < 0) ? g.ny : 0; y -= (y >= g.ny) ? g.ny : 0; } else if (y < 0 || y >= g.ny) return;
+        if (perz) { zl += (zl < 0) ? g.nz : 0; zl -= (zl >= g.nz) ? g.nz : 0; } else if (zl < 0 || zl >= g.nz) return;
+    } else {
+        x = cx;
+        y = cy;
+        zl = cz;
+        if (x >= g.nx || y >= g.ny) return;
+        if (MODE == K1_FAR) {
+            const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
+            const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
+            const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
+            if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
+                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN) &&
+                (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN))
+                return;
+        }
+    }
+    const int ring = S.ring;
+    float q[27];
+    pull27<ST>(g, src, x, y, zl, ring, S.reseed, utop_in, q);
+    const float omega = omega_of(g, zl);
+    bool forced = false;
+    float hx = 0.0f, hy = 0.0f, hz = 0.0f;
+    if (MODE == K1_ALLF || MODE == K1_NEAR) {
+        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], 0, g.nx, perx);
+        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], 0, g.ny, pery);
+        const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], 0, g.nz, perz);
+        if ((unsigned)rx < (unsigned)box.Bx && (unsigned)ry < (unsigned)box.By && (unsigned)rz < (unsigned)box.Bz) {
+            const size_t b = ((size_t)rz * box.By + ry) * box.Bx + rx;
+            hx = __ldg(hbox + b);
+            hy = __ldg(hbox + box.nbox + b);
+            hz = __ldg(hbox + 2 * box.nbox + b);
+            forced = true;
+        }
+    }
+    const Macro M = macro_of(moments27(q));
+    if (zl == g.nz - 1) {
+        const size_t c = (size_t)y * g.nx + x;
+        utop_out[c] = M.ux;
+        utop_out[g.plane + c] = M.uy;
+        utop_out[2 * g.plane + c] = M.uz;
+    }
+    if (MODE == K1_ALLF || MODE == K1_NEAR)
+        collide_factored(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
+    else
+        collide_factored(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
+    const int own = zphys(zl, ring, g.nz) * (int)g.plane + y * g.nx + x;
+    const int ncell = (int)g.ncell;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i], i);
+}
+
+// Tile of a 1-D block of blockDim.x threads over (x, y): tx threads along x,
+// blockDim.x / tx rows along y, one plane; block b of a region ex x ey x ez,
+// x fastest.
+__device__ __forceinline__ void tile_coords(int b, int tx, int ex, int ey, int &cx, int &cy, int &cz) {
+    const int ty = blockDim.x / tx;
+    const int gx = (ex + tx - 1) / tx, gy = (ey + ty - 1) / ty;
+    const int bx = b % gx, rest = b / gx;
+    cx = bx * tx + (int)threadIdx.x % tx;
+    cy = (rest % gy) * ty + (int)threadIdx.x / tx;
+    cz = rest / gy;
+}
+
+// ---------------------------------------------------------------------------
+// Batched K1: one launch over the (run, tile) table of many independent runs.
+// Block b belongs to the run r with prefix[r] <= b < prefix[r + 1]; every run
+// keeps its own storage type, window, boundary conditions, relaxation times
+// and tile, read from its descriptor.  PHASE_BULK: the far cells of runs that
+// split (no blocks for the others); PHASE_NEAR: the near region of runs that
+// split, the whole window (with forcing) of runs that do not.
+__device__ __forceinline__ int find_run(const int *__restrict__ prefix, int nruns, int b, int &local) {
+    int lo = 0, hi = nruns;  // largest r with prefix[r] <= b
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid;
+    }
+    local = b - __ldg(prefix + lo);
+    return lo;
+}
+
+// K2 + binning, one launch.  Blocks [0, nmom): u* and the stress of Eq. 10,
+// sigma = -p I + (1/(2 tau) - 1) P1 with p = c_s^2 (rho - 1), at every
+// support-box cell, from f(t+1) pulled from the post-collision buffer (box
+// cells outside a closed face get zeros).  Blocks [nmom, nmom + ntiles): for
+// one TILE^3 tile of the box, two lists in marker order (ordered compaction
+// with warp ballots; no atomics): list 0, the markers whose 4x4x4 stencil
+// overlaps the tile (spreading); list 1, those whose stencil overlaps the
+// stencil of any marker based in the tile (rows of A).
+constexpr int MB_THREADS = 256;
+
+template <int ST>
+__device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
+                                         const float *__restrict__ utop_in, const DevState *__restrict__ st, int slot,
+                                         const BoxGeom &box, const BoxArrays &ba, int nmom, int nm,
+                                         const int *__restrict__ mbase, int *__restrict__ tile_list,
+                                         int *__restrict__ tile_count, int cap, DevState *stw, int blk) {
+    if (blk >= nmom) {
+        constexpr int NW = MB_THREADS / 32;
+        const int tile = blk - nmom;
+        const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
+        const int t0[3] = {TILE * tx, TILE * ty, TILE * tz};
+        __shared__ int wcount[2][NW];
+        __shared__ int total[2];
+        const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+        if (tid < 2) total[tid] = 0;
+        int pb = (tid < nm) ? __ldg(mbase + tid) : 0;
+        __syncthreads();
+        for (int chunk = 0; chunk < nm; chunk += MB_THREADS) {
+            const int k = chunk + tid;
+            const int nxt = (k + MB_THREADS < nm) ? __ldg(mbase + k + MB_THREADS) : 0;  // prefetch
+            bool hit[2] = {false, false};
+            if (k < nm) {
+                const int b[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
+                hit[0] = hit[1] = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const bool lo = b[a] + 3 >= t0[a];
+                    hit[0] = hit[0] && lo && (b[a] <= t0[a] + TILE - 1);  // stencil overlaps the tile
+                    hit[1] = hit[1] && lo && (b[a] <= t0[a] + TILE + 2);  // ... or a stencil based in it
+                }
+            }
+            unsigned bal[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                bal[l] = __ballot_sync(0xffffffffu, hit[l]);
+                if (lane == 0) wcount[l][warp] = __popc(bal[l]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                int off = total[l];
+                for (int w = 0; w < warp; ++w) off += wcount[l][w];
+                if (hit[l]) {
+                    const int pos = off + __popc(bal[l] & ((1u << lane) - 1u));
+                    if (pos < cap) tile_list[((size_t)l * (box.tx * box.ty * box.tz) + tile) * cap + pos] = k;
+                }
+            }
+            __syncthreads();
+            if (tid < 2) {
+                int sum = 0;
+                for (int w = 0; w < NW; ++w) sum += wcount[tid][w];
+                total[tid] += sum;
+            }
+            __syncthreads();
+            pb = nxt;
+        }
+        if (tid < 2) {
+            tile_count[tid * (box.tx * box.ty * box.tz) + tile] = total[tid] < cap ? total[tid] : cap;
+            if (total[tid] > cap) atomicCAS(&stw->status, 0, STAT_OVERFLOW);
+        }
+        return;
+    }
+    const long long b = (long long)blk * blockDim.x + threadIdx.x;
+    if (b >= box.nbox) return;
+    const int bx = (int)(b % box.Bx);
+    const int by = (int)((b / box.Bx) % box.By);
+    const int bz = (int)(b / ((long long)box.Bx * box.By));
+    int c[3] = {st->s[slot].box_lo[0] + bx, st->s[slot].box_lo[1] + by, st->s[slot].box_lo[2] + bz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (per[a]) {
+            c[a] %= n[a];
+            if (c[a] < 0) c[a] += n[a];
+        } else if (c[a] < 0 || c[a] >= n[a]) {
+            inside = false;
+        }
+    }
+    if (!inside) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ba.u[k * box.nbox + b] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ba.s[k * box.nbox + b] = 0.0f;
+        return;
+    }
+    float q[27];
+    pull27<ST>(g, src, c[0], c[1], c[2], st->s[slot].ring, st->s[slot].reseed, utop_in, q);
+    const Macro M = macro_of(moments27(q));
+    const float tau = tau_of(g, c[2]);
+    const float k2 = (0.5f / tau - 1.0f) * INV_SCALE;  // P1 = P1~ / 216
+    const float p = M.drho * (1.0f / 3.0f);
+    ba.u[b] = M.ux;
+    ba.u[box.nbox + b] = M.uy;
+    ba.u[2 * box.nbox + b] = M.uz;
+    ba.s[b] = -p + k2 * M.Pxx;
+    ba.s[box.nbox + b] = -p + k2 * M.Pyy;
+    ba.s[2 * box.nbox + b] = -p + k2 * M.Pzz;
+    ba.s[3 * box.nbox + b] = k2 * M.Pxy;
+    ba.s[4 * box.nbox + b] = k2 * M.Pxz;
+    ba.s[5 * box.nbox + b] = k2 * M.Pyz;
+}
+
+}  // namespace turret

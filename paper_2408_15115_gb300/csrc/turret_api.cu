@@ -27,45 +27,10 @@
 #include <vector>
 
 #include "../../include/turret.h"
+#include "turret_ctx.cuh"
 #include "turret_internal.cuh"
 
 using namespace turret;
-
-struct turret_ctx {
-    turret_window win;
-    turret_flags flags;
-    int storage;
-    double nu, tau0, kappa, g[3];
-    cudaStream_t stream;  // caller's stream
-    cudaStream_t side;    // internal high-priority stream of the immersed-boundary chain
-    cudaStream_t aux;     // internal stream of the FP64 force/torque reduction
-    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done;
-    Geom geom;
-    // fluid workspace
-    void *f[2];
-    float *utop[2];
-    DevState *dstate;
-    // particle
-    bool has_particle;
-    bool split;  // near/far collide+stream with the chain on the side stream
-    int nm;
-    BodyConst body;
-    BoxGeom box;
-    MarkerArrays mk;
-    BoxArrays ba;
-    int *tile_list, *tile_count;
-    int cap;
-    double vol, area;
-    DevState host_state;
-    DevState *pinned;  // page-locked staging of the device state for queries
-    std::vector<float> staging;
-    std::vector<float> tau_host;  // staging of the per-plane relaxation times
-    // stepping
-    long long step;
-    cudaGraphExec_t graph[2];
-    bool graph_ready[2];
-    std::string err;
-};
 
 static std::string g_init_err;
 

@@ -1,0 +1,47 @@
+// turret_ctx.cuh -- the context behind the opaque turret_ctx handle of the
+// C ABI (include/turret.h), shared by the single-run and the batch entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/turret.h"
+#include "turret_internal.cuh"
+
+struct turret_ctx {
+    turret_window win;
+    turret_flags flags;
+    int storage;
+    double nu, tau0, kappa, g[3];
+    cudaStream_t stream;  // caller's stream
+    cudaStream_t side;    // internal high-priority stream of the immersed-boundary chain
+    cudaStream_t aux;     // internal stream of the FP64 force/torque reduction
+    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done;
+    turret::Geom geom;
+    // fluid workspace
+    void *f[2];
+    float *utop[2];
+    turret::DevState *dstate;
+    // particle
+    bool has_particle;
+    bool split;  // near/far collide+stream with the chain on the side stream
+    int nm;
+    turret::BodyConst body;
+    turret::BoxGeom box;
+    turret::MarkerArrays mk;
+    turret::BoxArrays ba;
+    int *tile_list, *tile_count;
+    int cap;
+    double vol, area;
+    turret::DevState host_state;
+    turret::DevState *pinned;  // page-locked staging of the device state for queries
+    std::vector<float> staging;
+    std::vector<float> tau_host;  // staging of the per-plane relaxation times
+    // stepping
+    long long step;
+    cudaGraphExec_t graph[2];
+    bool graph_ready[2];
+    std::string err;
+};
+

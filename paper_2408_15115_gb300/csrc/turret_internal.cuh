@@ -118,6 +118,27 @@ struct BoxArrays {
     float *h;   // [3][nbox] spread force (h_imm after the last cycle)
 };
 
+// One run of a batch: everything a batched kernel needs about one context,
+// in device memory.  A batched launch covers the (run, block) table of all
+// runs; block b belongs to run r when prefix[r] <= b < prefix[r + 1].
+struct RunDesc {
+    Geom g;
+    BodyConst bc;
+    BoxGeom box;
+    MarkerArrays m;
+    BoxArrays ba;
+    void *f[2];          // ping-pong population buffers
+    float *utop[2];      // top-plane velocity buffers
+    DevState *st;
+    int *tile_list, *tile_count;
+    int storage, cap, nm;
+    int split;           // 1: far / near collide+stream, 0: the whole window in the near phase
+    int tx;              // collide+stream tile width (threads along x)
+};
+enum { PHASE_BULK = 0, PHASE_NEAR = 1 };
+// h arrays of the IBM cycles, selected per run in batched launches
+enum { HSEL_R0 = 0, HSEL_HL = 1, HSEL_HB = 2 };
+
 // ---------------------------------------------------------------------------
 // D3Q27 index i = ex + 3 ey + 9 ez with e = xi + 1 in {0,1,2}; opposite 26 - i.
 // Tensor-product weights w_i = w1(x) w1(y) w1(z), w1 = (1/6, 2/3, 1/6).
@@ -175,6 +196,19 @@ cudaError_t launch_init_equilibrium(const Geom &g, int storage, void *dst, const
                                     float *utop, cudaStream_t s);
 cudaError_t launch_macro(const Geom &g, int storage, const void *src, const float *utop_in, const DevState *st,
                          int slot, float *out, bool pops, cudaStream_t s);
+// K1 over one window with a 1-D block of `threads` and tile width tx (timing
+// of tile candidates; same cells and arithmetic as launch_collide_stream).
+// minb: register-budget variant (3: <= 80 registers, 4: <= 64 registers).
+bool valid_tile(int threads, int tx, int minb);
+cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
+                                 float *utop_out, const DevState *st, int slot, const float *hbox,
+                                 const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s);
+// Batched K1 of phase PHASE_BULK or PHASE_NEAR over nblocks blocks.
+cudaError_t launch_batch_collide(int phase, const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                 int threads, int minb, cudaStream_t s);
+bool is_batch_bulk_kernel(const void *fn);
+cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                         cudaStream_t s);
 // Support-box moments (u*, sigma) and the tile candidate lists, one launch.
 cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
                                    const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
@@ -197,6 +231,23 @@ cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out
 cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, cudaStream_t s);
 cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
                           const int *tile_count, int cap, cudaStream_t s);
+// Batched forms of the launches above, one launch over all runs of a batch
+// (time level p -> p ^ 1; blocks per run from the per-phase prefix table).
+cudaError_t launch_batch_particle_markers(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
+                                          cudaStream_t s);
+cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s);
+cudaError_t launch_batch_cycle(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int sel_in,
+                               int sel_out, int last, cudaStream_t s);
+cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, cudaStream_t s);
+cudaError_t launch_batch_spread(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s);
+// Blocks of one run in each batched phase (host side, same formulas as the kernels).
+int blocks_bulk(const RunDesc &r, int threads);
+int blocks_near(const RunDesc &r, int threads);
+int blocks_particle_markers(const RunDesc &r);
+int blocks_box_moments_bin(const RunDesc &r);
+int blocks_interp0(const RunDesc &r);
+int blocks_cycle(const RunDesc &r);
+int blocks_spread(const RunDesc &r);
 
 constexpr int TILE = 4;          // support-box tiles of TILE^3 cells (spreading)
 constexpr int INTERP_WARPS = 8;  // markers per interpolation block

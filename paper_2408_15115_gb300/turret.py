@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libturret.so")
 
 STATUS = {0: "TURRET_OK", 1: "TURRET_EINVAL", 2: "TURRET_ENOMEM", 3: "TURRET_ECUDA", 4: "TURRET_ESTATE",
-          5: "TURRET_EDIVERGED", 6: "TURRET_ETIMEOUT", 7: "TURRET_EDOMAIN"}
+          5: "TURRET_EDIVERGED", 6: "TURRET_ETIMEOUT", 7: "TURRET_EDOMAIN", 8: "TURRET_EOVERFLOW"}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 PERIODIC, NOSLIP, PRESSURE = 0, 1, 2
 
@@ -91,6 +91,20 @@ def lib():
         L.ibm_spread_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp, vp]
         L.turret_last_error.restype = C.c_char_p
         L.turret_last_error.argtypes = [vp]
+        L.turret_batch_workspace_bytes.restype = C.c_size_t
+        L.turret_batch_workspace_bytes.argtypes = [C.c_int32]
+        L.turret_batch_init.restype = C.c_int
+        L.turret_batch_init.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int32, vp, C.c_size_t, vp]
+        L.turret_batch_set_tiles.restype = C.c_int
+        L.turret_batch_set_tiles.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+        L.turret_batch_step.restype = C.c_int
+        L.turret_batch_step.argtypes = [vp, C.c_int64]
+        L.turret_batch_destroy.restype = C.c_int
+        L.turret_batch_destroy.argtypes = [vp]
+        L.turret_batch_last_error.restype = C.c_char_p
+        L.turret_batch_last_error.argtypes = [vp]
+        L.turret_time_collide.restype = C.c_int
+        L.turret_time_collide.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         _lib = L
     return _lib
 
@@ -143,6 +157,7 @@ class Turret:
         self._L = lib()
         self.win = Window(nx, ny, nz, bc_x, bc_y, bc_bottom, bc_top, sponge, slide, 0, float(anchor_frac))
         st = STORAGE[storage]
+        self.storage = storage
         nb = self._L.lbm_workspace_bytes(C.byref(self.win), st)
         if nb == 0:
             raise TurretError(1, "invalid window")
@@ -213,10 +228,83 @@ class Turret:
         self._check(self._L.lbm_copy_populations(self.ctx, C.c_void_p(out.data_ptr())))
         return out
 
+    def time_collide(self, threads, tx, minb, reps=20):
+        """Mean microseconds of one collide+stream launch with the given launch
+        shape (the context's state is left unchanged)."""
+        us = C.c_float()
+        self._check(self._L.turret_time_collide(self.ctx, int(threads), int(tx), int(minb), int(reps), C.byref(us)))
+        return float(us.value)
+
+    @property
+    def cells(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
     def close(self):
         if getattr(self, "ctx", None) is not None:
             self._L.lbm_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent runs (Turret objects with a loaded surface) advanced together:
+    one launch per phase of the step for all runs, one CUDA graph per step.
+    Every run evolves bit for bit as it would alone."""
+
+    def __init__(self, turrets, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.runs = list(turrets)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._L = lib()
+        n = len(self.runs)
+        nb = self._L.turret_batch_workspace_bytes(n)
+        if nb == 0:
+            raise TurretError(1, "empty batch")
+        self._ws, ptr = _aligned_workspace(torch, nb, self.device)
+        arr = (C.c_void_p * n)(*[t.ctx.value for t in self.runs])
+        b = C.c_void_p()
+        rc = self._L.turret_batch_init(C.byref(b), arr, n, C.c_void_p(ptr), C.c_size_t(nb),
+                                       C.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise TurretError(rc, self._L.turret_batch_last_error(None).decode())
+        self.b = b
+        self.tiles = (128, 3, [32] * n)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TurretError(rc, self._L.turret_batch_last_error(self.b).decode())
+
+    def set_tiles(self, threads, minb, tx):
+        arr = (C.c_int32 * len(self.runs))(*[int(t) for t in tx])
+        self._check(self._L.turret_batch_set_tiles(self.b, int(threads), int(minb), arr))
+        self.tiles = (int(threads), int(minb), [int(t) for t in tx])
+
+    def autotune(self, cache_path=None, reps=20, candidates=None):
+        """Choose the collide+stream launch shape by timing candidates on one
+        run per (nx, storage) class; timings are cached in a JSON file."""
+        from . import autotune as AT
+        choice = AT.tune([AT.RunInfo(t.shape[2], t.storage, t.cells, t) for t in self.runs],
+                         timer=lambda t, th, tx, mb: t.time_collide(th, tx, mb, reps),
+                         cache_path=cache_path, device_name=self.torch.cuda.get_device_name(self.device),
+                         candidates=candidates)
+        self.set_tiles(choice.threads, choice.minb, choice.tx)
+        return choice
+
+    def step(self, n=1):
+        self._check(self._L.turret_batch_step(self.b, int(n)))
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            self._L.turret_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
