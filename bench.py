@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GLUPS & %HBM roofline per RR-LBM+IBM step; mixed/batched vs FP32 at ≤1% drag err"
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}
 K1_PROFILE = os.path.join(ROOT, "profiles", "k_collide_stream_prolate_96x96x192.md")
-K1_SOURCE = os.path.join(ROOT, "paper_2408_15115_gb300", "csrc", "lbm_kernels.cu")
+K1_SOURCES = [os.path.join(ROOT, "paper_2408_15115_gb300", "csrc", f) for f in ("lbm_cell.cuh", "lbm_kernels.cu")]
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--workload", default="prolate_turret")
     p.add_argument("--storage", default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--ensemble-steps", type=int, default=100)
     return p.parse_args()
 
 
@@ -112,6 +114,14 @@ class Clocks:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
+def source_hash():
+    """Hash of the collide+stream kernel's sources (cell code and kernel)."""
+    h = hashlib.sha256()
+    for f in K1_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic():
     """DRAM bytes per launch of the collide+stream kernel from the committed ncu
     summary, or None when the kernel source changed since it was taken."""
@@ -119,7 +129,7 @@ def profile_traffic():
         txt = open(K1_PROFILE).read()
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(K1_SOURCE, "rb").read()).hexdigest()[:16]
+    src_hash = source_hash()
     vals = {}
     for line in txt.splitlines():
         if line.startswith("machine:"):
@@ -191,6 +201,77 @@ def run_reference(args):
                                       (k, cfg["name"], args.steps)},
            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def ensemble_leg(dev, K, W, tile_cache):
+    """The 64-run settling ensemble (seed 4): the plain FP32 form (each run
+    alone, one after another, per-run step graphs) against the batched form
+    (one launch per phase for all runs, autotuned tiles), in FP32 and with
+    storage alternating FP32 / FP16.  Rates in particle-steps/s and GLUPS."""
+    import torch
+
+    from paper_2408_15115_gb300 import configs
+    from paper_2408_15115_gb300 import turret as T
+
+    base = configs.ensemble(64, seed=4, storage="alternate")
+    cells = [c["nx"] * c["ny"] * c["nz"] for c in base]
+    total = sum(cells)
+    n = len(base)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def rates(ms, steps):
+        s = ms / 1e3
+        return {"particle_steps_per_s": n * steps / s, "glups": total * steps / s / 1e9, "ms_per_step": ms / steps}
+
+    # plain FP32: every run alone, one after another
+    f32 = configs.load_ensemble([dict(c, storage="f32") for c in base], device=dev)
+    seq_ms = 0.0
+    for t in f32:
+        t.step(W)
+        torch.cuda.synchronize(dev)
+        a, b = ev(), ev()
+        a.record(t.stream)
+        t.step(K)
+        b.record(t.stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += a.elapsed_time(b)
+    out = {"workload": "ensemble_64_seed4", "runs": n, "cells": total,
+           "markers": int(sum(c["verts"].shape[0] for c in base)), "steps": K,
+           "windows": sorted({"%dx%dx%d" % (c["nx"], c["ny"], c["nz"]) for c in base}),
+           "plain_f32_sequential": rates(seq_ms, K)}
+
+    def batched(runs, key):
+        b = T.Batch(runs, device=dev)
+        choice = b.autotune(cache_path=tile_cache, reps=10)
+        b.step(W)
+        torch.cuda.synchronize(dev)
+        a, e = ev(), ev()
+        a.record(b.stream)
+        b.step(K)
+        e.record(b.stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(e)
+        r = rates(ms, K)
+        alg = sum(c * (216 if t.storage == "f32" else 108) for c, t in zip(cells, runs))
+        r["whole_step_gbs"] = alg / (ms / K / 1e3) / 1e9
+        r["tiles"] = {"threads": choice.threads, "minb": choice.minb, "tx": choice.tx}
+        r["gpu_launches_per_step"] = 6 + 3 + 1  # collide bulk + near, markers, moments, interp, reduce, 3 cycles, spread
+        b.close()
+        out[key] = r
+
+    batched(f32, "batched_f32")
+    for t in f32:
+        t.close()
+    del f32
+    mixed = configs.load_ensemble(base, device=dev)
+    batched(mixed, "batched_mixed")
+    for t in mixed:
+        t.close()
+    out["speedup_batched_mixed_vs_plain_f32"] = (out["batched_mixed"]["particle_steps_per_s"] /
+                                                 out["plain_f32_sequential"]["particle_steps_per_s"])
+    return out
 
 
 def run_ours(args):
@@ -291,7 +372,7 @@ def run_ours(args):
            "dtype": cfg["storage"], "data": "synthetic",
            "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
                       "storage": cfg["storage"], "nu": cfg["nu"], "kappa": cfg["kappa"], "g": cfg["g"][2],
-                      "l2": "inputs larger than L2 (two population buffers of %d MB)" % (27 * cells * bpc // 2 // 2**20),
+                      "l2": "inputs larger than L2 (two population buffers of %d MiB)" % (cells * bpc // 2 // 2**20),
                       "replicas": world},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -300,6 +381,9 @@ def run_ours(args):
                         "peak_kind": peak_kind,
                         "whole_step_frac": (bpc * cells / (ms / K / 1e3) / 1e9) / peaks["hbm_gbs"]},
            "e2e": e2e, "gpu_launches": kps * K, "clocks": clocks}
+    if world == 1 and not args.no_ensemble:
+        out["ensemble"] = ensemble_leg(dev, args.ensemble_steps, max(W, 3),
+                                       os.path.join(ROOT, "paper_2408_15115_gb300", "_build", "tiles.json"))
     if world == 1 and not args.no_cpu_baseline:
         v, cores, n, dt = oracle_sample(cfg)
         out["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",

@@ -76,3 +76,67 @@ def make_turret(cfg, **kw):
     t = Turret(cfg["nx"], cfg["ny"], cfg["nz"], cfg["nu"], cfg["kappa"], cfg["g"], *cfg["bc"], sponge=cfg["sponge"],
                slide=cfg["slide"], anchor_frac=cfg["anchor"], storage=cfg["storage"], **kw)
     return t
+
+
+ENSEMBLE_SHAPES = ("sphere", "oblate", "prolate", "irregular")
+ENSEMBLE_WINDOWS = ((64, 64, 64), (96, 96, 192), (128, 128, 256))
+
+
+def _freq_for(r_max, spacing=0.9):
+    """Icosphere frequency giving marker spacing about ``spacing`` on a surface
+    whose largest radius is r_max (the geodesic edge is about 1.2 r / n)."""
+    return max(4, int(math.ceil(1.2 * r_max / spacing)))
+
+
+def ensemble_member(shape, d, re, window, storage, seed, kappa=2.0):
+    """One settling run of the ensemble: a particle of volume-equivalent
+    diameter d (sphere, oblate 1:2, prolate 2:1 or spherical-harmonic
+    irregular), nu = 0.02 d / Re, g from Eq. 28, in a sliding turret window."""
+    rng = np.random.default_rng(seed)
+    R = 0.5 * d
+    if shape == "sphere":
+        V, T = I.sphere(_freq_for(R), d)
+    elif shape == "oblate":
+        a = R * 2.0 ** (1.0 / 3.0)  # semi-axes (a, a, a/2): volume of the sphere of radius R
+        V, T = I.ellipsoid(_freq_for(a), (a, a, 0.5 * a))
+    elif shape == "prolate":
+        b = R / 2.0 ** (1.0 / 3.0)  # semi-axes (2b, b, b)
+        V, T = I.ellipsoid(_freq_for(2.0 * b), (2.0 * b, b, b))
+    else:
+        V, T = I.sh_particle(_freq_for(1.2 * R), d, seed=int(rng.integers(1 << 30)))
+    if shape != "sphere":
+        V = I.rotate(I.rotate(V, "x", float(rng.uniform(0.0, 45.0))), "z", float(rng.uniform(0.0, 90.0)))
+    nx, ny, nz = window
+    nu = 0.02 * d / re
+    g = gravity_for(re, d, nu, kappa)
+    return dict(name="%s_d%.1f_re%.1f_%dx%dx%d" % (shape, d, re, nx, ny, nz), nx=nx, ny=ny, nz=nz, nu=nu,
+                kappa=kappa, g=(0.0, 0.0, -g), bc=(0, 0, 1, 2), sponge=int(round(0.08 * nz)), slide=1,
+                anchor=0.25, storage=storage, verts=V, tris=T,
+                r0=(0.5 * nx - 0.5, 0.5 * ny - 0.5, 0.25 * nz + 0.5), d_eq=d, re=re, shape=shape)
+
+
+def ensemble(n_runs=64, seed=4, storage="alternate", d_range=(8.0, 24.0), re_range=(1.0, 100.0)):
+    """Independent settling runs drawn by seed: shape uniform over
+    ENSEMBLE_SHAPES, d ~ U(d_range), Re log-uniform over re_range, window the
+    smallest of ENSEMBLE_WINDOWS at least 4 d wide; storage 'alternate'
+    (FP32, FP16, FP32, ...) or one storage name for every run."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for k in range(n_runs):
+        shape = ENSEMBLE_SHAPES[int(rng.integers(len(ENSEMBLE_SHAPES)))]
+        d = float(rng.uniform(*d_range))
+        re = float(math.exp(rng.uniform(math.log(re_range[0]), math.log(re_range[1]))))
+        window = next(w for w in ENSEMBLE_WINDOWS if w[0] >= 4.0 * d or w is ENSEMBLE_WINDOWS[-1])
+        st = ("f32" if k % 2 == 0 else "f16") if storage == "alternate" else storage
+        runs.append(ensemble_member(shape, d, re, window, st, seed=int(rng.integers(1 << 30))))
+    return runs
+
+
+def load_ensemble(cfgs, **kw):
+    """Turret objects with loaded surfaces for a list of ensemble configurations."""
+    out = []
+    for c in cfgs:
+        t = make_turret(c, **kw)
+        t.load_surface(c["verts"], c["tris"], c["r0"])
+        out.append(t)
+    return out

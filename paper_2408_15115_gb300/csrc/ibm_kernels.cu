@@ -38,7 +38,7 @@ __device__ __forceinline__ float peskin_out(float a) {
     return 0.125f * (5.0f - 2.0f * a - sqrtf(fmaxf(0.0f, -7.0f + 12.0f * a - 4.0f * a * a)));
 }
 
-constexpr int PM_THREADS = 128;
+constexpr int PM_THREADS = MARKER_SEG;
 
 // Every block recomputes the (tiny) rigid-body update from slot `slot` in
 // warp 0 -- identical inputs, identical FP64 results -- and block 0 stores it
@@ -166,51 +166,74 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
     const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};
     const int B[3] = {box.Bx, box.By, box.Bz};
     const int k = blk * PM_THREADS + tid;
-    if (k >= nm) return;
-    bool bad = false;
-    const float xb[3] = {m.Xb[k], m.Xb[nm + k], m.Xb[2 * nm + k]};
-    const float nbv[3] = {m.nb[k], m.nb[nm + k], m.nb[2 * nm + k]};
-    float arm[3], nn[3];
+    int bbv[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};  // no marker: neutral for the minimum
+    int bbmax[3] = {-1, -1, -1};
+    if (k < nm) {
+        bool bad = false;
+        const float xb[3] = {m.Xb[k], m.Xb[nm + k], m.Xb[2 * nm + k]};
+        const float nbv[3] = {m.nb[k], m.nb[nm + k], m.nb[2 * nm + k]};
+        float arm[3], nn[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        arm[a] = f_d[a] * xb[0] + f_d[3 + a] * xb[1] + f_d[6 + a] * xb[2];
-        nn[a] = f_d[a] * nbv[0] + f_d[3 + a] * nbv[1] + f_d[6 + a] * nbv[2];
-    }
-    const float U[3] = {f_v[0] + (f_w[1] * arm[2] - f_w[2] * arm[1]), f_v[1] + (f_w[2] * arm[0] - f_w[0] * arm[2]),
-                        f_v[2] + (f_w[0] * arm[1] - f_w[1] * arm[0])};
-    MRec r;
-    int bbv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float xr = f_cf[a] + arm[a];  // marker position relative to Ci
-        const float fl = floorf(xr);
-        const float t = xr - fl;            // in [0, 1)
-        int base_rel = (int)fl - 1;         // stencil cells base_rel .. base_rel + 3
-        int bv = i_ci[a] + base_rel - i_lo[a];
-        float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
-        // a non-finite or out-of-box position must never index memory: park the
-        // stencil at the box origin with zero weights and latch the status
-        if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
-            bv = 0;
-            base_rel = i_lo[a] - i_ci[a];
-            w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;
-            bad = true;
+        for (int a = 0; a < 3; ++a) {
+            arm[a] = f_d[a] * xb[0] + f_d[3 + a] * xb[1] + f_d[6 + a] * xb[2];
+            nn[a] = f_d[a] * nbv[0] + f_d[3 + a] * nbv[1] + f_d[6 + a] * nbv[2];
         }
-        const int abs_base = i_ci[a] + base_rel;
-        if (!per[a] && (abs_base < 0 || abs_base + 3 > n[a] - 1)) bad = true;
-        bbv[a] = bv;
-        float *dstw = (a == 0) ? r.wx : (a == 1) ? r.wy : r.wz;
+        const float U[3] = {f_v[0] + (f_w[1] * arm[2] - f_w[2] * arm[1]), f_v[1] + (f_w[2] * arm[0] - f_w[0] * arm[2]),
+                            f_v[2] + (f_w[0] * arm[1] - f_w[1] * arm[0])};
+        MRec r;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dstw[q] = w4[q];
-        m.U[a * nm + k] = U[a];
-        m.n[a * nm + k] = nn[a];
-        m.arm[a * nm + k] = arm[a];
+        for (int a = 0; a < 3; ++a) {
+            const float xr = f_cf[a] + arm[a];  // marker position relative to Ci
+            const float fl = floorf(xr);
+            const float t = xr - fl;            // in [0, 1)
+            int base_rel = (int)fl - 1;         // stencil cells base_rel .. base_rel + 3
+            int bv = i_ci[a] + base_rel - i_lo[a];
+            float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
+            // a non-finite or out-of-box position must never index memory: park the
+            // stencil at the box origin with zero weights and latch the status
+            if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
+                bv = 0;
+                base_rel = i_lo[a] - i_ci[a];
+                w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;
+                bad = true;
+            }
+            const int abs_base = i_ci[a] + base_rel;
+            if (!per[a] && (abs_base < 0 || abs_base + 3 > n[a] - 1)) bad = true;
+            bbv[a] = bv;
+            float *dstw = (a == 0) ? r.wx : (a == 1) ? r.wy : r.wz;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dstw[q] = w4[q];
+            m.U[a * nm + k] = U[a];
+            m.n[a * nm + k] = nn[a];
+            m.arm[a * nm + k] = arm[a];
+        }
+        r.base = bbv[0] | (bbv[1] << 10) | (bbv[2] << 20);
+        r.hdS[0] = r.hdS[1] = r.hdS[2] = 0.0f;
+        m.rec[k] = r;
+        m.base[k] = r.base;
+        if (bad) atomicCAS(&st->status, 0, STAT_DOMAIN);  // the first latched error wins
+        for (int a = 0; a < 3; ++a) bbmax[a] = bbv[a];
     }
-    r.base = bbv[0] | (bbv[1] << 10) | (bbv[2] << 20);
-    r.hdS[0] = r.hdS[1] = r.hdS[2] = 0.0f;
-    m.rec[k] = r;
-    m.base[k] = r.base;
-    if (bad) atomicCAS(&st->status, 0, STAT_DOMAIN);  // the first latched error wins
+    // bounding box of the stencil bases of this block's markers (a segment of
+    // PM_THREADS consecutive markers), read by the tile-list scan to skip
+    // segments that cannot reach a tile
+    __shared__ int s_seg[PM_THREADS / 32][6];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = __reduce_min_sync(0xffffffffu, bbv[a]);
+        const int hi = __reduce_max_sync(0xffffffffu, bbmax[a]);
+        if (lane == 0) {
+            s_seg[warp][a] = lo;
+            s_seg[warp][3 + a] = hi;
+        }
+    }
+    __syncthreads();
+    if (tid < 6) {
+        int v = s_seg[0][tid];
+        for (int w = 1; w < PM_THREADS / 32; ++w) v = (tid < 3) ? min(v, s_seg[w][tid]) : max(v, s_seg[w][tid]);
+        m.seg[blk * 6 + tid] = v;
+    }
 }
 
 __global__ void __launch_bounds__(PM_THREADS) k_particle_markers(Geom g, BodyConst bc, BoxGeom box, DevState *st,
@@ -248,6 +271,53 @@ __device__ __forceinline__ float overlap4(const float wk[4], const float wj[4], 
 constexpr int ROWS_THREADS = 256;
 constexpr int ROWS_WARPS = ROWS_THREADS / 32;
 
+// Step l = 0 for marker k by one warp: interpolation of u* and sigma (two
+// stencil cells per lane, xor-shuffle sums), h^0 = U - I[u*] and the
+// traction dS sigma.n with its moment about C_m.
+__device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, const MarkerArrays &m,
+                                                   const BoxArrays &ba, int k, const MRec &rk, int lane) {
+    const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
+    const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
+    const float wxy = pick4(rk.wx, i) * pick4(rk.wy, j);
+    const float w0 = wxy * (kz ? rk.wz[1] : rk.wz[0]);
+    const float w1 = wxy * (kz ? rk.wz[3] : rk.wz[2]);
+    const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
+    const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
+    const size_t N = box.nbox;
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = w0 * ba.u[c * N + c0] + w1 * ba.u[c * N + c1];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], q);
+    if (lane == 0) {
+        // l = 0: h_k = U_k - I[u*](X_k); traction dS sigma(X_k) n_k and its moment
+        const float dS = m.dS[k];
+        for (int c = 0; c < 3; ++c) {
+            const float h = m.U[c * nm + k] - acc[c];
+            m.r0[c * nm + k] = h;
+            m.hl[c * nm + k] = h;
+            m.rec[k].hdS[c] = h * dS;
+        }
+        const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
+        const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k];
+        const float f0 = dS * (sxx * nx + sxy * ny + sxz * nz);
+        const float f1 = dS * (sxy * nx + syy * ny + syz * nz);
+        const float f2 = dS * (sxz * nx + syz * ny + szz * nz);
+        const float r0 = m.arm[k], r1 = m.arm[nm + k], r2 = m.arm[2 * nm + k];
+        m.ft[k] = f0;
+        m.ft[nm + k] = f1;
+        m.ft[2 * nm + k] = f2;
+        m.ft[3 * nm + k] = r1 * f2 - r2 * f1;
+        m.ft[4 * nm + k] = r2 * f0 - r0 * f2;
+        m.ft[5 * nm + k] = r0 * f1 - r1 * f0;
+    }
+}
+
+
 __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const MarkerArrays &m, const BoxArrays &ba,
                                               const int *__restrict__ wlist, const int *__restrict__ wcount,
                                               int cap, DevState *st, int k) {
@@ -255,46 +325,7 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MRec rk = m.rec[k];
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
-    if (warp == 0) {
-        const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
-        const float wxy = pick4(rk.wx, i) * pick4(rk.wy, j);
-        const float w0 = wxy * (kz ? rk.wz[1] : rk.wz[0]);
-        const float w1 = wxy * (kz ? rk.wz[3] : rk.wz[2]);
-        const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
-        const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
-        const size_t N = box.nbox;
-        float acc[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = w0 * ba.u[c * N + c0] + w1 * ba.u[c * N + c1];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
-#pragma unroll
-        for (int c = 0; c < 9; ++c)
-#pragma unroll
-            for (int q = 16; q > 0; q >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], q);
-        if (lane == 0) {
-            // l = 0: h_k = U_k - I[u*](X_k); traction dS sigma(X_k) n_k and its moment
-            const float dS = m.dS[k];
-            for (int c = 0; c < 3; ++c) {
-                const float h = m.U[c * nm + k] - acc[c];
-                m.r0[c * nm + k] = h;
-                m.hl[c * nm + k] = h;
-                m.rec[k].hdS[c] = h * dS;
-            }
-            const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
-            const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k];
-            const float f0 = dS * (sxx * nx + sxy * ny + sxz * nz);
-            const float f1 = dS * (sxy * nx + syy * ny + syz * nz);
-            const float f2 = dS * (sxz * nx + syz * ny + szz * nz);
-            const float r0 = m.arm[k], r1 = m.arm[nm + k], r2 = m.arm[2 * nm + k];
-            m.ft[k] = f0;
-            m.ft[nm + k] = f1;
-            m.ft[2 * nm + k] = f2;
-            m.ft[3 * nm + k] = r1 * f2 - r2 * f1;
-            m.ft[4 * nm + k] = r2 * f0 - r0 * f2;
-            m.ft[5 * nm + k] = r0 * f1 - r1 * f0;
-        }
-    }
+    if (warp == 0) interp_marker_warp(box, nm, m, ba, k, rk, lane);
     // ---- row k of A -----------------------------------------------------------
     const int tile = (bx / TILE) + box.tx * ((by / TILE) + box.ty * (bz / TILE));
     const int cnt = wcount[tile];
@@ -347,6 +378,139 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int 
                                                                 const int *__restrict__ wcount, int cap,
                                                                 DevState *st) {
     interp0_block(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x);
+}
+
+// The same step l = 0 and rows of A with one block per TILE^3 tile of the
+// support box, for batched launches (many markers, throughput-bound): the
+// block finds the markers whose stencil base lies in the tile (from the
+// tile's list 0, in marker order), interpolates each with one warp (the code
+// above), and builds their rows from the tile's list 1 staged once in shared
+// memory in chunks, one warp per marker and one candidate per lane with warp
+// ordered compaction.  Entries and their order equal those of interp0_block.
+constexpr int IT_MAXB = 256;   // markers based in one tile
+constexpr int IT_STAGE = 256;  // candidates staged per chunk
+
+__device__ __forceinline__ void interp0_tile_block(const BoxGeom &box, int nm, const MarkerArrays &m,
+                                                   const BoxArrays &ba, const int *__restrict__ tile_list,
+                                                   const int *__restrict__ tile_count, int cap, DevState *st,
+                                                   int tile) {
+    __shared__ int kb[IT_MAXB], klen[IT_MAXB];
+    __shared__ int wc[ROWS_WARPS];
+    __shared__ int nbased;
+    __shared__ int sidx[IT_STAGE], sbase[IT_STAGE];
+    // candidate weights per axis padded with three zeros on either side:
+    // sp[a][3 + e][j] = w_a[e] of candidate j, so the overlap at base offset d
+    // reads sp[a][i - d + 3] for i = 0..3 without branches; the padding adds
+    // fmaf(w, 0, o) = o exactly (all weights are non-negative)
+    __shared__ float sp[3][10][IT_STAGE];
+    __shared__ float sdS[IT_STAGE];
+    const int ntiles = box.tx * box.ty * box.tz;
+    const int c0 = tile_count[tile];
+    if (c0 == 0) return;  // no stencil overlaps the tile: no marker is based in it
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
+    const int *l0 = tile_list + (size_t)tile * cap;
+    if (tid == 0) nbased = 0;
+    __syncthreads();
+    for (int base = 0; base < c0; base += ROWS_THREADS) {
+        const int i = base + tid;
+        bool hit = false;
+        int k = 0;
+        if (i < c0) {
+            k = __ldg(l0 + i);
+            const int pb = __ldg(m.base + k);
+            hit = ((pb & 1023) / TILE == tx) && (((pb >> 10) & 1023) / TILE == ty) && (((pb >> 20) & 1023) / TILE == tz);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wc[warp] = __popc(bal);
+        __syncthreads();
+        int off = nbased;
+        for (int w = 0; w < warp; ++w) off += wc[w];
+        if (hit) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            if (pos < IT_MAXB) kb[pos] = k;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int sum = 0;
+            for (int w = 0; w < ROWS_WARPS; ++w) sum += wc[w];
+            nbased += sum;
+        }
+        __syncthreads();
+    }
+    const int nb = nbased < IT_MAXB ? nbased : IT_MAXB;
+    if (tid == 0 && nbased > IT_MAXB) atomicCAS(&st->status, 0, STAT_OVERFLOW);
+    if (nb == 0) return;
+    for (int q = warp; q < nb; q += ROWS_WARPS) {
+        const int k = kb[q];
+        const MRec rk = m.rec[k];
+        interp_marker_warp(box, nm, m, ba, k, rk, lane);
+    }
+    for (int q = tid; q < nb; q += ROWS_THREADS) klen[q] = 0;
+    for (int q = tid; q < 3 * 6 * IT_STAGE; q += ROWS_THREADS) {
+        const int a = q / (6 * IT_STAGE), r = (q / IT_STAGE) % 6, j = q % IT_STAGE;
+        sp[a][r < 3 ? r : r + 4][j] = 0.0f;
+    }
+    const int c1 = tile_count[ntiles + tile];
+    const int *l1 = tile_list + ((size_t)ntiles + tile) * cap;
+    for (int base = 0; base < c1; base += IT_STAGE) {
+        const int n = min(IT_STAGE, c1 - base);
+        __syncthreads();  // the previous chunk is consumed (and klen is set)
+        if (tid < n) {
+            const int j = __ldg(l1 + base + tid);
+            const MRec r = m.rec[j];
+            sidx[tid] = j;
+            sbase[tid] = r.base;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                sp[0][3 + e][tid] = r.wx[e];
+                sp[1][3 + e][tid] = r.wy[e];
+                sp[2][3 + e][tid] = r.wz[e];
+            }
+            sdS[tid] = m.dS[j];
+        }
+        __syncthreads();
+        for (int q = warp; q < nb; q += ROWS_WARPS) {
+            const int k = kb[q];
+            const MRec rk = m.rec[k];
+            const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
+            float *arow = m.aval + (size_t)k * ROWCAP;
+            int *irow = m.aidx + (size_t)k * ROWCAP;
+            int len = klen[q];
+            for (int s0 = 0; s0 < n; s0 += 32) {
+                const int jj = (s0 + lane < n) ? s0 + lane : 0;
+                const int pb = sbase[jj];
+                const int dx = (pb & 1023) - bx, dy = ((pb >> 10) & 1023) - by, dz = ((pb >> 20) & 1023) - bz;
+                const bool hit = (s0 + lane < n) && dx >= -3 && dx <= 3 && dy >= -3 && dy <= 3 && dz >= -3 && dz <= 3;
+                // the same fmaf sequence as overlap4, evaluated for every lane
+                const int ox = 3 - min(max(dx, -3), 3), oy = 3 - min(max(dy, -3), 3), oz = 3 - min(max(dz, -3), 3);
+                float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    fx = fmaf(rk.wx[i], sp[0][i + ox][jj], fx);
+                    fy = fmaf(rk.wy[i], sp[1][i + oy][jj], fy);
+                    fz = fmaf(rk.wz[i], sp[2][i + oz][jj], fz);
+                }
+                const float a = sdS[jj] * fx * fy * fz;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    const int pos = len + __popc(bal & ((1u << lane) - 1u));
+                    if (pos < ROWCAP) {
+                        arow[pos] = a;
+                        irow[pos] = sidx[jj];
+                    }
+                }
+                len += __popc(bal);
+            }
+            if (lane == 0) klen[q] = len;
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < nb; q += ROWS_THREADS) {
+        const int len = klen[q];
+        m.alen[kb[q]] = len < ROWCAP ? len : ROWCAP;
+        if (len > ROWCAP) atomicCAS(&st->status, 0, STAT_OVERFLOW);
+    }
 }
 
 // One cycle of steps l = 1..4 (Sec. 2.2) in matrix form:
@@ -509,13 +673,11 @@ __global__ void __launch_bounds__(PM_THREADS) k_batch_particle_markers(const Run
     pm_block(R.g, R.bc, R.box, R.st, p, 1, R.m, lb);
 }
 
-__global__ void __launch_bounds__(ROWS_THREADS) k_batch_interp0_rows(const RunDesc *__restrict__ runs,
-                                                                     const int *__restrict__ prefix, int nruns) {
+__global__ void __launch_bounds__(ROWS_THREADS) k_batch_interp0_tiles(const RunDesc *__restrict__ runs,
+                                                                      const int *__restrict__ prefix, int nruns) {
     int lb;
     const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
-    const int ntiles = R.box.tx * R.box.ty * R.box.tz;  // list 1 (rows of A) follows list 0
-    interp0_block(R.box, R.nm, R.m, R.ba, R.tile_list + (size_t)ntiles * R.cap, R.tile_count + ntiles, R.cap, R.st,
-                  lb);
+    interp0_tile_block(R.box, R.nm, R.m, R.ba, R.tile_list, R.tile_count, R.cap, R.st, lb);
 }
 
 __device__ __forceinline__ float *hsel(const MarkerArrays &m, int sel) {
@@ -575,7 +737,7 @@ cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays 
 }
 
 int blocks_particle_markers(const RunDesc &r) { return (r.nm + PM_THREADS - 1) / PM_THREADS; }
-int blocks_interp0(const RunDesc &r) { return r.nm; }
+int blocks_interp0(const RunDesc &r) { return r.box.tx * r.box.ty * r.box.tz; }
 int blocks_cycle(const RunDesc &r) { return (r.nm + INTERP_WARPS - 1) / INTERP_WARPS; }
 int blocks_spread(const RunDesc &r) { return r.box.tx * r.box.ty * r.box.tz; }
 
@@ -586,7 +748,7 @@ cudaError_t launch_batch_particle_markers(const RunDesc *runs, const int *prefix
 }
 
 cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s) {
-    k_batch_interp0_rows<<<nblocks, ROWS_THREADS, 0, s>>>(runs, prefix, nruns);
+    k_batch_interp0_tiles<<<nblocks, ROWS_THREADS, 0, s>>>(runs, prefix, nruns);
     return cudaGetLastError();
 }
 

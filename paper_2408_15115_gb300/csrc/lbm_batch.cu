@@ -90,16 +90,16 @@ __global__ void __launch_bounds__(MB_THREADS) k_batch_box_moments_bin(const RunD
     const int so = 1 - p;
     switch (R.storage) {
         case ST_F32:
-            mb_block<ST_F32>(g, (const float *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base,
-                             R.tile_list, R.tile_count, R.cap, R.st, lb);
+            mb_block<ST_F32>(g, (const float *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base, R.m.seg,
+                             R.tile_list, R.tile_count, R.cap, R.st, R.bc.rmin, R.bc.rmax, lb);
             break;
         case ST_F16:
-            mb_block<ST_F16>(g, (const __half *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base,
-                             R.tile_list, R.tile_count, R.cap, R.st, lb);
+            mb_block<ST_F16>(g, (const __half *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm, R.m.base, R.m.seg,
+                             R.tile_list, R.tile_count, R.cap, R.st, R.bc.rmin, R.bc.rmax, lb);
             break;
         default:
             mb_block<ST_BF16>(g, (const __nv_bfloat16 *)R.f[1 - p], R.utop[p], R.st, so, box, R.ba, nmom, R.nm,
-                              R.m.base, R.tile_list, R.tile_count, R.cap, R.st, lb);
+                              R.m.base, R.m.seg, R.tile_list, R.tile_count, R.cap, R.st, R.bc.rmin, R.bc.rmax, lb);
             break;
     }
 }

@@ -427,24 +427,59 @@ template <int ST>
 __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
                                          const float *__restrict__ utop_in, const DevState *__restrict__ st, int slot,
                                          const BoxGeom &box, const BoxArrays &ba, int nmom, int nm,
-                                         const int *__restrict__ mbase, int *__restrict__ tile_list,
-                                         int *__restrict__ tile_count, int cap, DevState *stw, int blk) {
+                                         const int *__restrict__ mbase, const int *__restrict__ mseg,
+                                         int *__restrict__ tile_list, int *__restrict__ tile_count, int cap,
+                                         DevState *stw, float rmin,
+                                         float rmax, int blk) {
     if (blk >= nmom) {
         constexpr int NW = MB_THREADS / 32;
         const int tile = blk - nmom;
         const int tx = tile % box.tx, ty = (tile / box.tx) % box.ty, tz = tile / (box.tx * box.ty);
         const int t0[3] = {TILE * tx, TILE * ty, TILE * tz};
-        __shared__ int wcount[2][NW];
-        __shared__ int total[2];
+        {
+            // Both lists hold markers whose stencil base b lies in [t0 - 3, t0 + 6]
+            // per axis, i.e. whose position X lies in [t0 - 2, t0 + 8).  Markers
+            // sit at rmin <= |X - C| <= rmax (body-frame radii, up to rounding):
+            // a region outside that shell has no candidates.
+            const BodySlot &S = st->s[slot];
+            float dmin2 = 0.0f, dmax2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float c = (float)(S.Ci[a] - S.box_lo[a]) + (float)S.Cf[a];
+                const float lo = (float)(t0[a] - 2), hi = (float)(t0[a] + 8);
+                const float dn = fmaxf(fmaxf(lo - c, c - hi), 0.0f);
+                const float dx = fmaxf(fabsf(c - lo), fabsf(c - hi));
+                dmin2 += dn * dn;
+                dmax2 += dx * dx;
+            }
+            const float margin = 0.25f;
+            if (dmin2 > (rmax + margin) * (rmax + margin) ||
+                (rmin > margin && dmax2 < (rmin - margin) * (rmin - margin))) {
+                if (threadIdx.x < 2) tile_count[threadIdx.x * (box.tx * box.ty * box.tz) + tile] = 0;
+                return;
+            }
+        }
+        // one barrier per chunk: the warp counts alternate between two buffers
+        __shared__ int wcount[2][2][NW];
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-        if (tid < 2) total[tid] = 0;
-        int pb = (tid < nm) ? __ldg(mbase + tid) : 0;
-        __syncthreads();
+        const int nseg = (nm + MARKER_SEG - 1) / MARKER_SEG;
+        int tot[2] = {0, 0};  // identical in every thread
+        int par = 0;
         for (int chunk = 0; chunk < nm; chunk += MB_THREADS) {
+            // skip chunks whose segments' stencil bases all miss [t0 - 3, t0 + 6]
+            bool reach = false;
+            for (int sg = chunk / MARKER_SEG; sg < nseg && sg * MARKER_SEG < chunk + MB_THREADS; ++sg) {
+                const int *bb = mseg + 6 * sg;
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) in = in && __ldg(bb + 3 + a) + 3 >= t0[a] && __ldg(bb + a) <= t0[a] + TILE + 2;
+                reach = reach || in;
+            }
+            if (!reach) continue;  // uniform over the block
             const int k = chunk + tid;
-            const int nxt = (k + MB_THREADS < nm) ? __ldg(mbase + k + MB_THREADS) : 0;  // prefetch
             bool hit[2] = {false, false};
             if (k < nm) {
+                const int pb = __ldg(mbase + k);
                 const int b[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
                 hit[0] = hit[1] = true;
 #pragma unroll
@@ -458,30 +493,28 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 bal[l] = __ballot_sync(0xffffffffu, hit[l]);
-                if (lane == 0) wcount[l][warp] = __popc(bal[l]);
+                if (lane == 0) wcount[par][l][warp] = __popc(bal[l]);
             }
             __syncthreads();
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                int off = total[l];
-                for (int w = 0; w < warp; ++w) off += wcount[l][w];
+                int off = tot[l], sum = 0;
+                for (int w = 0; w < NW; ++w) {
+                    const int c = wcount[par][l][w];
+                    off += (w < warp) ? c : 0;
+                    sum += c;
+                }
                 if (hit[l]) {
                     const int pos = off + __popc(bal[l] & ((1u << lane) - 1u));
                     if (pos < cap) tile_list[((size_t)l * (box.tx * box.ty * box.tz) + tile) * cap + pos] = k;
                 }
+                tot[l] += sum;
             }
-            __syncthreads();
-            if (tid < 2) {
-                int sum = 0;
-                for (int w = 0; w < NW; ++w) sum += wcount[tid][w];
-                total[tid] += sum;
-            }
-            __syncthreads();
-            pb = nxt;
+            par ^= 1;
         }
         if (tid < 2) {
-            tile_count[tid * (box.tx * box.ty * box.tz) + tile] = total[tid] < cap ? total[tid] : cap;
-            if (total[tid] > cap) atomicCAS(&stw->status, 0, STAT_OVERFLOW);
+            tile_count[tid * (box.tx * box.ty * box.tz) + tile] = tot[tid] < cap ? tot[tid] : cap;
+            if (tot[tid] > cap) atomicCAS(&stw->status, 0, STAT_OVERFLOW);
         }
         return;
     }

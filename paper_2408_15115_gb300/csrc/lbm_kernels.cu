@@ -78,9 +78,12 @@ __global__ void __launch_bounds__(MB_THREADS) k_box_moments_bin(Geom g, const ty
                                                                 const DevState *__restrict__ st, int slot, BoxGeom box,
                                                                 BoxArrays ba, int nmom, int nm,
                                                                 const int *__restrict__ mbase,
+                                                                const int *__restrict__ mseg,
                                                                 int *__restrict__ tile_list,
-                                                                int *__restrict__ tile_count, int cap, DevState *stw) {
-    mb_block<ST>(g, src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw, blockIdx.x);
+                                                                int *__restrict__ tile_count, int cap, DevState *stw,
+                                                                float rmin, float rmax) {
+    mb_block<ST>(g, src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax,
+                 blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -143,14 +146,14 @@ cudaError_t launch_macro(const Geom &g, int storage, const void *src, const floa
 
 cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
                                    const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
-                                   const int *mbase, int *tile_list, int *tile_count, int cap, DevState *stw,
-                                   cudaStream_t s) {
+                                   const int *mbase, const int *mseg, int *tile_list, int *tile_count, int cap,
+                                   DevState *stw, float rmin, float rmax, cudaStream_t s) {
     const int nmom = (int)((box.nbox + MB_THREADS - 1) / MB_THREADS);
     const unsigned nb = (unsigned)(nmom + box.tx * box.ty * box.tz);
     switch (storage) {
-        case ST_F32: k_box_moments_bin<ST_F32><<<nb, MB_THREADS, 0, s>>>(g, (const float *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
-        case ST_F16: k_box_moments_bin<ST_F16><<<nb, MB_THREADS, 0, s>>>(g, (const __half *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
-        default: k_box_moments_bin<ST_BF16><<<nb, MB_THREADS, 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, tile_list, tile_count, cap, stw); break;
+        case ST_F32: k_box_moments_bin<ST_F32><<<nb, MB_THREADS, 0, s>>>(g, (const float *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
+        case ST_F16: k_box_moments_bin<ST_F16><<<nb, MB_THREADS, 0, s>>>(g, (const __half *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
+        default: k_box_moments_bin<ST_BF16><<<nb, MB_THREADS, 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
     }
     return cudaGetLastError();
 }

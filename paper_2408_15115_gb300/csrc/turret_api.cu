@@ -340,18 +340,22 @@ static bool inverse3(const double *A, double *B) {
 struct IbmLayout {
     BoxGeom box;
     int nm, cap, rc;
+    double rmin, rmax;
 };
 
 // Support box: every marker lies within rc = ceil(bounding radius) of C_m,
 // so all 4x4x4 stencils fit a cube of 2 rc + 6 cells placed at floor(C) - rc - 2.
 static bool ibm_layout(const MeshProps &mp, const double *V, int64_t nv, IbmLayout &L) {
     if (nv <= 0 || nv >= (1 << 24)) return false;
-    double rb = 0.0;
+    double rb = 0.0, rs = INFINITY;
     for (int64_t k = 0; k < nv; ++k) {
         double s = 0.0;
         for (int a = 0; a < 3; ++a) s += (V[3 * k + a] - mp.com[a]) * (V[3 * k + a] - mp.com[a]);
         rb = fmax(rb, sqrt(s));
+        rs = fmin(rs, sqrt(s));
     }
+    L.rmin = rs;
+    L.rmax = rb;
     L.rc = (int)ceil(rb + 1e-6);
     const int B = 2 * L.rc + 6;
     L.box.Bx = L.box.By = L.box.Bz = B;
@@ -381,6 +385,7 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     m.aval = (float *)cv.take(nm * (size_t)ROWCAP * 4);
     m.aidx = (int *)cv.take(nm * (size_t)ROWCAP * 4);
     m.alen = (int *)cv.take(nm * 4);
+    m.seg = (int *)cv.take(6 * ((nm + MARKER_SEG - 1) / MARKER_SEG) * 4);
     BoxArrays ba;
     ba.u = (float *)cv.take(3 * nb * 4);
     ba.s = (float *)cv.take(6 * nb * 4);
@@ -419,8 +424,8 @@ static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float
     const int so = advance ? (slot ^ 1) : slot;
     const bool branch = (s == c->side);  // reduce F, T on the aux branch
     CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, slot, advance, c->mk, s));
-    CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base,
-                              c->tile_list, c->tile_count, c->cap, c->dstate, s));
+    CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base, c->mk.seg,
+                              c->tile_list, c->tile_count, c->cap, c->dstate, c->body.rmin, c->body.rmax, s));
     CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, s));
     if (branch) {
         CE(cudaEventRecord(c->ev_red, s));
@@ -524,6 +529,8 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     B.slide = c->win.slide;
     B.nm = L.nm;
     B.rc = L.rc;
+    B.rmin = (float)L.rmin;
+    B.rmax = (float)L.rmax;
     // static marker data (body frame): offsets from C_m, normals, areas
     const size_t nm = (size_t)L.nm;
     c->staging.assign(7 * nm, 0.0f);

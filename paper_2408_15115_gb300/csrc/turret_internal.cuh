@@ -83,11 +83,16 @@ struct BodyConst {
     int rot_form, renorm, slide;
     int nm;            // markers
     int rc;            // ceil of the bounding radius of the markers about C_m
+    float rmin, rmax;  // smallest and largest marker distance from C_m
 };
 
 // Per-marker record read by the transfer kernels (64 bytes, one per marker):
 // packed stencil base in support-box coordinates (x | y << 10 | z << 20), the
 // 12 one-dimensional Peskin weights (x0..3, y0..3, z0..3) and h_k dS_k.
+// Markers are processed in segments of MARKER_SEG consecutive markers (one
+// block of the marker kernel); each segment's stencil bases have a bounding box.
+constexpr int MARKER_SEG = 128;
+
 struct __align__(16) MRec {
     int base;
     float wx[4], wy[4], wz[4];
@@ -110,6 +115,8 @@ struct MarkerArrays {
     float *aval;       // [nm][ROWCAP] A_kj = dS_j sum_x W(x - X_k) W(x - X_j)
     int *aidx;         // [nm][ROWCAP] column j of each entry, in marker order
     int *alen;         // [nm] entries per row
+    int *seg;          // [ceil(nm / MARKER_SEG)][6] per segment of MARKER_SEG consecutive
+                       // markers: min x, y, z then max x, y, z of the stencil bases
 };
 
 struct BoxArrays {
@@ -210,10 +217,12 @@ bool is_batch_bulk_kernel(const void *fn);
 cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
                                          cudaStream_t s);
 // Support-box moments (u*, sigma) and the tile candidate lists, one launch.
+// Tiles that no marker can reach (outside the shell rmin <= |X - C_m| <= rmax
+// grown by the stencil reach) get empty lists without a scan.
 cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
                                    const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
-                                   const int *mbase, int *tile_list, int *tile_count, int cap, DevState *stw,
-                                   cudaStream_t s);
+                                   const int *mbase, const int *mseg, int *tile_list, int *tile_count, int cap,
+                                   DevState *stw, float rmin, float rmax, cudaStream_t s);
 
 // Launchers (ibm_kernels.cu).
 // Rigid-body update t -> t+1 (advance = 1; reads window slot `slot`, writes

@@ -1,0 +1,92 @@
+"""Reduced-precision population storage (FP16 / BF16 deviations from the
+weights, FP32 arithmetic, FP64 reductions and rigid-body update): drag,
+settling velocity and trajectory against the FP64 oracle and against FP32
+storage, and the mixed-storage batched ensemble against the plain FP32 form."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2408_15115_gb300 import configs
+from paper_2408_15115_gb300 import inputs as I
+
+from cases import make_pair
+
+pytestmark = pytest.mark.gpu
+
+# drag and settling-velocity bar of the reduced-precision and batched forms
+TOL_REDUCED = 1e-2
+
+
+def _history(step_fn, state_fn, nsteps, every):
+    rows = []
+    for _ in range(nsteps // every):
+        step_fn(every)
+        s = state_fn()
+        rows.append((s["F"][2], s["v"][2], s["r"][2]))
+    return np.array(rows)
+
+
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+@pytest.mark.slow
+def test_sphere_box_storage_vs_oracle():
+    # the 32x32x64 closed-box sphere (d = 8, 252 markers) from rest, 400 steps:
+    # time-averaged drag and settling velocity over the second half, and the
+    # fall distance, for every storage type against the FP64 oracle
+    V, T = I.sphere(5, 8.0)
+    O.set_threads(0)
+    hist = {}
+    sim = None
+    for st in ("f32", "f16", "bf16"):
+        t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), storage=st,
+                         particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
+        hist[st] = _history(t.step, t.state, 400, 10)
+        if sim is None:
+            sim = s
+        t.close()
+    ref = _history(sim.step, sim.state, 400, 10)
+    half = slice(20, 40)
+    for st, tol in (("f32", 5e-3), ("f16", TOL_REDUCED), ("bf16", TOL_REDUCED)):
+        h = hist[st]
+        assert _rel(h[half, 0].mean(), ref[half, 0].mean()) < tol, (st, "drag")
+        assert _rel(h[half, 1].mean(), ref[half, 1].mean()) < tol, (st, "settling velocity")
+        fall, fall_ref = h[-1, 2] - 44.0, ref[-1, 2] - 44.0
+        assert _rel(fall, fall_ref) < tol, (st, "fall distance")
+
+
+def _ensemble_cfgs():
+    # four 64^3 sliding turret windows: sphere, oblate, prolate, irregular
+    spec = [("sphere", 10.0, 20.0), ("oblate", 12.0, 5.0), ("prolate", 10.0, 40.0), ("irregular", 12.0, 10.0)]
+    return [configs.ensemble_member(sh, d, re, (64, 64, 64), "f32", seed=100 + k)
+            for k, (sh, d, re) in enumerate(spec)]
+
+
+def test_mixed_batched_ensemble_vs_plain_f32():
+    # plain form: FP32 storage, each run alone; batched form: one launch per
+    # phase for all runs with FP16 / BF16 storage.  Time-averaged drag and
+    # settling velocity over steps 1000..2000 within 1 %.
+    from paper_2408_15115_gb300 import turret as T
+    cfgs = _ensemble_cfgs()
+    plain = configs.load_ensemble(cfgs)
+    ref = [_history(t.step, t.state, 2000, 50) for t in plain]
+    for t in plain:
+        t.close()
+    for st in ("f16", "bf16"):
+        runs = configs.load_ensemble([dict(c, storage=st) for c in cfgs])
+        b = T.Batch(runs)
+        hist = [[] for _ in runs]
+        for _ in range(2000 // 50):
+            b.step(50)
+            for k, t in enumerate(runs):
+                s = t.state()
+                hist[k].append((s["F"][2], s["v"][2], s["r"][2]))
+        b.close()
+        for k, c in enumerate(cfgs):
+            h, r = np.array(hist[k]), ref[k]
+            late = slice(20, 40)
+            assert _rel(h[late, 0].mean(), r[late, 0].mean()) < TOL_REDUCED, (st, c["name"], "drag")
+            assert _rel(h[late, 1].mean(), r[late, 1].mean()) < TOL_REDUCED, (st, c["name"], "velocity")
+        for t in runs:
+            t.close()
