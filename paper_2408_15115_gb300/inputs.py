@@ -177,3 +177,20 @@ def random_state(shape, u_amp=0.01, rho_amp=0.001, kmax=4, seed=1):
     u = smooth_field(shape, 3, u_amp, kmax, seed)
     drho = smooth_field(shape, 1, rho_amp, kmax, seed + 1000)[..., 0]
     return 1.0 + drho, u
+
+
+# --------------------------------------------------------------------------
+# Seeded initial weights of the force/torque surrogate network (34 -> 3 x 128
+# -> 6, flat layout W1 b1 W2 b2 W3 b3 W4 b4): normal weights with variance
+# 2 / fan_in (He et al. 2015), zero biases, returned as float64.
+
+MLP_LAYERS = ((128, 34), (128, 128), (128, 128), (6, 128))
+
+
+def mlp_init_params(seed=0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for n_out, n_in in MLP_LAYERS:
+        parts.append(rng.standard_normal(n_out * n_in) * math.sqrt(2.0 / n_in))
+        parts.append(np.zeros(n_out))
+    return np.concatenate(parts)
