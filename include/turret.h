@@ -277,6 +277,124 @@ TURRET_API const char *turret_batch_last_error(const turret_batch *b);
 TURRET_API turret_status turret_time_collide(turret_ctx *c, int32_t threads, int32_t tx, int32_t minb, int32_t reps,
                                              float *us_out);
 
+/* ---- force/torque surrogate network ------------------------------------------ */
+
+/* A small multilayer perceptron that predicts the particle's next
+ * hydrodynamic force and torque from its recent state; the paper has no
+ * counterpart (its only predictor is the orientation predictor-corrector of
+ * Sec. 2.3).  Architecture: TURRET_MLP_IN = 34 inputs -> three hidden layers
+ * of 128 units with the exact GELU x Phi(x) -> TURRET_MLP_OUT = 6 outputs,
+ * applied to standardised inputs (x - mean_x) / std_x; outputs are
+ * standardised targets, returned de-standardised.  Parameters are a flat
+ * float array of TURRET_MLP_NPARAM values: W1 [128][34], b1 [128],
+ * W2 [128][128], b2 [128], W3 [128][128], b3 [128], W4 [6][128], b4 [6]
+ * (row-major, y = W x + b per layer).  precision 0: matrix products on BF16
+ * tensor cores (weights and activations rounded to BF16, FP32 accumulation);
+ * precision 1: FP32 throughout (a check mode).  Training: mean squared error
+ * of the standardised outputs, AdamW with decoupled weight decay on the
+ * weight matrices.  All calls run on the stream given to mlp_init.         */
+#define TURRET_MLP_IN 34
+#define TURRET_MLP_OUT 6
+#define TURRET_MLP_NPARAM 38278
+typedef struct turret_mlp turret_mlp;
+typedef struct {
+    float lr, beta1, beta2, eps, weight_decay;
+} turret_adamw;
+
+/* Device workspace for a network trained on batches of up to batch_cap rows
+ * (0 for batch_cap outside 1 .. 2^20).                                      */
+TURRET_API size_t mlp_workspace_bytes(int32_t batch_cap);
+/* Creates a network with the host parameters `params` [TURRET_MLP_NPARAM],
+ * identity standardisation and zero optimiser moments; waits.               */
+TURRET_API turret_status mlp_init(turret_mlp **out, int32_t batch_cap, int32_t precision, const float *params,
+                                  void *device_workspace, size_t workspace_bytes, void *stream);
+/* Copies parameters from / to the host; wait.                               */
+TURRET_API turret_status mlp_set_params(turret_mlp *m, const float *params);
+TURRET_API turret_status mlp_get_params(turret_mlp *m, float *params);
+/* Sets the standardisation (host arrays of 34, 34, 6, 6 floats; std > 0).   */
+TURRET_API turret_status mlp_set_norm(turret_mlp *m, const float *mean_x, const float *std_x, const float *mean_y,
+                                      const float *std_y);
+/* y [n][6] = network(x [n][34]), device arrays, 1 <= n <= batch_cap, with the
+ * training kernels (batched matrix products).  Asynchronous.               */
+TURRET_API turret_status mlp_forward(turret_mlp *m, const float *x, int32_t n, float *y);
+/* The same outputs from the fused inference kernel (16 rows per block, any
+ * n >= 1), as used by the particle predictor.  Asynchronous.               */
+TURRET_API turret_status mlp_infer(turret_mlp *m, const float *x, int32_t n, float *y);
+/* Loss of raw targets y [n][6] and, if grad is not NULL, its gradient with
+ * respect to the parameters into device memory grad [TURRET_MLP_NPARAM].
+ * Waits.                                                                    */
+TURRET_API turret_status mlp_loss_grad(turret_mlp *m, const float *x, const float *y, int32_t n, float *loss,
+                                       float *grad);
+/* One AdamW step on the batch (x, y); the loss before the step to *loss if
+ * loss is not NULL (then waits).                                            */
+TURRET_API turret_status mlp_train_step(turret_mlp *m, const float *x, const float *y, int32_t n,
+                                        const turret_adamw *opt, float *loss);
+/* Releases the network (not the workspace).                                 */
+TURRET_API turret_status mlp_destroy(turret_mlp *m);
+TURRET_API const char *mlp_last_error(const turret_mlp *m);
+
+/* ---- force/torque predictor (surrogate modes) -------------------------------- */
+
+/* The paper's step (mode 0, the default) forms the marker target velocities
+ * U_k from v, w at t + 1/2 and runs ibm_cycles IBM cycles from h = 0.  The
+ * predictor modes, which the paper does not have, predict the force and
+ * torque of the next time level -- mode 1 by linear extrapolation
+ * 2 F(t) - F(t-1), mode 2 by the network `net` (kept by the caller; it
+ * corrects the linear extrapolation, see mlp_build_samples) with linear
+ * extrapolation as its fallback: in mode 2 the network runs at every step
+ * once four time levels of history exist, and its prediction is used unless
+ * its previous one missed the force by |F - F^| / |F| > resid_theta.
+ * options (bits):
+ *   TURRET_PRED_VEL:  form U_k from the estimates
+ *       v(t+1) = v(t+1/2) + (g_eff + F^/m) / 2 and L(t+1) = L(t+1/2) + T^/2
+ *       (w(t+1) = w(t+1/2) + (J/m)^-1 T^/(2m) in the literal rotation form);
+ *   TURRET_PRED_WARM: start the IBM cycles from the previous step's
+ *       Lagrangian force and run at most ibm_cycles of them, skipping the
+ *       rest once the slip max_k |U_k - I[u* + S h](X_k)| is below slip_eps.
+ * Takes effect for the following steps (a batch copies it when created).    */
+#define TURRET_PRED_WARM 1
+#define TURRET_PRED_VEL 2
+TURRET_API turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const turret_mlp *net, int32_t options,
+                                              double slip_eps, double resid_theta);
+
+/* Trajectory log: after the force of each time level j is known, record
+ * (n mod capacity), n the count of records written so far, of the caller's
+ * device array records [capacity][TURRET_LOG_REC] doubles receives d(j) [9]
+ * (rows of the orientation matrix), v(j - 1/2) [3], w(j - 1/2) [3], F(j)
+ * [3], T(j) [3], j, the relative error |F - F^| / |F| of the prediction made
+ * for j (or -1), F^ [3], T^ [3], 1 if the network made it (0 linear, -1 no
+ * prediction), the relative error of the network's prediction for j (or -1:
+ * the network did not run), 0.  capacity 0 detaches the log.               */
+#define TURRET_LOG_REC 32
+TURRET_API turret_status turret_set_log(turret_ctx *c, double *records, int64_t capacity);
+
+typedef struct {
+    int64_t steps;      /* predictions made                                   */
+    int64_t net_steps;  /* ... of them by the network                          */
+    int64_t fallbacks;  /* linear predictions made in network mode             */
+    int64_t cycles;     /* IBM cycles run in the predictor modes               */
+    int64_t logged;     /* trajectory records written                          */
+    double resid;       /* |F - F^| / |F| of the last checked prediction       */
+    double slip[8];     /* slip seen by each IBM cycle of the last step        */
+    int32_t hist_n, fallback;
+} turret_predictor_stats;
+
+/* Counters of the predictor (waits for the stream).                        */
+TURRET_API turret_status turret_query_predictor(turret_ctx *c, turret_predictor_stats *out);
+
+/* Training pairs of the network from n_records consecutive records of a
+ * trajectory log (device): sample j (0 <= j < n_records - 4) is built at
+ * t = record j + 3, in the body frame M of t.  Inputs x [j][34]: quaternion
+ * (w >= 0) of M, M v, M w, then M F / sF, M T / sT of records t, t - 1,
+ * t - 2, t - 3, with sF, sT the largest of those four force and torque
+ * magnitudes.  Targets y [j][6]: M (F(t+1) - 2 F(t) + F(t-1)) / sF and the
+ * torque alike -- the departure from linear extrapolation, which the
+ * predictor adds back (F^ = 2 F(t) - F(t-1) + sF M^T y).  Records whose time
+ * levels are not consecutive give NaN inputs and are counted in the device
+ * integer *bad.  Asynchronous on `stream`.                                 */
+TURRET_API turret_status mlp_build_samples(const double *records, int64_t n_records, float *x, float *y, int32_t *bad,
+                                           void *stream);
+
 /* Releases the context (not the caller's workspaces).                       */
 TURRET_API turret_status lbm_destroy(turret_ctx *c);
 

@@ -129,3 +129,80 @@ def standardisation(data):
     sd = data.std(0)
     sd[sd == 0.0] = 1.0
     return mu, sd
+
+
+# --------------------------------------------------------------------------
+# Predictor features (the network's inputs), from the particle state at time
+# level t with orientation matrix M (rows d_0, d_1, d_2: the body axes):
+#   quaternion (w, x, y, z), w >= 0, of M; M v; M w; M F(t-h) / sF,
+#   M T(t-h) / sT for h = 0..3, sF = max_h |F(t-h)|, sT = max_h |T(t-h)|.
+# Targets: M (F(t+1) - 2 F(t) + F(t-1)) / sF and the torque alike -- the
+# departure from linear extrapolation -- so F^ = 2 F(t) - F(t-1) + sF M^T y.
+
+def quaternion(M):
+    """Unit quaternion (w, x, y, z), w >= 0, with rotation matrix M.  The
+    products q q^T are linear in M (the matrix entries of a unit quaternion's
+    rotation are quadratic in q), so q is the principal eigenvector of that
+    4 x 4 matrix."""
+    M = np.asarray(M, dtype=np.float64).reshape(3, 3)
+    tr = np.trace(M)
+    Q = 0.25 * np.array([
+        [1 + tr, M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]],
+        [M[2, 1] - M[1, 2], 1 + M[0, 0] - M[1, 1] - M[2, 2], M[0, 1] + M[1, 0], M[0, 2] + M[2, 0]],
+        [M[0, 2] - M[2, 0], M[0, 1] + M[1, 0], 1 - M[0, 0] + M[1, 1] - M[2, 2], M[1, 2] + M[2, 1]],
+        [M[1, 0] - M[0, 1], M[0, 2] + M[2, 0], M[1, 2] + M[2, 1], 1 - M[0, 0] - M[1, 1] + M[2, 2]]])
+    w, V = np.linalg.eigh(Q)
+    q = V[:, np.argmax(w)]
+    q = q / np.linalg.norm(q)
+    return -q if q[0] < 0 else q
+
+
+def scales(Fh, Th):
+    sF = max(float(np.linalg.norm(f)) for f in Fh) or 1.0
+    sT = max(float(np.linalg.norm(t)) for t in Th) or 1.0
+    return sF, sT
+
+
+def features(M, v, w, Fh, Th):
+    """Inputs of the network: Fh, Th = lab-frame forces and torques at t, t-1,
+    t-2, t-3 (newest first)."""
+    M = np.asarray(M, dtype=np.float64).reshape(3, 3)
+    sF, sT = scales(Fh, Th)
+    out = [quaternion(M), M @ np.asarray(v, float), M @ np.asarray(w, float)]
+    for h in range(4):
+        out += [M @ np.asarray(Fh[h], float) / sF, M @ np.asarray(Th[h], float) / sT]
+    return np.concatenate(out)
+
+
+def target(M, Fh, Th, F_next, T_next):
+    M = np.asarray(M, dtype=np.float64).reshape(3, 3)
+    sF, sT = scales(Fh, Th)
+    lin_F = 2 * np.asarray(Fh[0], float) - np.asarray(Fh[1], float)
+    lin_T = 2 * np.asarray(Th[0], float) - np.asarray(Th[1], float)
+    return np.concatenate([M @ (np.asarray(F_next, float) - lin_F) / sF, M @ (np.asarray(T_next, float) - lin_T) / sT])
+
+
+def prediction(M, Fh, Th, y):
+    """Lab-frame (F^, T^) from the network's outputs y [6]."""
+    M = np.asarray(M, dtype=np.float64).reshape(3, 3)
+    sF, sT = scales(Fh, Th)
+    return (2 * np.asarray(Fh[0], float) - np.asarray(Fh[1], float) + sF * (M.T @ y[:3]),
+            2 * np.asarray(Th[0], float) - np.asarray(Th[1], float) + sT * (M.T @ y[3:]))
+
+
+LOG_REC = 32
+
+
+def samples(log):
+    """(x [n-4][34], y [n-4][6]) from n consecutive trajectory records
+    [n][32] (d [9], v [3], w [3], F [3], T [3], step, ...)."""
+    log = np.asarray(log, dtype=np.float64)
+    xs, ys = [], []
+    for j in range(log.shape[0] - 4):
+        t = j + 3
+        M = log[t, 0:9].reshape(3, 3)
+        Fh = [log[t - h, 15:18] for h in range(4)]
+        Th = [log[t - h, 18:21] for h in range(4)]
+        xs.append(features(M, log[t, 9:12], log[t, 12:15], Fh, Th))
+        ys.append(target(M, Fh, Th, log[t + 1, 15:18], log[t + 1, 18:21]))
+    return np.array(xs), np.array(ys)

@@ -38,14 +38,14 @@ struct turret_batch {
     int n;
     std::vector<turret_ctx *> ctx;
     cudaStream_t stream, side, aux;
-    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done, ev_done;
+    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done, ev_done, ev_pred;
     std::vector<cudaEvent_t> ev_ctx;  // one per run: the work already on its context's stream
     RunDesc *d_runs;
     int *d_prefix;                    // T_COUNT tables of n + 1 ints
     std::vector<RunDesc> h_runs;
     std::vector<int> h_prefix;
     int total[T_COUNT];
-    int threads, minb, cycles;
+    int threads, minb, cycles, predictor, warm;
     long long step;
     cudaGraphExec_t graph[2];
     bool graph_ready[2];
@@ -123,7 +123,7 @@ static void release_batch(turret_batch *b) {
     drop_batch_graphs(b);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->aux) cudaStreamDestroy(b->aux);
-    cudaEvent_t evs[5] = {b->ev_fork, b->ev_join, b->ev_red, b->ev_red_done, b->ev_done};
+    cudaEvent_t evs[6] = {b->ev_fork, b->ev_join, b->ev_red, b->ev_red_done, b->ev_done, b->ev_pred};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_ctx)
@@ -146,6 +146,10 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
         if ((c->step & 1) != (ctxs[0]->step & 1)) return bfail(b, TURRET_ESTATE, "runs at time levels of different parity");
         if (c->flags.ibm_cycles != ctxs[0]->flags.ibm_cycles)
             return bfail(b, TURRET_EINVAL, "runs with different ibm_cycles");
+        if ((c->body.predictor != 0) != (ctxs[0]->body.predictor != 0))
+            return bfail(b, TURRET_EINVAL, "runs with and without a force predictor");
+        if (c->body.predictor != 0 && ((c->body.pred_opts ^ ctxs[0]->body.pred_opts) & PRED_WARM))
+            return bfail(b, TURRET_EINVAL, "runs with and without warm-started IBM cycles");
     }
     if (!ws || ws_bytes < turret_batch_workspace_bytes(n)) return bfail(b, TURRET_ENOMEM, "batch workspace too small");
     if (((uintptr_t)ws & 255) != 0) return bfail(b, TURRET_EINVAL, "workspace must be 256-byte aligned");
@@ -155,13 +159,15 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
     b->ctx.assign(ctxs, ctxs + n);
     b->stream = (cudaStream_t)stream;
     b->side = b->aux = nullptr;
-    b->ev_fork = b->ev_join = b->ev_red = b->ev_red_done = b->ev_done = nullptr;
+    b->ev_fork = b->ev_join = b->ev_red = b->ev_red_done = b->ev_done = b->ev_pred = nullptr;
     b->graph_ready[0] = b->graph_ready[1] = false;
     b->d_runs = (RunDesc *)ws;
     b->d_prefix = (int *)((char *)ws + prefix_offset(n));
     b->threads = 128;
     b->minb = 3;
     b->cycles = ctxs[0]->flags.ibm_cycles;
+    b->predictor = ctxs[0]->body.predictor != 0 ? 1 : 0;
+    b->warm = (b->predictor && (ctxs[0]->body.pred_opts & PRED_WARM)) ? 1 : 0;
     b->step = ctxs[0]->step;
     b->h_runs.resize(n);
     for (int r = 0; r < n; ++r) {
@@ -185,6 +191,8 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
         R.nm = c->nm;
         R.split = c->split ? 1 : 0;
         R.tx = 32;
+        const MlpDev *net = mlp_device_view(c->net);
+        if (c->body.predictor == 2 && net) R.mlp = *net;
     }
     if (!build_tables(b)) {
         release_batch(b);
@@ -194,7 +202,7 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->aux, cudaStreamNonBlocking, hi);
-    cudaEvent_t *evs[5] = {&b->ev_fork, &b->ev_join, &b->ev_red, &b->ev_red_done, &b->ev_done};
+    cudaEvent_t *evs[6] = {&b->ev_fork, &b->ev_join, &b->ev_red, &b->ev_red_done, &b->ev_done, &b->ev_pred};
     for (cudaEvent_t *ev : evs)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     b->ev_ctx.assign(n, nullptr);
@@ -244,22 +252,40 @@ static cudaError_t batch_enqueue(turret_batch *b, int p) {
     const RunDesc *R = b->d_runs;
     CE(cudaEventRecord(b->ev_fork, b->stream));
     CE(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    if (b->predictor) {  // the predictions overlap the near collide+stream
+        CE(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+        CE(launch_batch_predict(R, n, p, b->aux));
+        CE(cudaEventRecord(b->ev_pred, b->aux));
+    }
     CE(launch_batch_collide(PHASE_BULK, R, tab(T_BULK), n, p, b->total[T_BULK], b->threads, b->minb, b->stream));
     CE(launch_batch_collide(PHASE_NEAR, R, tab(T_NEAR), n, p, b->total[T_NEAR], b->threads, 1, b->side));
+    if (b->predictor) CE(cudaStreamWaitEvent(b->side, b->ev_pred, 0));
     CE(launch_batch_particle_markers(R, tab(T_PM), n, p, b->total[T_PM], b->side));
     CE(launch_batch_box_moments_bin(R, tab(T_MB), n, p, b->total[T_MB], b->side));
-    CE(launch_batch_interp0(R, tab(T_IP), n, b->total[T_IP], b->side));
+    CE(launch_batch_interp0(R, tab(T_IP), n, b->total[T_IP], b->warm, b->side));
     CE(cudaEventRecord(b->ev_red, b->side));
     CE(cudaStreamWaitEvent(b->aux, b->ev_red, 0));
-    CE(launch_batch_reduce_ft(R, n, b->aux));
+    CE(launch_batch_reduce_ft(R, n, p ^ 1, b->aux));
     CE(cudaEventRecord(b->ev_red_done, b->aux));
-    // cycles 1 .. n-1 read r0, then alternate so that the last one writes hl
-    const int C = b->cycles - 1;
-    int src = HSEL_R0;
-    for (int cyc = 1; cyc <= C; ++cyc) {
-        const int dst = ((C - cyc) % 2 == 0) ? HSEL_HL : HSEL_HB;
-        CE(launch_batch_cycle(R, tab(T_CYC), n, b->total[T_CYC], src, dst, cyc == C, b->side));
-        src = dst;
+    if (!b->warm) {
+        // the paper's cycles: h^0 = r0, then 1 .. n-1 alternating so that the last writes hl
+        const int C = b->cycles - 1;
+        int src = HSEL_R0;
+        for (int cyc = 1; cyc <= C; ++cyc) {
+            const int dst = ((C - cyc) % 2 == 0) ? HSEL_HL : HSEL_HB;
+            CE(launch_batch_cycle(R, tab(T_CYC), n, b->total[T_CYC], src, dst, -1, cyc == C, cyc - 1, 0, b->side));
+            src = dst;
+        }
+    } else {
+        // predictor modes: up to n adaptive cycles from the previous h
+        const int C = b->cycles;
+        int src = HSEL_HL;
+        for (int cyc = 1; cyc <= C; ++cyc) {
+            const int dst = (cyc % 2 == 1) ? HSEL_HB : HSEL_HL;
+            const int fin = (cyc == C && dst != HSEL_HL) ? HSEL_HL : -1;
+            CE(launch_batch_cycle(R, tab(T_CYC), n, b->total[T_CYC], src, dst, fin, cyc == C, cyc - 1, 1, b->side));
+            src = dst;
+        }
     }
     CE(launch_batch_spread(R, tab(T_SP), n, b->total[T_SP], b->side));
     CE(cudaStreamWaitEvent(b->side, b->ev_red_done, 0));

@@ -144,16 +144,45 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
                 S.step += 1;
             }
             __syncwarp();
+            if (blk == 0 && lane < 8) st->pr.slip[lane] = 0u;
             if (blk == 0) {
                 int *gdst = reinterpret_cast<int *>(&st->s[so]);
                 const int *ssrc = reinterpret_cast<const int *>(&S);
                 for (int q = lane; q < (int)(sizeof(BodySlot) / 4); q += 32) gdst[q] = ssrc[q];
             }
         }
+        // marker velocities: v, w at t + 1/2 (the paper's step), or in the
+        // predictor modes their estimates at t + 1 from the predicted force
+        // and torque, v^ = v + (g_eff + F^ / m) / 2, L^ = L + T^ / 2 (or
+        // w^ = w + (J/m)^-1 T^ / (2 m) in the literal rotation form)
+        const bool pred = advance && bc.predictor != 0 && (bc.pred_opts & PRED_VEL) && st->pr.predicted;
+        if (pred) {
+            if (lane < 3) {
+                s_src[lane] = st->pr.That[lane];
+                s_F[lane] = S.v[lane] + 0.5 * (bc.g_eff[lane] + st->pr.Fhat[lane] * bc.inv_mass);
+            }
+            __syncwarp();
+            if (lane < 3) {
+                const double src = (bc.rot_form == 1) ? s_src[0] : S.L[0] + 0.5 * s_src[0];
+                const double src1 = (bc.rot_form == 1) ? s_src[1] : S.L[1] + 0.5 * s_src[1];
+                const double src2 = (bc.rot_form == 1) ? s_src[2] : S.L[2] + 0.5 * s_src[2];
+                s_sb[lane] = S.d[3 * lane] * src + S.d[3 * lane + 1] * src1 + S.d[3 * lane + 2] * src2;
+            }
+            __syncwarp();
+            if (lane < 3)
+                s_wb[lane] = bc.Jinv_b[3 * lane] * s_sb[0] + bc.Jinv_b[3 * lane + 1] * s_sb[1] +
+                             bc.Jinv_b[3 * lane + 2] * s_sb[2];
+            __syncwarp();
+            if (lane < 3) {
+                const double wl = S.d[lane] * s_wb[0] + S.d[3 + lane] * s_wb[1] + S.d[6 + lane] * s_wb[2];
+                s_T[lane] = (bc.rot_form == 1) ? S.w[lane] + 0.5 * wl : wl;
+            }
+            __syncwarp();
+        }
         if (lane < 9) f_d[lane] = (float)S.d[lane];
         if (lane < 3) {
-            f_v[lane] = (float)S.v[lane];
-            f_w[lane] = (float)S.w[lane];
+            f_v[lane] = (float)(pred ? s_F[lane] : S.v[lane]);
+            f_w[lane] = (float)(pred ? s_T[lane] : S.w[lane]);
             f_cf[lane] = (float)S.Cf[lane];
             i_ci[lane] = S.Ci[lane];
             i_lo[lane] = S.box_lo[lane];
@@ -274,8 +303,9 @@ constexpr int ROWS_WARPS = ROWS_THREADS / 32;
 // Step l = 0 for marker k by one warp: interpolation of u* and sigma (two
 // stencil cells per lane, xor-shuffle sums), h^0 = U - I[u*] and the
 // traction dS sigma.n with its moment about C_m.
+// warm: the IBM cycles start from the previous step's h (kept in hl).
 __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, const MarkerArrays &m,
-                                                   const BoxArrays &ba, int k, const MRec &rk, int lane) {
+                                                   const BoxArrays &ba, int k, const MRec &rk, int lane, int warm) {
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
     const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
     const float wxy = pick4(rk.wx, i) * pick4(rk.wy, j);
@@ -299,8 +329,10 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
         for (int c = 0; c < 3; ++c) {
             const float h = m.U[c * nm + k] - acc[c];
             m.r0[c * nm + k] = h;
-            m.hl[c * nm + k] = h;
-            m.rec[k].hdS[c] = h * dS;
+            if (!warm) {
+                m.hl[c * nm + k] = h;
+                m.rec[k].hdS[c] = h * dS;
+            }
         }
         const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
         const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k];
@@ -320,12 +352,12 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
 
 __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const MarkerArrays &m, const BoxArrays &ba,
                                               const int *__restrict__ wlist, const int *__restrict__ wcount,
-                                              int cap, DevState *st, int k) {
+                                              int cap, DevState *st, int k, int warm) {
     __shared__ int wc[ROWS_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MRec rk = m.rec[k];
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
-    if (warp == 0) interp_marker_warp(box, nm, m, ba, k, rk, lane);
+    if (warp == 0) interp_marker_warp(box, nm, m, ba, k, rk, lane, warm);
     // ---- row k of A -----------------------------------------------------------
     const int tile = (bx / TILE) + box.tx * ((by / TILE) + box.ty * (bz / TILE));
     const int cnt = wcount[tile];
@@ -376,8 +408,8 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
 __global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
                                                                 const int *__restrict__ wlist,
                                                                 const int *__restrict__ wcount, int cap,
-                                                                DevState *st) {
-    interp0_block(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x);
+                                                                DevState *st, int warm) {
+    interp0_block(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x, warm);
 }
 
 // The same step l = 0 and rows of A with one block per TILE^3 tile of the
@@ -393,7 +425,7 @@ constexpr int IT_STAGE = 256;  // candidates staged per chunk
 __device__ __forceinline__ void interp0_tile_block(const BoxGeom &box, int nm, const MarkerArrays &m,
                                                    const BoxArrays &ba, const int *__restrict__ tile_list,
                                                    const int *__restrict__ tile_count, int cap, DevState *st,
-                                                   int tile) {
+                                                   int tile, int warm) {
     __shared__ int kb[IT_MAXB], klen[IT_MAXB];
     __shared__ int wc[ROWS_WARPS];
     __shared__ int nbased;
@@ -444,7 +476,7 @@ __device__ __forceinline__ void interp0_tile_block(const BoxGeom &box, int nm, c
     for (int q = warp; q < nb; q += ROWS_WARPS) {
         const int k = kb[q];
         const MRec rk = m.rec[k];
-        interp_marker_warp(box, nm, m, ba, k, rk, lane);
+        interp_marker_warp(box, nm, m, ba, k, rk, lane, warm);
     }
     for (int q = tid; q < nb; q += ROWS_THREADS) klen[q] = 0;
     for (int q = tid; q < 3 * 6 * IT_STAGE; q += ROWS_THREADS) {
@@ -517,47 +549,87 @@ __device__ __forceinline__ void interp0_tile_block(const BoxGeom &box, int nm, c
 //   h_out_k = h_in_k + U_k - I[u* + S h_in](X_k) = h_in_k + r0_k - sum_j A_kj h_in_j.
 // One warp per marker, entries of the row in order per lane, xor-shuffle sum.
 // The last cycle also stores h dS for the spreading of h_imm.
+// adaptive (predictor modes): cycle `cyc` (0-based) is skipped -- h_out = h_in
+// -- once the slip max_k |U_k - I[u* + S h_in](X_k)| = max |r0 - A h_in| seen
+// by cycle cyc - 1 is below eps; each executed cycle records its slip (an
+// atomic maximum of non-negative float bits: exact, order-independent).
+// h_final: also receives the last cycle's h when that is not h_out.
 __device__ __forceinline__ void cycle_block(int nm, const MarkerArrays &m, const float *__restrict__ h_in,
-                                            float *__restrict__ h_out, int last, int blk) {
+                                            float *__restrict__ h_out, float *__restrict__ h_final, int last,
+                                            int blk, DevState *st, int cyc, int adaptive, float eps) {
+    __shared__ float smax[INTERP_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = blk * INTERP_WARPS + warp;
-    if (k >= nm) return;
-    const int len = m.alen[k];
-    const float *arow = m.aval + (size_t)k * ROWCAP;
-    const int *irow = m.aidx + (size_t)k * ROWCAP;
-    float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    for (int e = lane; e < len; e += 32) {
-        const float a = arow[e];
-        const int j = irow[e];
-        ax = fmaf(a, h_in[j], ax);
-        ay = fmaf(a, h_in[nm + j], ay);
-        az = fmaf(a, h_in[2 * nm + j], az);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
-        az += __shfl_xor_sync(0xffffffffu, az, o);
-    }
-    if (lane == 0) {
-        const float acc[3] = {ax, ay, az};
+    const bool skip = adaptive && cyc > 0 && __uint_as_float(st->pr.slip[cyc - 1]) < eps;
+    float res_max = 0.0f;
+    if (k < nm) {
         const float dS = m.dS[k];
-        for (int c = 0; c < 3; ++c) {
-            const float h = h_in[c * nm + k] + (m.r0[c * nm + k] - acc[c]);
-            h_out[c * nm + k] = h;
-            if (last) m.rec[k].hdS[c] = h * dS;
+        if (skip) {
+            if (lane == 0)
+                for (int c = 0; c < 3; ++c) {
+                    const float h = h_in[c * nm + k];
+                    h_out[c * nm + k] = h;
+                    if (last) m.rec[k].hdS[c] = h * dS;
+                    if (last && h_final) h_final[c * nm + k] = h;
+                }
+        } else {
+            const int len = m.alen[k];
+            const float *arow = m.aval + (size_t)k * ROWCAP;
+            const int *irow = m.aidx + (size_t)k * ROWCAP;
+            float ax = 0.0f, ay = 0.0f, az = 0.0f;
+            for (int e = lane; e < len; e += 32) {
+                const float a = arow[e];
+                const int j = irow[e];
+                ax = fmaf(a, h_in[j], ax);
+                ay = fmaf(a, h_in[nm + j], ay);
+                az = fmaf(a, h_in[2 * nm + j], az);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+            }
+            if (lane == 0) {
+                const float acc[3] = {ax, ay, az};
+                for (int c = 0; c < 3; ++c) {
+                    const float res = m.r0[c * nm + k] - acc[c];
+                    const float h = h_in[c * nm + k] + res;
+                    h_out[c * nm + k] = h;
+                    if (last) m.rec[k].hdS[c] = h * dS;
+                    if (last && h_final) h_final[c * nm + k] = h;
+                    res_max = fmaxf(res_max, fabsf(res));
+                }
+            }
         }
+    }
+    if (skip) return;  // uniform over the block
+    if (lane == 0) smax[warp] = res_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = smax[0];
+        for (int w = 1; w < INTERP_WARPS; ++w) b = fmaxf(b, smax[w]);
+        if (cyc < 8) atomicMax(&st->pr.slip[cyc], __float_as_uint(b));
+        if (blk == 0) st->pr.cycles += 1;
     }
 }
 
 __global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArrays m, const float *__restrict__ h_in,
-                                                             float *__restrict__ h_out, int last) {
-    cycle_block(nm, m, h_in, h_out, last, blockIdx.x);
+                                                             float *__restrict__ h_out, float *__restrict__ h_final,
+                                                             int last, DevState *st, int cyc, int adaptive,
+                                                             float eps) {
+    cycle_block(nm, m, h_in, h_out, h_final, last, blockIdx.x, st, cyc, adaptive, eps);
 }
 
 // F = sum_k dS sigma.n, T = sum_k arm x (dS sigma.n) in FP64: warp c sums
 // component c, lane l the markers l, l+32, ... in order, then an xor tree.
-__device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ ft, DevState *st) {
+// Then, in thread 0: the relative error of the prediction made for this time
+// level (predictor modes: a large one switches the next prediction to the
+// linear one), the force/torque history, and the trajectory record of time
+// level st->s[slot] (when a log is attached).
+__device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ ft, DevState *st, int slot,
+                                             int predictor, double theta, double *__restrict__ log,
+                                             long long log_cap) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double a = 0.0;
     for (int k = lane; k < nm; k += 32) a += (double)ft[c * nm + k];
@@ -567,10 +639,68 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
         if (c < 3) st->F[c] = a; else st->T[c - 3] = a;
         if (!isfinite(a)) atomicCAS(&st->status, 0, STAT_DIVERGED);
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    Predictor &P = st->pr;
+    double resid = -1.0, resid_net = -1.0, made = -1.0, fh[6] = {0, 0, 0, 0, 0, 0};
+    auto rel_err = [&](const double *Fp) {
+        double num = 0.0, den = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            num += (st->F[q] - Fp[q]) * (st->F[q] - Fp[q]);
+            den += st->F[q] * st->F[q];
+        }
+        return den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+    };
+    if (predictor != 0 && P.predicted) {
+        made = P.by_net ? 1.0 : 0.0;
+        for (int q = 0; q < 3; ++q) {
+            fh[q] = P.Fhat[q];
+            fh[3 + q] = P.That[q];
+        }
+        resid = rel_err(P.Fhat);
+        P.resid = resid;
+        P.predicted = 0;
+    }
+    if (predictor != 0 && P.net_ok) {  // the network's own accuracy decides the fallback
+        resid_net = rel_err(P.Fnet);
+        P.resid_net = resid_net;
+        P.fallback = !(resid_net <= theta);
+        P.net_ok = 0;
+    }
+    for (int h = 3; h > 0; --h)
+        for (int q = 0; q < 3; ++q) {
+            P.Fh[h][q] = P.Fh[h - 1][q];
+            P.Th[h][q] = P.Th[h - 1][q];
+        }
+    for (int q = 0; q < 3; ++q) {
+        P.Fh[0][q] = st->F[q];
+        P.Th[0][q] = st->T[q];
+    }
+    P.hist_n = P.hist_n < 4 ? P.hist_n + 1 : 4;
+    if (log && log_cap > 0) {
+        const BodySlot &S = st->s[slot];
+        double *r = log + (size_t)(P.logged % log_cap) * LOG_REC;
+        for (int q = 0; q < 9; ++q) r[q] = S.d[q];
+        for (int q = 0; q < 3; ++q) {
+            r[9 + q] = S.v[q];
+            r[12 + q] = S.w[q];
+            r[15 + q] = st->F[q];
+            r[18 + q] = st->T[q];
+        }
+        r[21] = (double)S.step;
+        r[22] = resid;
+        for (int q = 0; q < 6; ++q) r[23 + q] = fh[q];
+        r[29] = made;
+        r[30] = resid_net;
+        r[31] = 0.0;
+    }
+    P.logged += 1;
 }
 
-__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st) {
-    reduce_block(nm, ft, st);
+__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st, int slot,
+                                                   int predictor, double theta, double *__restrict__ log,
+                                                   long long log_cap) {
+    reduce_block(nm, ft, st, slot, predictor, theta, log, log_cap);
 }
 
 constexpr int SPREAD_SLICES = 8;                               // candidate slices per tile
@@ -674,10 +804,11 @@ __global__ void __launch_bounds__(PM_THREADS) k_batch_particle_markers(const Run
 }
 
 __global__ void __launch_bounds__(ROWS_THREADS) k_batch_interp0_tiles(const RunDesc *__restrict__ runs,
-                                                                      const int *__restrict__ prefix, int nruns) {
+                                                                      const int *__restrict__ prefix, int nruns,
+                                                                      int warm) {
     int lb;
     const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
-    interp0_tile_block(R.box, R.nm, R.m, R.ba, R.tile_list, R.tile_count, R.cap, R.st, lb);
+    interp0_tile_block(R.box, R.nm, R.m, R.ba, R.tile_list, R.tile_count, R.cap, R.st, lb, warm);
 }
 
 __device__ __forceinline__ float *hsel(const MarkerArrays &m, int sel) {
@@ -686,15 +817,17 @@ __device__ __forceinline__ float *hsel(const MarkerArrays &m, int sel) {
 
 __global__ void __launch_bounds__(32 * INTERP_WARPS) k_batch_cycle(const RunDesc *__restrict__ runs,
                                                                    const int *__restrict__ prefix, int nruns,
-                                                                   int sel_in, int sel_out, int last) {
+                                                                   int sel_in, int sel_out, int sel_final, int last,
+                                                                   int cyc, int adaptive) {
     int lb;
     const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
-    cycle_block(R.nm, R.m, hsel(R.m, sel_in), hsel(R.m, sel_out), last, lb);
+    cycle_block(R.nm, R.m, hsel(R.m, sel_in), hsel(R.m, sel_out), sel_final >= 0 ? hsel(R.m, sel_final) : nullptr,
+                last, lb, R.st, cyc, adaptive, R.bc.slip_eps);
 }
 
-__global__ void __launch_bounds__(192) k_batch_reduce_ft(const RunDesc *__restrict__ runs) {
+__global__ void __launch_bounds__(192) k_batch_reduce_ft(const RunDesc *__restrict__ runs, int slot) {
     const RunDesc &R = runs[blockIdx.x];
-    reduce_block(R.nm, R.m.ft, R.st);
+    reduce_block(R.nm, R.m.ft, R.st, slot, R.bc.predictor, R.bc.resid_theta, R.bc.log, R.bc.log_cap);
 }
 
 __global__ void __launch_bounds__(SPREAD_THREADS) k_batch_spread(const RunDesc *__restrict__ runs,
@@ -712,20 +845,22 @@ cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const Bo
 }
 
 cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
-                           const int *tile_count, int cap, DevState *st, cudaStream_t s) {
+                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s) {
     const int ntiles = box.tx * box.ty * box.tz;  // list 1 (rows of A) follows list 0
     k_interp0_rows<<<nm, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
-                                               tile_count + ntiles, cap, st);
+                                               tile_count + ntiles, cap, st, warm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, int last, cudaStream_t s) {
-    k_cycle<<<(nm + INTERP_WARPS - 1) / INTERP_WARPS, 32 * INTERP_WARPS, 0, s>>>(nm, m, h_in, h_out, last);
+cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, float *h_final, int last,
+                         DevState *st, int cyc, int adaptive, float eps, cudaStream_t s) {
+    k_cycle<<<(nm + INTERP_WARPS - 1) / INTERP_WARPS, 32 * INTERP_WARPS, 0, s>>>(nm, m, h_in, h_out, h_final, last,
+                                                                                 st, cyc, adaptive, eps);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, cudaStream_t s) {
-    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st);
+cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, int slot, const BodyConst &bc, cudaStream_t s) {
+    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st, slot, bc.predictor, bc.resid_theta, bc.log, bc.log_cap);
     return cudaGetLastError();
 }
 
@@ -747,19 +882,21 @@ cudaError_t launch_batch_particle_markers(const RunDesc *runs, const int *prefix
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s) {
-    k_batch_interp0_tiles<<<nblocks, ROWS_THREADS, 0, s>>>(runs, prefix, nruns);
+cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int warm,
+                                 cudaStream_t s) {
+    k_batch_interp0_tiles<<<nblocks, ROWS_THREADS, 0, s>>>(runs, prefix, nruns, warm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_cycle(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int sel_in,
-                               int sel_out, int last, cudaStream_t s) {
-    k_batch_cycle<<<nblocks, 32 * INTERP_WARPS, 0, s>>>(runs, prefix, nruns, sel_in, sel_out, last);
+                               int sel_out, int sel_final, int last, int cyc, int adaptive, cudaStream_t s) {
+    k_batch_cycle<<<nblocks, 32 * INTERP_WARPS, 0, s>>>(runs, prefix, nruns, sel_in, sel_out, sel_final, last, cyc,
+                                                        adaptive);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, cudaStream_t s) {
-    k_batch_reduce_ft<<<nruns, 192, 0, s>>>(runs);
+cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, int slot, cudaStream_t s) {
+    k_batch_reduce_ft<<<nruns, 192, 0, s>>>(runs, slot);
     return cudaGetLastError();
 }
 

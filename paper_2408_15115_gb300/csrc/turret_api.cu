@@ -110,6 +110,7 @@ static void release(turret_ctx *c) {
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_red) cudaEventDestroy(c->ev_red);
     if (c->ev_red_done) cudaEventDestroy(c->ev_red_done);
+    if (c->ev_pred) cudaEventDestroy(c->ev_pred);
     if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
 }
@@ -133,7 +134,14 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
 
     c = new turret_ctx();
     c->side = c->aux = nullptr;
-    c->ev_fork = c->ev_join = c->ev_red = c->ev_red_done = nullptr;
+    c->ev_fork = c->ev_join = c->ev_red = c->ev_red_done = c->ev_pred = nullptr;
+    c->pred_mode = 0;
+    c->pred_opts = 0;
+    c->pred_eps = 0.0f;
+    c->pred_theta = INFINITY;
+    c->net = nullptr;
+    c->log = nullptr;
+    c->log_cap = 0;
     c->pinned = nullptr;
     c->graph_ready[0] = c->graph_ready[1] = false;
     c->win = *win;
@@ -183,6 +191,7 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_pred, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tau_z, c->tau_host.data(), c->tau_host.size() * sizeof(float), cudaMemcpyHostToDevice,
                             c->stream);
@@ -426,22 +435,37 @@ static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float
     CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, slot, advance, c->mk, s));
     CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base, c->mk.seg,
                               c->tile_list, c->tile_count, c->cap, c->dstate, c->body.rmin, c->body.rmax, s));
-    CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, s));
+    const int warm = (advance && c->body.predictor != 0 && (c->body.pred_opts & PRED_WARM)) ? 1 : 0;
+    CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, warm, s));
     if (branch) {
         CE(cudaEventRecord(c->ev_red, s));
         CE(cudaStreamWaitEvent(c->aux, c->ev_red, 0));
-        CE(launch_reduce_ft(nm, c->mk, c->dstate, c->aux));
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, c->aux));
         CE(cudaEventRecord(c->ev_red_done, c->aux));
     } else {
-        CE(launch_reduce_ft(nm, c->mk, c->dstate, s));
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, s));
     }
-    // cycles 1 .. n-1 read r0, then alternate so that the last one writes hl
-    const int C = c->flags.ibm_cycles - 1;
-    const float *src = c->mk.r0;
-    for (int cyc = 1; cyc <= C; ++cyc) {
-        float *dst = ((C - cyc) % 2 == 0) ? c->mk.hl : c->mk.hb;
-        CE(launch_cycle(nm, c->mk, src, dst, cyc == C, s));
-        src = dst;
+    if (!warm) {
+        // the paper's cycles: h^0 = r0, then cycles 1 .. n-1 alternating so
+        // that the last one writes hl
+        const int C = c->flags.ibm_cycles - 1;
+        const float *src = c->mk.r0;
+        for (int cyc = 1; cyc <= C; ++cyc) {
+            float *dst = ((C - cyc) % 2 == 0) ? c->mk.hl : c->mk.hb;
+            CE(launch_cycle(nm, c->mk, src, dst, nullptr, cyc == C, c->dstate, cyc - 1, 0, 0.0f, s));
+            src = dst;
+        }
+    } else {
+        // predictor modes: up to n cycles from the previous h (in hl), each
+        // skipped once the slip is below the tolerance; hl ends with the result
+        const int C = c->flags.ibm_cycles;
+        const float *src = c->mk.hl;
+        for (int cyc = 1; cyc <= C; ++cyc) {
+            float *dst = (cyc % 2 == 1) ? c->mk.hb : c->mk.hl;
+            float *fin = (cyc == C && dst != c->mk.hl) ? c->mk.hl : nullptr;
+            CE(launch_cycle(nm, c->mk, src, dst, fin, cyc == C, c->dstate, cyc - 1, 1, c->body.slip_eps, s));
+            src = dst;
+        }
     }
     CE(launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, s));
     if (branch) CE(cudaStreamWaitEvent(s, c->ev_red_done, 0));
@@ -455,14 +479,23 @@ static cudaError_t enqueue_step(turret_ctx *c, int p) {
         return launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
                                      1 - p, nullptr, c->box, false, REGION_ALL, c->stream);
     cudaStream_t chain = c->split ? c->side : c->stream;
+    const bool predict = c->body.predictor != 0;
+    const MlpDev *net = (c->body.predictor == 2) ? mlp_device_view(c->net) : nullptr;
     if (c->split) {
         CE(cudaEventRecord(c->ev_fork, c->stream));
         CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        if (predict) {  // the prediction overlaps the near collide+stream
+            CE(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+            CE(launch_predict(net, c->dstate, p, c->body.predictor, c->aux));
+            CE(cudaEventRecord(c->ev_pred, c->aux));
+        }
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_FAR, c->stream));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_NEAR, c->side));
+        if (predict) CE(cudaStreamWaitEvent(c->side, c->ev_pred, 0));
     } else {
+        if (predict) CE(launch_predict(net, c->dstate, p, c->body.predictor, c->stream));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_ALL, c->stream));
     }
@@ -531,6 +564,12 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     B.rc = L.rc;
     B.rmin = (float)L.rmin;
     B.rmax = (float)L.rmax;
+    B.predictor = c->pred_mode;
+    B.pred_opts = c->pred_opts;
+    B.slip_eps = c->pred_eps;
+    B.resid_theta = c->pred_theta;
+    B.log = c->log;
+    B.log_cap = c->log_cap;
     // static marker data (body frame): offsets from C_m, normals, areas
     const size_t nm = (size_t)L.nm;
     c->staging.assign(7 * nm, 0.0f);
@@ -640,6 +679,60 @@ extern "C" turret_status step(turret_ctx *c, int64_t n) {
     return TURRET_OK;
 }
 
+extern "C" turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const turret_mlp *net, int32_t options,
+                                              double slip_eps, double resid_theta) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (mode < 0 || mode > 2) return fail(c, TURRET_EINVAL, "predictor mode must be 0, 1 or 2");
+    if (options < 0 || options > (PRED_WARM | PRED_VEL)) return fail(c, TURRET_EINVAL, "invalid predictor options");
+    if (mode == 2 && !net) return fail(c, TURRET_EINVAL, "the network predictor needs a network");
+    if (!(slip_eps >= 0.0) || !(resid_theta > 0.0)) return fail(c, TURRET_EINVAL, "invalid tolerances");
+    c->pred_mode = mode;
+    c->pred_opts = options;
+    c->body.pred_opts = options;
+    c->net = net;
+    c->pred_eps = (float)slip_eps;
+    c->pred_theta = resid_theta;
+    c->body.predictor = mode;
+    c->body.slip_eps = c->pred_eps;
+    c->body.resid_theta = resid_theta;
+    drop_graphs(c);
+    return TURRET_OK;
+}
+
+extern "C" turret_status turret_set_log(turret_ctx *c, double *records, int64_t capacity) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (capacity < 0 || (capacity > 0 && !records)) return fail(c, TURRET_EINVAL, "invalid log");
+    c->log = capacity > 0 ? records : nullptr;
+    c->log_cap = capacity;
+    c->body.log = c->log;
+    c->body.log_cap = capacity;
+    drop_graphs(c);
+    return TURRET_OK;
+}
+
+extern "C" turret_status turret_query_predictor(turret_ctx *c, turret_predictor_stats *out) {
+    if (!c || !out) return fail(c, TURRET_EINVAL, "NULL argument");
+    DevState D;
+    CK(cudaMemcpyAsync(&D, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "query");
+    CK(cudaStreamSynchronize(c->stream), "query sync");
+    memset(out, 0, sizeof *out);
+    out->steps = D.pr.steps;
+    out->net_steps = D.pr.mlp_steps;
+    out->fallbacks = D.pr.fallbacks;
+    out->cycles = D.pr.cycles;
+    out->logged = D.pr.logged;
+    out->resid = D.pr.resid;
+    for (int k = 0; k < 8; ++k) {
+        unsigned int b = D.pr.slip[k];
+        float f;
+        memcpy(&f, &b, 4);
+        out->slip[k] = f;
+    }
+    out->hist_n = D.pr.hist_n;
+    out->fallback = D.pr.fallback;
+    return TURRET_OK;
+}
+
 extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
     if (!c) return fail(c, TURRET_EINVAL, "NULL context");
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
@@ -681,7 +774,10 @@ extern "C" turret_status query_particle_state(turret_ctx *c, turret_particle_sta
     // collide+stream (1, or far + near), particle + markers, moments + tile
     // lists, interpolation + rows of A, F/T reduction, one product per extra
     // cycle, spread of h_imm
-    out->kernels_per_step = c->has_particle ? (c->split ? 2 : 1) + 5 + (c->flags.ibm_cycles - 1) : 1;
+    out->kernels_per_step = c->has_particle ? (c->split ? 2 : 1) + 5 + (c->flags.ibm_cycles - 1) +
+                                                  (c->pred_mode != 0 ? 1 : 0) +  // prediction
+                                                  ((c->pred_mode != 0 && (c->pred_opts & PRED_WARM)) ? 1 : 0)
+                                            : 1;
     if (D.status == STAT_DOMAIN) return fail(c, TURRET_EDOMAIN, "a marker stencil left the window");
     if (D.status == STAT_DIVERGED) return fail(c, TURRET_EDIVERGED, "non-finite force or torque");
     if (D.status == STAT_OVERFLOW) return fail(c, TURRET_EOVERFLOW, "a support tile overflowed its marker list");

@@ -17,7 +17,7 @@ struct turret_ctx {
     cudaStream_t stream;  // caller's stream
     cudaStream_t side;    // internal high-priority stream of the immersed-boundary chain
     cudaStream_t aux;     // internal stream of the FP64 force/torque reduction
-    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done;
+    cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done, ev_pred;
     turret::Geom geom;
     // fluid workspace
     void *f[2];
@@ -38,6 +38,13 @@ struct turret_ctx {
     turret::DevState *pinned;  // page-locked staging of the device state for queries
     std::vector<float> staging;
     std::vector<float> tau_host;  // staging of the per-plane relaxation times
+    // force/torque predictor (surrogate modes) and trajectory log
+    int pred_mode, pred_opts;
+    float pred_eps;
+    double pred_theta;
+    const turret_mlp *net;
+    double *log;
+    long long log_cap;
     // stepping
     long long step;
     cudaGraphExec_t graph[2];

@@ -48,12 +48,44 @@ struct BodySlot {
     int reseed;        // physical plane that entered the ring (reads as rest), -1 none
 };
 
+// Force/torque predictor state (surrogate modes; not in the paper).  The
+// history is kept in every mode; the prediction is made at the start of a
+// step t -> t+1 for F(t+1), T(t+1).
+struct Predictor {
+    double Fh[4][3], Th[4][3];  // lab-frame F, T at t, t-1, t-2, t-3 (newest first)
+    double Fhat[3], That[3];    // prediction for the next time level (the one used)
+    double Fnet[3], Tnet[3];    // the network's prediction (made whenever it can run)
+    double resid;               // |F - Fhat| / |F| of the last checked prediction
+    double resid_net;           // |F - Fnet| / |F| of the network's last prediction
+    unsigned int slip[8];       // per IBM cycle: max over markers of |U - I[u* + S h]| (float bits)
+    int hist_n;                 // valid history entries, 0..4
+    int fallback;               // 1: the next prediction is the linear one
+    int predicted;              // 1: Fhat, That hold the prediction for the current step
+    int by_net;                 // 1: that prediction came from the network
+    int net_ok;                 // 1: Fnet, Tnet hold the network's prediction for the current step
+    int pad1;
+    long long steps, mlp_steps, fallbacks, cycles;  // predictions made, by the network, fallbacks, IBM cycles run
+    long long logged;           // trajectory records written
+    float feat[40];             // features of the last network prediction (34 used)
+    float yb[8];                // its outputs (6 used)
+};
+
 struct DevState {
     BodySlot s[2];
     double F[3], T[3];     // hydrodynamic force / torque at the latest time level
     int status;
     unsigned int counter;
+    Predictor pr;
 };
+
+enum { PRED_WARM = 1, PRED_VEL = 2 };
+
+// Trajectory record written after the force of each time level j is known:
+// d(j) [9], v(j-1/2) [3], w(j-1/2) [3], F(j) [3], T(j) [3], j, |F - Fhat| / |F|
+// of the prediction used for j (or -1), Fhat [3], That [3], 1 if the network
+// made it (0 linear, -1 none), |F - Fnet| / |F| of the network's prediction
+// for j (or -1), 0.
+constexpr int LOG_REC = 32;
 
 // Constant per-context parameters of the fluid window.
 struct Geom {
@@ -84,6 +116,16 @@ struct BodyConst {
     int nm;            // markers
     int rc;            // ceil of the bounding radius of the markers about C_m
     float rmin, rmax;  // smallest and largest marker distance from C_m
+    // force/torque predictor: 0 the paper's step (marker velocities at
+    // t + 1/2, cold IBM cycles); 1 linear extrapolation, 2 network; in modes
+    // 1, 2 the marker velocities are predicted at t + 1 and the IBM cycles
+    // start from the previous h and stop once the slip is below slip_eps
+    int predictor;
+    int pred_opts;       // PRED_WARM: warm-started adaptive cycles; PRED_VEL: marker velocities at t + 1
+    float slip_eps;
+    double resid_theta;  // fall back to the linear prediction above this relative error
+    double *log;         // trajectory records [log_cap][LOG_REC], or null
+    long long log_cap;
 };
 
 // Per-marker record read by the transfer kernels (64 bytes, one per marker):
@@ -125,6 +167,15 @@ struct BoxArrays {
     float *h;   // [3][nbox] spread force (h_imm after the last cycle)
 };
 
+// Force/torque surrogate network (mlp.cu): 34 -> 3 x 128 GELU -> 6.
+constexpr int MLP_IN = 34, MLP_INP = 48, MLP_H = 128, MLP_OUT = 6, MLP_OUTP = 8, MLP_NPARAM = 38278;
+struct MlpDev {
+    const float *P;            // FP32 parameters, flat layout W1 b1 W2 b2 W3 b3 W4 b4
+    const __nv_bfloat16 *Wb;   // BF16 weights, padded: W1 [128][48], W2, W3 [128][128], W4 [8][128]
+    const float *mean_x, *std_x, *mean_y, *std_y;
+    int precision;             // 0: BF16 tensor cores, 1: FP32
+};
+
 // One run of a batch: everything a batched kernel needs about one context,
 // in device memory.  A batched launch covers the (run, block) table of all
 // runs; block b belongs to run r when prefix[r] <= b < prefix[r + 1].
@@ -141,6 +192,7 @@ struct RunDesc {
     int storage, cap, nm;
     int split;           // 1: far / near collide+stream, 0: the whole window in the near phase
     int tx;              // collide+stream tile width (threads along x)
+    MlpDev mlp;          // the force/torque network (predictor mode 2)
 };
 enum { PHASE_BULK = 0, PHASE_NEAR = 1 };
 // h arrays of the IBM cycles, selected per run in batched launches
@@ -233,21 +285,24 @@ cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const Bo
 // l = 0 interpolation of u* and sigma, the surface traction per marker, and
 // the row k of the interaction matrix A (one warp per marker).
 cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
-                           const int *tile_count, int cap, DevState *st, cudaStream_t s);
+                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s);
 // One IBM cycle in matrix form: h_out = h_in + r0 - A h_in (= steps l = 1..4).
-cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, int last, cudaStream_t s);
+cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, float *h_final, int last,
+                         DevState *st, int cyc, int adaptive, float eps, cudaStream_t s);
 // F = sum_k f_k, T = sum_k t_k in FP64, fixed order, into the device state.
-cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, cudaStream_t s);
+cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, int slot, const BodyConst &bc, cudaStream_t s);
 cudaError_t launch_spread(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
                           const int *tile_count, int cap, cudaStream_t s);
 // Batched forms of the launches above, one launch over all runs of a batch
 // (time level p -> p ^ 1; blocks per run from the per-phase prefix table).
 cudaError_t launch_batch_particle_markers(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
                                           cudaStream_t s);
-cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s);
+cudaError_t launch_batch_interp0(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int warm,
+                                 cudaStream_t s);
 cudaError_t launch_batch_cycle(const RunDesc *runs, const int *prefix, int nruns, int nblocks, int sel_in,
-                               int sel_out, int last, cudaStream_t s);
-cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, cudaStream_t s);
+                               int sel_out, int sel_final, int last, int cyc, int adaptive, cudaStream_t s);
+cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, int slot, cudaStream_t s);
+cudaError_t launch_batch_predict(const RunDesc *runs, int nruns, int slot, cudaStream_t s);
 cudaError_t launch_batch_spread(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s);
 // Blocks of one run in each batched phase (host side, same formulas as the kernels).
 int blocks_bulk(const RunDesc &r, int threads);
@@ -258,9 +313,18 @@ int blocks_interp0(const RunDesc &r);
 int blocks_cycle(const RunDesc &r);
 int blocks_spread(const RunDesc &r);
 
+// Forward pass of n raw feature rows x [n][34] -> raw outputs y [n][6].
+cudaError_t launch_mlp_infer(const MlpDev &w, const float *x, int n, float *y, cudaStream_t s);
+// Force/torque prediction at the start of a step from window slot `slot`
+// (mode 1 linear, 2 network w; w may be null), single run or every run.
+cudaError_t launch_predict(const MlpDev *w, DevState *st, int slot, int mode, cudaStream_t s);
+
 constexpr int TILE = 4;          // support-box tiles of TILE^3 cells (spreading)
 constexpr int INTERP_WARPS = 8;  // markers per interpolation block
 constexpr int MAX_CANDIDATES = 2048;  // markers listed per support tile
 constexpr int ROWCAP = 512;           // entries per row of A
 
 }  // namespace turret
+
+struct turret_mlp;
+const turret::MlpDev *mlp_device_view(const turret_mlp *m);

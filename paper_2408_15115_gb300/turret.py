@@ -45,8 +45,20 @@ class TurretError(RuntimeError):
         self.status = status
 
 
+class PredictorStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("net_steps", C.c_int64), ("fallbacks", C.c_int64), ("cycles", C.c_int64),
+                ("logged", C.c_int64), ("resid", C.c_double), ("slip", C.c_double * 8), ("hist_n", C.c_int32),
+                ("fallback", C.c_int32)]
+
+
+class AdamW(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("weight_decay", C.c_float)]
+
+
 _lib = None
 _dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
 
 
 def lib():
@@ -103,6 +115,34 @@ def lib():
         L.turret_batch_destroy.argtypes = [vp]
         L.turret_batch_last_error.restype = C.c_char_p
         L.turret_batch_last_error.argtypes = [vp]
+        L.mlp_workspace_bytes.restype = C.c_size_t
+        L.mlp_workspace_bytes.argtypes = [C.c_int32]
+        L.mlp_init.restype = C.c_int
+        L.mlp_init.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32, _fp, vp, C.c_size_t, vp]
+        for name in ("mlp_set_params", "mlp_get_params"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [vp, _fp]
+        L.mlp_set_norm.restype = C.c_int
+        L.mlp_set_norm.argtypes = [vp, _fp, _fp, _fp, _fp]
+        for name in ("mlp_forward", "mlp_infer"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [vp, vp, C.c_int32, vp]
+        L.mlp_loss_grad.restype = C.c_int
+        L.mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int32, _fp, vp]
+        L.mlp_train_step.restype = C.c_int
+        L.mlp_train_step.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(AdamW), _fp]
+        L.mlp_destroy.restype = C.c_int
+        L.mlp_destroy.argtypes = [vp]
+        L.mlp_last_error.restype = C.c_char_p
+        L.mlp_last_error.argtypes = [vp]
+        L.turret_set_predictor.restype = C.c_int
+        L.turret_set_predictor.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_double, C.c_double]
+        L.turret_set_log.restype = C.c_int
+        L.turret_set_log.argtypes = [vp, vp, C.c_int64]
+        L.turret_query_predictor.restype = C.c_int
+        L.turret_query_predictor.argtypes = [vp, C.POINTER(PredictorStats)]
+        L.mlp_build_samples.restype = C.c_int
+        L.mlp_build_samples.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
         L.turret_time_collide.restype = C.c_int
         L.turret_time_collide.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         _lib = L
@@ -235,6 +275,43 @@ class Turret:
         self._check(self._L.turret_time_collide(self.ctx, int(threads), int(tx), int(minb), int(reps), C.byref(us)))
         return float(us.value)
 
+    PREDICTORS = {"paper": 0, "linear": 1, "mlp": 2}
+    LOG_REC = 32
+
+    def set_predictor(self, mode="paper", net=None, warm=False, velocity=True, slip_eps=1e-4, resid_theta=0.5):
+        """Force/torque predictor: 'paper' (the method as published), 'linear'
+        or 'mlp' (with the MLP object `net`); warm: warm-started adaptive IBM
+        cycles; velocity: marker velocities at t + 1.  See turret_set_predictor."""
+        self._net = net
+        opts = (1 if warm else 0) | (2 if velocity else 0)
+        self._check(self._L.turret_set_predictor(self.ctx, self.PREDICTORS[mode], net.m if net is not None else None,
+                                                 opts, float(slip_eps), float(resid_theta)))
+
+    def set_log(self, capacity):
+        """Attach a device trajectory log of `capacity` records (0 detaches)."""
+        if capacity > 0:
+            self._log = self.torch.zeros((int(capacity), self.LOG_REC), dtype=self.torch.float64, device=self.device)
+            self._check(self._L.turret_set_log(self.ctx, C.c_void_p(self._log.data_ptr()), int(capacity)))
+        else:
+            self._check(self._L.turret_set_log(self.ctx, None, 0))
+            self._log = None
+
+    def log_records(self):
+        """The logged records in time order (float64 CUDA tensor [n][32])."""
+        n = self.predictor_stats()["logged"]
+        cap = self._log.shape[0]
+        if n <= cap:
+            return self._log[:n].clone()
+        k = n % cap
+        return self.torch.cat([self._log[k:], self._log[:k]]).clone()
+
+    def predictor_stats(self):
+        s = PredictorStats()
+        self._check(self._L.turret_query_predictor(self.ctx, C.byref(s)))
+        return dict(steps=int(s.steps), net_steps=int(s.net_steps), fallbacks=int(s.fallbacks),
+                    cycles=int(s.cycles), logged=int(s.logged), resid=float(s.resid), slip=list(s.slip),
+                    hist_n=int(s.hist_n), fallback=int(s.fallback))
+
     @property
     def cells(self):
         nz, ny, nx = self.shape
@@ -311,3 +388,125 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+MLP_IN, MLP_OUT, MLP_NPARAM = 34, 6, 38278
+
+
+class MLP:
+    """The force/torque surrogate network (34 -> 3 x 128 GELU -> 6) on the GPU.
+
+    precision "bf16": tensor-core matrix products with BF16 operands and FP32
+    accumulation; "fp32": FP32 throughout (check mode)."""
+
+    def __init__(self, params, batch_cap=4096, precision="bf16", device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self._L = lib()
+        self.cap = int(batch_cap)
+        nb = self._L.mlp_workspace_bytes(self.cap)
+        if nb == 0:
+            raise TurretError(1, "invalid batch capacity")
+        self._ws, ptr = _aligned_workspace(torch, nb, self.device)
+        p = _arr(params, np.float32)
+        m = C.c_void_p()
+        rc = self._L.mlp_init(C.byref(m), self.cap, {"bf16": 0, "fp32": 1}[precision], p.ctypes.data_as(_fp),
+                              C.c_void_p(ptr), C.c_size_t(nb), C.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise TurretError(rc, self._L.mlp_last_error(None).decode())
+        self.m = m
+        self.precision = precision
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TurretError(rc, self._L.mlp_last_error(self.m).decode())
+
+    def _dev(self, a, shape):
+        t = a if isinstance(a, self.torch.Tensor) else self.torch.as_tensor(np.asarray(a, dtype=np.float32))
+        t = t.to(device=self.device, dtype=self.torch.float32).contiguous()
+        assert tuple(t.shape) == shape, (t.shape, shape)
+        return t
+
+    def set_params(self, params):
+        p = _arr(params, np.float32)
+        self._check(self._L.mlp_set_params(self.m, p.ctypes.data_as(_fp)))
+
+    def params(self):
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(self._L.mlp_get_params(self.m, p.ctypes.data_as(_fp)))
+        return p
+
+    def set_norm(self, mean_x, std_x, mean_y, std_y):
+        a = [_arr(v, np.float32) for v in (mean_x, std_x, mean_y, std_y)]
+        self._check(self._L.mlp_set_norm(self.m, *[v.ctypes.data_as(_fp) for v in a]))
+        self.norm = tuple(np.array(v) for v in a)
+
+    def _run(self, fn, x):
+        n = x.shape[0]
+        xt = self._dev(x, (n, MLP_IN))
+        y = self.torch.empty((n, MLP_OUT), dtype=self.torch.float32, device=self.device)
+        self.torch.cuda.current_stream(self.device).synchronize()
+        self._check(fn(self.m, C.c_void_p(xt.data_ptr()), n, C.c_void_p(y.data_ptr())))
+        self.stream.synchronize()
+        return y
+
+    def forward(self, x):
+        """Outputs [n][6] of rows x [n][34] through the training kernels."""
+        return self._run(self._L.mlp_forward, x)
+
+    def infer(self, x):
+        """Outputs [n][6] through the fused inference kernel of the predictor."""
+        return self._run(self._L.mlp_infer, x)
+
+    def loss_grad(self, x, y):
+        n = x.shape[0]
+        xt, yt = self._dev(x, (n, MLP_IN)), self._dev(y, (n, MLP_OUT))
+        g = self.torch.empty(MLP_NPARAM, dtype=self.torch.float32, device=self.device)
+        L = C.c_float()
+        self.torch.cuda.current_stream(self.device).synchronize()
+        self._check(self._L.mlp_loss_grad(self.m, C.c_void_p(xt.data_ptr()), C.c_void_p(yt.data_ptr()), n,
+                                          C.byref(L), C.c_void_p(g.data_ptr())))
+        return float(L.value), g
+
+    def train_step(self, x, y, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, want_loss=True):
+        """One AdamW step; x, y float32 CUDA tensors [n][34], [n][6] (n <= batch_cap)."""
+        n = x.shape[0]
+        opt = AdamW(lr, beta1, beta2, eps, weight_decay)
+        L = C.c_float()
+        self._check(self._L.mlp_train_step(self.m, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), n,
+                                           C.byref(opt), C.byref(L) if want_loss else None))
+        return float(L.value) if want_loss else None
+
+    def close(self):
+        if getattr(self, "m", None) is not None:
+            self._L.mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_samples(records):
+    """Training pairs (x [n-4][34], y [n-4][6]) from consecutive trajectory
+    records (float64 CUDA tensor [n][32]), built on the GPU."""
+    import torch
+    n = records.shape[0]
+    if n < 5:
+        raise TurretError(1, "at least five records are needed")
+    dev = records.device
+    x = torch.empty((n - 4, MLP_IN), dtype=torch.float32, device=dev)
+    y = torch.empty((n - 4, MLP_OUT), dtype=torch.float32, device=dev)
+    bad = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    rc = lib().mlp_build_samples(C.c_void_p(records.contiguous().data_ptr()), n, C.c_void_p(x.data_ptr()),
+                                 C.c_void_p(y.data_ptr()), C.c_void_p(bad.data_ptr()), C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise TurretError(rc, "mlp_build_samples failed")
+    if int(bad.item()) != 0:
+        raise TurretError(1, "%d samples span non-consecutive time levels" % int(bad.item()))
+    return x, y

@@ -90,3 +90,57 @@ def test_adamw_bias_correction_with_a_constant_gradient():
         p, m, v = M.adamw(p, g, m, v, step, lr, eps=eps, wd=wd)
         want = q - lr * (g / (np.abs(g) + eps) + wd * mask * q)
         assert np.allclose(p, want, rtol=0, atol=1e-15)
+
+
+def _rot(axis, deg):
+    a = math.radians(deg)
+    c, s = math.cos(a), math.sin(a)
+    return {"x": np.array([[1, 0, 0], [0, c, -s], [0, s, c]]),
+            "y": np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]]),
+            "z": np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])}[axis]
+
+
+def _matrix_of(q):
+    # rotation matrix of a unit quaternion (w, x, y, z) (textbook form)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_quaternion_special_rotations():
+    assert np.allclose(M.quaternion(np.eye(3)), [1, 0, 0, 0], atol=1e-15)
+    for deg in (10.0, 75.0, 170.0):
+        h = math.radians(deg) / 2
+        assert np.allclose(M.quaternion(_rot("z", deg)), [math.cos(h), 0, 0, math.sin(h)], atol=1e-14)
+        assert np.allclose(M.quaternion(_rot("x", deg)), [math.cos(h), math.sin(h), 0, 0], atol=1e-14)
+    # half turns: w = 0, the axis carries the sign convention's remaining freedom
+    for axis, e in (("x", 1), ("y", 2), ("z", 3)):
+        q = M.quaternion(_rot(axis, 180.0))
+        assert abs(q[0]) < 1e-12 and abs(abs(q[e]) - 1.0) < 1e-12
+
+
+def test_quaternion_reconstructs_random_rotations():
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        A = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+        if np.linalg.det(A) < 0:
+            A[:, 0] = -A[:, 0]
+        q = M.quaternion(A)
+        assert abs(np.linalg.norm(q) - 1) < 1e-13 and q[0] >= 0
+        assert np.allclose(_matrix_of(q), A, atol=1e-12)
+
+
+def test_features_are_frame_invariant():
+    # rotating the lab frame rotates M's columns and every lab vector alike:
+    # body-frame features are unchanged
+    rng = np.random.default_rng(2)
+    M0 = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+    M0 *= np.sign(np.linalg.det(M0))
+    v, w = rng.standard_normal(3), rng.standard_normal(3)
+    Fh, Th = rng.standard_normal((4, 3)), rng.standard_normal((4, 3))
+    Rl = _rot("y", 33.0) @ _rot("z", -71.0)
+    a = M.features(M0, v, w, Fh, Th)
+    b = M.features(M0 @ Rl.T, Rl @ v, Rl @ w, Fh @ Rl.T, Th @ Rl.T)
+    assert np.allclose(a[4:], b[4:], atol=1e-12)
+    assert a.shape == (34,)
