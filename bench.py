@@ -271,7 +271,51 @@ def ensemble_leg(dev, K, W, tile_cache):
         t.close()
     out["speedup_batched_mixed_vs_plain_f32"] = (out["batched_mixed"]["particle_steps_per_s"] /
                                                  out["plain_f32_sequential"]["particle_steps_per_s"])
+    # the surrogate: trained on the solver's own trajectories, then driving
+    # the predictor of the mixed-storage batched ensemble
+    net, sur = surrogate_leg(dev)
+    out["surrogate"] = sur
+    mixed = configs.load_ensemble(base, device=dev)
+    for t in mixed:
+        t.set_predictor("mlp", net)
+    batched(mixed, "batched_mixed_surrogate")
+    out["batched_mixed_surrogate"]["gpu_launches_per_step"] += 1  # the prediction
+    st = [t.predictor_stats() for t in mixed]
+    out["batched_mixed_surrogate"]["network_predictions"] = sum(s["net_steps"] for s in st)
+    out["batched_mixed_surrogate"]["fallbacks"] = sum(s["fallbacks"] for s in st)
+    for t in mixed:
+        t.close()
+    net.close()
+    out["speedup_batched_mixed_surrogate_vs_plain_f32"] = (
+        out["batched_mixed_surrogate"]["particle_steps_per_s"] / out["plain_f32_sequential"]["particle_steps_per_s"])
     return out
+
+
+def surrogate_leg(dev):
+    """Train the force/torque network on trajectories of a batched settling
+    ensemble (32 runs, 1500 steps; early stopping on 8 more) and compare its
+    one-step force error on 8 held-out runs with linear extrapolation."""
+    import time as _t
+
+    import torch
+
+    from paper_2408_15115_gb300 import configs
+    from paper_2408_15115_gb300 import surrogate as S
+
+    mk = lambda n, seed: configs.ensemble(n, seed=seed, storage="f32", d_range=(8.0, 16.0))
+    t0 = _t.perf_counter()
+    x, y = S.dataset(S.record_ensemble(mk(32, 11), 1500, device=dev))
+    xv, yv = S.dataset(S.record_ensemble(mk(8, 12), 1500, device=dev))
+    xt, yt = S.dataset(S.record_ensemble(mk(8, 13), 1500, device=dev))
+    torch.cuda.synchronize(dev)
+    t1 = _t.perf_counter()
+    net, hist = S.train(x, y, epochs=30, batch=4096, lr=1e-3, weight_decay=1e-4, val=(xv, yv), device=dev)
+    torch.cuda.synchronize(dev)
+    t2 = _t.perf_counter()
+    e = S.offline_errors(net, xt, yt)
+    return net, {"train_pairs": int(x.shape[0]), "epochs": len(hist), "collect_s": t1 - t0, "train_s": t2 - t1,
+                 "best_val_loss": min(h[1] for h in hist),
+                 "held_out_mean_rel_force_error": {k: float(v.mean()) for k, v in e.items()}}
 
 
 def run_ours(args):

@@ -395,6 +395,20 @@ TURRET_API turret_status turret_query_predictor(turret_ctx *c, turret_predictor_
 TURRET_API turret_status mlp_build_samples(const double *records, int64_t n_records, float *x, float *y, int32_t *bad,
                                            void *stream);
 
+/* ---- checkpoints --------------------------------------------------------------- */
+
+/* Writes the state of the context at its current time level to a file:
+ * post-collision populations (storage precision as is), the top-plane ghost
+ * velocity, the rigid-body and window state (ring offset, origin, slots,
+ * step count, F, T, predictor history), h_imm on the support box and the
+ * Lagrangian IBM force.  Waits for the stream.                              */
+TURRET_API turret_status turret_save(turret_ctx *c, const char *path);
+/* Restores a checkpoint into a context created with the same window,
+ * storage, viscosity, density ratio, gravity and flags and loaded with the
+ * same surface (TURRET_ESTATE otherwise); stepping then continues bit for
+ * bit as from the saved context.  Waits.                                   */
+TURRET_API turret_status turret_load(turret_ctx *c, const char *path);
+
 /* Releases the context (not the caller's workspaces).                       */
 TURRET_API turret_status lbm_destroy(turret_ctx *c);
 

@@ -21,6 +21,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <map>
 #include <string>
 #include <utility>
@@ -794,6 +796,126 @@ static turret_status copy_fields(turret_ctx *c, float *dev_out, bool pops) {
 
 extern "C" turret_status lbm_copy_macro(turret_ctx *c, float *dev_out) { return copy_fields(c, dev_out, false); }
 extern "C" turret_status lbm_copy_populations(turret_ctx *c, float *dev_out) { return copy_fields(c, dev_out, true); }
+
+// ---------------------------------------------------------------------------
+// Checkpoints.  The state of a context at time level t (parity p = t % 2):
+// the post-collision populations f*(t-1) in f[p] (storage precision as is),
+// the top-plane ghost velocity in utop[1 - p], the device state (body and
+// window slots, F, T, status, predictor history), h_imm(t) on the support
+// box and the Lagrangian force h (hl, the warm start of the next cycles).
+// Everything else a step reads is rebuilt by the step itself.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, storage, has_particle, nm;
+    turret_window win;
+    turret_flags flags;
+    double nu, kappa, g[3];
+    int64_t step, nbox;
+    int64_t bytes_pop, bytes_utop, bytes_state, bytes_h, bytes_hl;
+};
+const char CKPT_MAGIC[8] = {'T', 'U', 'R', 'R', 'E', 'T', 'C', 'K'};
+
+bool same_config(const CkptHeader &h, const turret_ctx *c) {
+    return h.storage == c->storage && h.has_particle == (c->has_particle ? 1 : 0) &&
+           h.nm == (c->has_particle ? c->nm : 0) && memcmp(&h.win, &c->win, sizeof(turret_window)) == 0 &&
+           h.flags.force_scheme == c->flags.force_scheme && h.flags.rot_form == c->flags.rot_form &&
+           h.flags.gravity == c->flags.gravity && h.flags.ibm_cycles == c->flags.ibm_cycles && h.nu == c->nu &&
+           h.kappa == c->kappa && h.g[0] == c->g[0] && h.g[1] == c->g[1] && h.g[2] == c->g[2] &&
+           h.nbox == (c->has_particle ? c->box.nbox : 0);
+}
+
+void fill_header(CkptHeader &h, const turret_ctx *c) {
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.storage = c->storage;
+    h.has_particle = c->has_particle ? 1 : 0;
+    h.nm = c->has_particle ? c->nm : 0;
+    h.win = c->win;
+    h.flags = c->flags;
+    h.nu = c->nu;
+    h.kappa = c->kappa;
+    for (int a = 0; a < 3; ++a) h.g[a] = c->g[a];
+    h.step = c->step;
+    h.nbox = c->has_particle ? c->box.nbox : 0;
+    h.bytes_pop = 27 * c->geom.ncell * (int64_t)storage_bytes(c->storage);
+    h.bytes_utop = 3 * c->geom.plane * 4;
+    h.bytes_state = sizeof(DevState);
+    h.bytes_h = 3 * h.nbox * 4;
+    h.bytes_hl = 3 * (int64_t)h.nm * 4;
+}
+}  // namespace
+
+extern "C" turret_status turret_save(turret_ctx *c, const char *path) {
+    if (!c || !path) return fail(c, TURRET_EINVAL, "NULL argument");
+    CkptHeader h;
+    fill_header(h, c);
+    const int p = (int)(c->step & 1);
+    struct Part {
+        const void *dev;
+        int64_t bytes;
+    } parts[5] = {{c->f[p], h.bytes_pop},
+                  {c->utop[1 - p], h.bytes_utop},
+                  {c->dstate, h.bytes_state},
+                  {c->has_particle ? c->ba.h : nullptr, h.bytes_h},
+                  {c->has_particle ? c->mk.hl : nullptr, h.bytes_hl}};
+    CK(cudaStreamSynchronize(c->stream), "save sync");
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(c, TURRET_EINVAL, std::string("cannot open ") + path);
+    bool ok = fwrite(&h, sizeof h, 1, fp) == 1;
+    std::vector<char> buf;
+    for (const Part &q : parts) {
+        if (!ok || q.bytes == 0) continue;
+        buf.resize((size_t)q.bytes);
+        if (cudaMemcpy(buf.data(), q.dev, (size_t)q.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(fp);
+            return cuda_fail(c, cudaGetLastError(), "save copy");
+        }
+        ok = fwrite(buf.data(), 1, (size_t)q.bytes, fp) == (size_t)q.bytes;
+    }
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok) return fail(c, TURRET_EINVAL, std::string("write failed: ") + path);
+    return TURRET_OK;
+}
+
+extern "C" turret_status turret_load(turret_ctx *c, const char *path) {
+    if (!c || !path) return fail(c, TURRET_EINVAL, "NULL argument");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(c, TURRET_EINVAL, std::string("cannot open ") + path);
+    CkptHeader h, want;
+    fill_header(want, c);
+    if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != 1) {
+        fclose(fp);
+        return fail(c, TURRET_EINVAL, "not a checkpoint of this format");
+    }
+    if (!same_config(h, c) || h.bytes_pop != want.bytes_pop || h.bytes_state != want.bytes_state) {
+        fclose(fp);
+        return fail(c, TURRET_ESTATE, "checkpoint of a differently configured context");
+    }
+    CK(cudaStreamSynchronize(c->stream), "load sync");
+    const int p = (int)(h.step & 1);
+    void *dst[5] = {c->f[p], c->utop[1 - p], c->dstate, c->has_particle ? c->ba.h : nullptr,
+                    c->has_particle ? c->mk.hl : nullptr};
+    const int64_t bytes[5] = {h.bytes_pop, h.bytes_utop, h.bytes_state, h.bytes_h, h.bytes_hl};
+    std::vector<char> buf;
+    for (int k = 0; k < 5; ++k) {
+        if (bytes[k] == 0) continue;
+        buf.resize((size_t)bytes[k]);
+        if (fread(buf.data(), 1, (size_t)bytes[k], fp) != (size_t)bytes[k]) {
+            fclose(fp);
+            return fail(c, TURRET_EINVAL, "truncated checkpoint");
+        }
+        if (cudaMemcpy(dst[k], buf.data(), (size_t)bytes[k], cudaMemcpyHostToDevice) != cudaSuccess) {
+            fclose(fp);
+            return cuda_fail(c, cudaGetLastError(), "load copy");
+        }
+    }
+    fclose(fp);
+    c->step = h.step;
+    drop_graphs(c);
+    return TURRET_OK;
+}
 
 extern "C" turret_status lbm_destroy(turret_ctx *c) {
     if (!c) return TURRET_EINVAL;

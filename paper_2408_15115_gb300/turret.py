@@ -143,6 +143,9 @@ def lib():
         L.turret_query_predictor.argtypes = [vp, C.POINTER(PredictorStats)]
         L.mlp_build_samples.restype = C.c_int
         L.mlp_build_samples.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
+        for name in ("turret_save", "turret_load"):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = [vp, C.c_char_p]
         L.turret_time_collide.restype = C.c_int
         L.turret_time_collide.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float)]
         _lib = L
@@ -267,6 +270,14 @@ class Turret:
         out = self.torch.empty((27,) + self.shape, dtype=self.torch.float32, device=self.device)
         self._check(self._L.lbm_copy_populations(self.ctx, C.c_void_p(out.data_ptr())))
         return out
+
+    def save(self, path):
+        """Checkpoint of the current time level (see turret_save)."""
+        self._check(self._L.turret_save(self.ctx, os.fsencode(path)))
+
+    def load(self, path):
+        """Restore a checkpoint into this identically configured context."""
+        self._check(self._L.turret_load(self.ctx, os.fsencode(path)))
 
     def time_collide(self, threads, tx, minb, reps=20):
         """Mean microseconds of one collide+stream launch with the given launch

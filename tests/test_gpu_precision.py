@@ -90,3 +90,38 @@ def test_mixed_batched_ensemble_vs_plain_f32():
             assert _rel(h[late, 1].mean(), r[late, 1].mean()) < TOL_REDUCED, (st, c["name"], "velocity")
         for t in runs:
             t.close()
+
+
+def test_mixed_batched_surrogate_ensemble_vs_plain_f32():
+    # the combined form: FP16 storage, one launch per phase, and the network
+    # predictor (trained briefly on solver trajectories), against the plain FP32
+    # form; drag and settling velocity over steps 1000..2000 within 1 %
+    from paper_2408_15115_gb300 import surrogate as S
+    from paper_2408_15115_gb300 import turret as T
+    x, y = S.dataset(S.record_ensemble(configs.ensemble(8, seed=21, storage="f32", d_range=(8.0, 14.0)), 800))
+    net, _ = S.train(x, y, epochs=10, batch=2048, lr=1e-3)
+    cfgs = _ensemble_cfgs()
+    plain = configs.load_ensemble(cfgs)
+    ref = [_history(t.step, t.state, 2000, 50) for t in plain]
+    for t in plain:
+        t.close()
+    runs = configs.load_ensemble([dict(c, storage="f16") for c in cfgs])
+    for t in runs:
+        t.set_predictor("mlp", net)
+    b = T.Batch(runs)
+    hist = [[] for _ in runs]
+    for _ in range(2000 // 50):
+        b.step(50)
+        for k, t in enumerate(runs):
+            s = t.state()
+            hist[k].append((s["F"][2], s["v"][2], s["r"][2]))
+    b.close()
+    for k, c in enumerate(cfgs):
+        h, r = np.array(hist[k]), ref[k]
+        late = slice(20, 40)
+        assert _rel(h[late, 0].mean(), r[late, 0].mean()) < TOL_REDUCED, (c["name"], "drag")
+        assert _rel(h[late, 1].mean(), r[late, 1].mean()) < TOL_REDUCED, (c["name"], "velocity")
+    assert sum(t.predictor_stats()["net_steps"] for t in runs) > 0
+    for t in runs:
+        t.close()
+    net.close()
