@@ -21,8 +21,9 @@
 //   rebuild : per-axis factors X, X', X'' and 9 (y,z) pair terms, then
 //             3 FMAs per population (collide_factored below)
 // about 300 FP32 flops per cell.  Populations are stored as deviations
-// q_i = f_i - w_i (FP32) or q_i / w_i scaled (FP16/BF16); the moments use
-// drho = sum q, so no O(1) term cancels in single precision.
+// s_i = 216 (f_i - w_i) (FP32) or s_i / W_i scaled (FP16/BF16) and every
+// pass works in that storage domain (Codec); the moments use drho = sum s, so
+// no O(1) term cancels in single precision.
 //
 // Memory: SoA planes [27][z][y][x], one thread per cell, x fastest; each warp
 // reads 27 coalesced 128-byte rows (the +-1 x-shifts hit the same sectors in
@@ -42,19 +43,25 @@ __device__ __forceinline__ int zphys(int zl, int ring, int nz) {
 __device__ __forceinline__ float tau_of(const Geom &g, int zl) { return __ldg(g.tau_z + zl); }
 __device__ __forceinline__ float omega_of(const Geom &g, int zl) { return __ldg(g.omega_z + zl); }
 
-// Source coordinate along one axis for velocity index e (= xi + 1): returns
-// 0 (s valid, wrapped if periodic) or 1 (bounce-back through a no-slip face).
+// Source coordinate along one axis for velocity index e (= xi + 1) of a cell
+// c in [0, n): returns 0 (s valid, wrapped if periodic) or 1 (bounce-back
+// through a no-slip face).  Only xi = -1 can leave through the top face and
+// only xi = +1 through the bottom one.
 __device__ __forceinline__ int src_axis(int c, int e, int n, int bc, int &s) {
-    s = c - (e - 1);
-    if (s < 0) {
-        if (bc == BC_PERIODIC) { s += n; return 0; }
-        return 1;
+    if (e == 1) {
+        s = c;
+        return 0;
     }
-    if (s >= n) {
-        if (bc == BC_PERIODIC) { s -= n; return 0; }
-        return 1;
+    if (e == 0) {
+        s = c + 1;
+        if (s < n) return 0;
+        s = 0;
+        return bc == BC_PERIODIC ? 0 : 1;
     }
-    return 0;
+    s = c - 1;
+    if (s >= 0) return 0;
+    s = n - 1;
+    return bc == BC_PERIODIC ? 0 : 1;
 }
 
 // Deviation of the rest-density equilibrium f0_i(1, u) - w_i from the
@@ -63,9 +70,11 @@ __device__ __forceinline__ int src_axis(int c, int e, int n, int bc, int &s) {
 __device__ __forceinline__ float eqfac_m1(int e, float u) {
     return e == 1 ? -1.5f * u * u : (e == 2 ? (3.0f * u + 3.0f * u * u) : (-3.0f * u + 3.0f * u * u));
 }
+template <int ST>
 __device__ __forceinline__ float ghost_dev(int i, float ux, float uy, float uz) {
     float a = eqfac_m1(i % 3, ux), b = eqfac_m1((i / 3) % 3, uy), c = eqfac_m1(i / 9, uz);
-    return Wq(i) * (a + b + c + a * b + a * c + b * c + a * b * c);  // scaled deviation
+    const float w = Codec<ST>::scaled ? Codec<ST>::K : Wq(i);  // storage domain
+    return w * (a + b + c + a * b + a * c + b * c + a * b * c);
 }
 
 // Pull the 27 pre-collision scaled deviations of cell (x, y, zl) from the
@@ -103,7 +112,7 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
 #pragma unroll
                 for (int ex = 0; ex < 3; ++ex) {
                     const int i = ex + 3 * ey + 9 * ez;
-                    q[i] = Codec<ST>::load(f + i * ncell + row + sx[ex], i);
+                    q[i] = Codec<ST>::load(f + i * ncell + row + sx[ex]);
                 }
             }
         return;
@@ -118,32 +127,45 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
 #pragma unroll
             for (int ex = 0; ex < 3; ++ex) {
                 const int i = ex + 3 * ey + 9 * ez;
+                // (bounce-back: W_{26-i} = W_i, so the opposite population's stored
+                // value is this one's in every storage domain)
                 if (bxf[ex] == 1 || byf[ey] == 1 || bzf[ez] == 1) {
-                    q[i] = own_rest ? 0.0f : Codec<ST>::load(f + (26 - i) * ncell + own, 26 - i);
+                    q[i] = own_rest ? 0.0f : Codec<ST>::load(f + (26 - i) * ncell + own);
                 } else if (bzf[ez] == 3) {
                     q[i] = 0.0f;
                 } else if (bzf[ez] == 2) {
                     const int c = sy[ey] * nx + sx[ex];
-                    q[i] = ghost_dev(i, __ldg(utop + c), __ldg(utop + plane + c), __ldg(utop + 2 * plane + c));
+                    q[i] = ghost_dev<ST>(i, __ldg(utop + c), __ldg(utop + plane + c), __ldg(utop + 2 * plane + c));
                 } else {
-                    q[i] = Codec<ST>::load(f + i * ncell + szp[ez] * plane + sy[ey] * nx + sx[ex], i);
+                    q[i] = Codec<ST>::load(f + i * ncell + szp[ez] * plane + sy[ey] * nx + sx[ex]);
                 }
             }
 }
 
 // Raw moments of the scaled deviations up to second order (all times 216):
 // drho = sum s, j = sum xi s, Pi'_ab = sum xi_a xi_b s, by three separable
-// 3-point passes.
+// 3-point passes.  From a storage domain r_i = K s_i / W_i the passes carry
+// the axis weights W1 = (1, 4, 1) of the sums that need them (the 4 sits on
+// xi = 0, where the xi-weighted sums vanish anyway) and the result is
+// divided by K (exact).
 struct Mom {
     float drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
+// a + W1(1) b + c: the centre weight applied in the storage domains
+template <bool SC>
+__device__ __forceinline__ float wsum3(float a, float b, float c) {
+    return SC ? fmaf(4.0f, b, a + c) : a + b + c;
+}
+
+template <int ST>
 __device__ __forceinline__ Mom moments27(const float q[27]) {
+    constexpr bool SC = Codec<ST>::scaled;
     float A0[9], A1[9], A2[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {  // k = ey + 3 ez; x pass
         const float a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
-        A0[k] = a + b + c;
+        A0[k] = wsum3<SC>(a, b, c);
         A1[k] = c - a;
         A2[k] = c + a;
     }
@@ -151,24 +173,29 @@ __device__ __forceinline__ Mom moments27(const float q[27]) {
 #pragma unroll
     for (int ez = 0; ez < 3; ++ez) {  // y pass
         const int k = 3 * ez;
-        B00[ez] = A0[k] + A0[k + 1] + A0[k + 2];
+        B00[ez] = wsum3<SC>(A0[k], A0[k + 1], A0[k + 2]);
         B01[ez] = A0[k + 2] - A0[k];
         B02[ez] = A0[k + 2] + A0[k];
-        B10[ez] = A1[k] + A1[k + 1] + A1[k + 2];
+        B10[ez] = wsum3<SC>(A1[k], A1[k + 1], A1[k + 2]);
         B11[ez] = A1[k + 2] - A1[k];
-        B20[ez] = A2[k] + A2[k + 1] + A2[k + 2];
+        B20[ez] = wsum3<SC>(A2[k], A2[k + 1], A2[k + 2]);
     }
     Mom m;  // z pass
-    m.drho = B00[0] + B00[1] + B00[2];
+    m.drho = wsum3<SC>(B00[0], B00[1], B00[2]);
     m.jz = B00[2] - B00[0];
     m.pzz = B00[2] + B00[0];
-    m.jy = B01[0] + B01[1] + B01[2];
+    m.jy = wsum3<SC>(B01[0], B01[1], B01[2]);
     m.pyz = B01[2] - B01[0];
-    m.pyy = B02[0] + B02[1] + B02[2];
-    m.jx = B10[0] + B10[1] + B10[2];
+    m.pyy = wsum3<SC>(B02[0], B02[1], B02[2]);
+    m.jx = wsum3<SC>(B10[0], B10[1], B10[2]);
     m.pxz = B10[2] - B10[0];
-    m.pxy = B11[0] + B11[1] + B11[2];
-    m.pxx = B20[0] + B20[1] + B20[2];
+    m.pxy = wsum3<SC>(B11[0], B11[1], B11[2]);
+    m.pxx = wsum3<SC>(B20[0], B20[1], B20[2]);
+    if (SC && Codec<ST>::K != 1.0f) {
+        constexpr float ik = 1.0f / Codec<ST>::K;
+        m.drho *= ik; m.jx *= ik; m.jy *= ik; m.jz *= ik; m.pxx *= ik;
+        m.pyy *= ik; m.pzz *= ik; m.pxy *= ik; m.pxz *= ik; m.pyz *= ik;
+    }
     return m;
 }
 
@@ -210,11 +237,14 @@ __device__ __forceinline__ Macro macro_of(const Mom &m) {
 //   s_i = 216 (f*_i - w_i) = [rho X Y Z - W_i] + X'' [P'xx/2 Y Z]
 //         + X [P'yy/2 Y'' Z + P'zz/2 Y Z'' + P'yz Y' Z'] + X' [P'xy Y' Z + P'xz Y Z'],
 // the bracketed equilibrium deviation evaluated as W_i (rho E + drho) with
-// E = (1+a_x)(1+a_y)(1+a_z) - 1 expanded so no O(1) term cancels.
+// E = (1+a_x)(1+a_y)(1+a_z) - 1 expanded so no O(1) term cancels.  In the
+// scaled storage domains every per-axis factor is divided by W1(e), which
+// divides each product by W_i: X / W1 = 1 + a, X' / W1, X'' / W1 = (6, -3, 6).
 struct AxisF {
     float a[3], X[3], Xp[3];
 };
 
+template <bool SC>
 __device__ __forceinline__ AxisF axis_of(float u) {
     AxisF f;
     const float u2 = u * u;
@@ -222,15 +252,16 @@ __device__ __forceinline__ AxisF axis_of(float u) {
     f.a[1] = -1.5f * u2;
     f.a[2] = 3.0f * (u2 + u);
     f.X[0] = 1.0f + f.a[0];
-    f.X[1] = 4.0f * (1.0f + f.a[1]);
+    f.X[1] = SC ? 1.0f + f.a[1] : 4.0f * (1.0f + f.a[1]);
     f.X[2] = 1.0f + f.a[2];
     f.Xp[0] = 6.0f * u - 3.0f;
-    f.Xp[1] = -12.0f * u;
+    f.Xp[1] = SC ? -3.0f * u : -12.0f * u;
     f.Xp[2] = 6.0f * u + 3.0f;
     return f;
 }
 
-// Scaled equilibrium deviation 216 (f0_i(rho, u) - w_i), times c, into s.
+// Equilibrium deviation W_i (rho E + drho) (SC: rho E + drho), times c, into s.
+template <bool SC>
 __device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
                                            float drho, float c, float s[27], bool first) {
     float sxy[9];
@@ -244,33 +275,38 @@ __device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, con
         for (int k = 0; k < 9; ++k) {
             const int i = k + 9 * ez;
             const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
-            const float v = (c * Wq(i)) * fmaf(E, rho, drho);
+            const float v = (SC ? c : c * Wq(i)) * fmaf(E, rho, drho);
             s[i] = first ? v : s[i] + v;
         }
 }
 
-// Post-collision scaled deviations s_i = 216 (f*_i - w_i) of one cell.
-// forced: equilibrium part (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
-// f0(u + tau h) (scheme 1), both reducing to f0(u) at h = 0.
+// Post-collision populations of one cell in the storage domain of ST
+// (FP32: s_i = 216 (f*_i - w_i)).  forced: equilibrium part
+// (1-w) f0(u) + w f0(u + tau h) (scheme 0) or f0(u + tau h) (scheme 1), both
+// reducing to f0(u) at h = 0.
+template <int ST>
 __device__ __forceinline__ void collide_factored(const Macro &M, float omega, float tau, bool forced, float hx,
                                                  float hy, float hz, int scheme, float s[27]) {
-    const AxisF fx = axis_of(M.ux), fy = axis_of(M.uy), fz = axis_of(M.uz);
+    constexpr bool SC = Codec<ST>::scaled;
+    constexpr float K = Codec<ST>::K;
+    const AxisF fx = axis_of<SC>(M.ux), fy = axis_of<SC>(M.uy), fz = axis_of<SC>(M.uz);
     if (!forced) {
-        add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f, s, true);
+        add_eq_dev<SC>(fx, fy, fz, M.rho, M.drho, K, s, true);
     } else {
-        const AxisF vx = axis_of(M.ux + tau * hx), vy = axis_of(M.uy + tau * hy), vz = axis_of(M.uz + tau * hz);
+        const AxisF vx = axis_of<SC>(M.ux + tau * hx), vy = axis_of<SC>(M.uy + tau * hy),
+                    vz = axis_of<SC>(M.uz + tau * hz);
         if (scheme == 1) {
-            add_eq_dev(vx, vy, vz, M.rho, M.drho, 1.0f, s, true);
+            add_eq_dev<SC>(vx, vy, vz, M.rho, M.drho, K, s, true);
         } else {
-            add_eq_dev(fx, fy, fz, M.rho, M.drho, 1.0f - omega, s, true);
-            add_eq_dev(vx, vy, vz, M.rho, M.drho, omega, s, false);
+            add_eq_dev<SC>(fx, fy, fz, M.rho, M.drho, K * (1.0f - omega), s, true);
+            add_eq_dev<SC>(vx, vy, vz, M.rho, M.drho, K * omega, s, false);
         }
     }
-    // P' = (1 - 1/tau) P1 with P1 = P1~ / 216
-    const float om1 = (1.0f - omega) * INV_SCALE;
+    // P' = (1 - 1/tau) P1 with P1 = P1~ / 216 (times K in the storage domain)
+    const float om1 = (1.0f - omega) * (INV_SCALE * K);
     const float hxx = 0.5f * om1 * M.Pxx, hyy = 0.5f * om1 * M.Pyy, hzz = 0.5f * om1 * M.Pzz;
     const float pxy = om1 * M.Pxy, pxz = om1 * M.Pxz, pyz = om1 * M.Pyz;
-    const float Xpp[3] = {6.0f, -12.0f, 6.0f};
+    const float Xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};
     float cY[3], cZ[3], bY[3], aY[3], bZ[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -340,13 +376,15 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
         zl = cz;
         if (x >= g.nx || y >= g.ny) return;
         if (MODE == K1_FAR) {
-            const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
-            const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
+            // the z test first: zl is the same for a whole block (plane)
             const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
-            if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
-                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN) &&
-                (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN))
-                return;
+            if ((unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN)) {
+                const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
+                const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
+                if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
+                    (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN))
+                    return;
+            }
         }
     }
     const int ring = S.ring;
@@ -367,7 +405,7 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
             forced = true;
         }
     }
-    const Macro M = macro_of(moments27(q));
+    const Macro M = macro_of(moments27<ST>(q));
     if (zl == g.nz - 1) {
         const size_t c = (size_t)y * g.nx + x;
         utop_out[c] = M.ux;
@@ -375,13 +413,13 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
         utop_out[2 * g.plane + c] = M.uz;
     }
     if (MODE == K1_ALLF || MODE == K1_NEAR)
-        collide_factored(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
+        collide_factored<ST>(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
     else
-        collide_factored(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
+        collide_factored<ST>(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
     const int own = zphys(zl, ring, g.nz) * (int)g.plane + y * g.nx + x;
     const int ncell = (int)g.ncell;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i], i);
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i]);
 }
 
 // Tile of a 1-D block of blockDim.x threads over (x, y): tx threads along x,
@@ -545,7 +583,7 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
     }
     float q[27];
     pull27<ST>(g, src, c[0], c[1], c[2], st->s[slot].ring, st->s[slot].reseed, utop_in, q);
-    const Macro M = macro_of(moments27(q));
+    const Macro M = macro_of(moments27<ST>(q));
     const float tau = tau_of(g, c[2]);
     const float k2 = (0.5f / tau - 1.0f) * INV_SCALE;  // P1 = P1~ / 216
     const float p = M.drho * (1.0f / 3.0f);

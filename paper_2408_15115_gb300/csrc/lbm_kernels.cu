@@ -36,9 +36,9 @@ __global__ void k_init_equilibrium(Geom g, typename Codec<ST>::T *__restrict__ d
     M.uz = u ? (float)u[3 * c + 2] : 0.0f;
     M.Pxx = M.Pyy = M.Pzz = M.Pxy = M.Pxz = M.Pyz = 0.0f;
     float q[27];
-    collide_factored(M, 1.0f, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
+    collide_factored<ST>(M, 1.0f, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
 #pragma unroll
-    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + c, q[i], i);
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + c, q[i]);
     const long long z = c / g.plane;
     if (z == g.nz - 1) {
         const long long p = c - z * g.plane;
@@ -60,12 +60,13 @@ __global__ void __launch_bounds__(128) k_macro(Geom g, const typename Codec<ST>:
     float q[27];
     pull27<ST>(g, src, x, y, zl, st->s[slot].ring, st->s[slot].reseed, utop_in, q);
     const size_t c = ((size_t)zl * g.ny + y) * g.nx + x;
-    if (pops) {
+    if (pops) {  // f_i - w_i = s_i / 216 = r_i W_i / (216 K)
 #pragma unroll
-        for (int i = 0; i < 27; ++i) out[(size_t)i * g.ncell + c] = q[i] * INV_SCALE;
+        for (int i = 0; i < 27; ++i)
+            out[(size_t)i * g.ncell + c] = q[i] * ((Codec<ST>::scaled ? Wq(i) / Codec<ST>::K : 1.0f) * INV_SCALE);
         return;
     }
-    const Macro M = macro_of(moments27(q));
+    const Macro M = macro_of(moments27<ST>(q));
     out[c] = M.rho;
     out[g.ncell + c] = M.ux;
     out[2 * g.ncell + c] = M.uy;

@@ -212,30 +212,37 @@ constexpr float INV_SCALE = 1.0f / 216.0f;
 __host__ __device__ constexpr float W1(int e) { return e == 1 ? 4.0f : 1.0f; }
 __host__ __device__ constexpr float Wq(int i) { return W1(i % 3) * W1((i / 3) % 3) * W1(i / 9); }
 
-// Storage codec for the scaled deviation s_i (FP32 arithmetic in every case).
-//   FP32: s_i as is.
-//   FP16: s_i / W_i * 16 = (f_i - w_i) / w_i * 16, which keeps corner
-//         populations out of subnormals; BF16: s_i / W_i.  All scalings are
-//         exact powers of two or exact integers.
+// Storage codec.  The kernels work in each type's storage domain, in FP32
+// arithmetic:
+//   FP32: r_i = s_i, the scaled deviation itself;
+//   FP16: r_i = K s_i / W_i with K = 16 = 16 (f_i - w_i) / w_i, which keeps
+//         corner populations out of subnormals;
+//   BF16: r_i = s_i / W_i (K = 1).
+// The weights W_i = W1(x) W1(y) W1(z) are exact integers and separable, so
+// the scalings fold into the separable moment passes (weights 1, 4, 1 per
+// axis) and into the per-axis factors of the collision: loads and stores
+// are plain conversions (RN-even on store).
 template <int ST> struct Codec;
 template <> struct Codec<ST_F32> {
     using T = float;
-    static __device__ __forceinline__ float load(const T *p, int) { return __ldg(p); }
-    static __device__ __forceinline__ void store(T *p, float s, int) { *p = s; }
+    static constexpr bool scaled = false;
+    static constexpr float K = 1.0f;
+    static __device__ __forceinline__ float load(const T *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store(T *p, float r) { *p = r; }
 };
 template <> struct Codec<ST_F16> {
     using T = __half;
-    static __device__ __forceinline__ float load(const T *p, int i) {
-        return __half2float(__ldg(p)) * (Wq(i) * 0.0625f);
-    }
-    static __device__ __forceinline__ void store(T *p, float s, int i) {
-        *p = __float2half_rn(s * (16.0f / Wq(i)));
-    }
+    static constexpr bool scaled = true;
+    static constexpr float K = 16.0f;
+    static __device__ __forceinline__ float load(const T *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void store(T *p, float r) { *p = __float2half_rn(r); }
 };
 template <> struct Codec<ST_BF16> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float load(const T *p, int i) { return __bfloat162float(__ldg(p)) * Wq(i); }
-    static __device__ __forceinline__ void store(T *p, float s, int i) { *p = __float2bfloat16_rn(s * (1.0f / Wq(i))); }
+    static constexpr bool scaled = true;
+    static constexpr float K = 1.0f;
+    static __device__ __forceinline__ float load(const T *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void store(T *p, float r) { *p = __float2bfloat16_rn(r); }
 };
 
 inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
