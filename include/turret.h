@@ -160,8 +160,10 @@ TURRET_API turret_status ibm_load_surface(turret_ctx *c, const double *verts_bod
 /* Advances n coupled time steps in the order of Table 1: collide+stream with
  * h_imm(t), particle update with F(t), T(t), window slide, stress and velocity
  * at t+1 on the support box, F(t+1), T(t+1), IBM cycles -> h_imm(t+1).
- * Without a particle, advances the fluid alone.  Asynchronous; replays a CUDA
- * graph per step after the first call.                                      */
+ * Without a particle, advances the fluid alone.  Asynchronous; replays CUDA
+ * graphs: groups of 8 steps as one graph in which the immersed-boundary chain
+ * of a step overlaps the bulk collide+stream of the next (same results as
+ * one graph per step), the remaining steps one graph each.                  */
 TURRET_API turret_status step(turret_ctx *c, int64_t n);
 
 /* Advances the fluid alone by n collide+stream steps (Eq. 7 / Eq. 15 with
@@ -245,16 +247,16 @@ TURRET_API size_t turret_batch_workspace_bytes(int32_t n_runs);
  * stream wait for it, so query_particle_state on a context sees the batched
  * steps.  device_workspace: >= turret_batch_workspace_bytes, 256-byte
  * aligned.  Initial tiles: 128 threads per block, tile width 32, register
- * budget variant 3 (see turret_batch_set_tiles).                           */
+ * budget variant 2 (see turret_batch_set_tiles).                           */
 TURRET_API turret_status turret_batch_init(turret_batch **out, turret_ctx *const *ctxs, int32_t n_runs,
                                            void *device_workspace, size_t workspace_bytes, void *stream);
 
 /* Collide+stream launch shape of a batch: threads per block (64, 128, 256),
- * register-budget variant minb (3: <= 80 registers per thread, 4: <= 64, the
+ * register-budget variant minb (2: <= 128 registers per thread, 3: <= 85, the
  * number of resident 256-thread blocks per SM the compiler plans for) and per
  * run the tile width tx[r] in {16, 32, 64, 128} (<= threads; the tile covers
- * tx cells along x and threads / tx rows along y of one plane).  Results do
- * not depend on these.  Waits for the batch stream.                        */
+ * tx cells along x and threads / tx rows along y of a pair of planes, two
+ * cells per thread).  Results do not depend on these.  Waits.              */
 TURRET_API turret_status turret_batch_set_tiles(turret_batch *b, int32_t threads, int32_t minb, const int32_t *tx);
 
 /* Advances every run of the batch by n coupled steps (the order of step()).

@@ -17,8 +17,8 @@ from collections import namedtuple
 RunInfo = namedtuple("RunInfo", "nx storage cells handle")
 Choice = namedtuple("Choice", "threads minb tx predicted_us table")
 
-CANDIDATES = tuple((th, tx, mb) for th in (128, 256) for tx in (32, 64, 128) if tx <= th for mb in (3, 4))
-CACHE_VERSION = 1
+CANDIDATES = tuple((th, tx, mb) for th in (128, 256) for tx in (32, 64, 128) if tx <= th for mb in (2, 3))
+CACHE_VERSION = 2  # 2: collide+stream on plane pairs (new register budgets)
 
 
 def class_key(nx, storage):

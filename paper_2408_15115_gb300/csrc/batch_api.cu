@@ -164,7 +164,7 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
     b->d_runs = (RunDesc *)ws;
     b->d_prefix = (int *)((char *)ws + prefix_offset(n));
     b->threads = 128;
-    b->minb = 3;
+    b->minb = 2;
     b->cycles = ctxs[0]->flags.ibm_cycles;
     b->predictor = ctxs[0]->body.predictor != 0 ? 1 : 0;
     b->warm = (b->predictor && (ctxs[0]->body.pred_opts & PRED_WARM)) ? 1 : 0;
@@ -252,15 +252,15 @@ static cudaError_t batch_enqueue(turret_batch *b, int p) {
     const RunDesc *R = b->d_runs;
     CE(cudaEventRecord(b->ev_fork, b->stream));
     CE(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-    if (b->predictor) {  // the predictions overlap the near collide+stream
-        CE(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
-        CE(launch_batch_predict(R, n, p, b->aux));
-        CE(cudaEventRecord(b->ev_pred, b->aux));
-    }
+    // the predictions and the particle/marker updates run on the aux stream
+    // beside the near collide+stream
+    CE(cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+    if (b->predictor) CE(launch_batch_predict(R, n, p, b->aux));
+    CE(launch_batch_particle_markers(R, tab(T_PM), n, p, b->total[T_PM], b->aux));
+    CE(cudaEventRecord(b->ev_pred, b->aux));
     CE(launch_batch_collide(PHASE_BULK, R, tab(T_BULK), n, p, b->total[T_BULK], b->threads, b->minb, b->stream));
     CE(launch_batch_collide(PHASE_NEAR, R, tab(T_NEAR), n, p, b->total[T_NEAR], b->threads, 1, b->side));
-    if (b->predictor) CE(cudaStreamWaitEvent(b->side, b->ev_pred, 0));
-    CE(launch_batch_particle_markers(R, tab(T_PM), n, p, b->total[T_PM], b->side));
+    CE(cudaStreamWaitEvent(b->side, b->ev_pred, 0));
     CE(launch_batch_box_moments_bin(R, tab(T_MB), n, p, b->total[T_MB], b->side));
     CE(launch_batch_interp0(R, tab(T_IP), n, b->total[T_IP], b->warm, b->side));
     CE(cudaEventRecord(b->ev_red, b->side));

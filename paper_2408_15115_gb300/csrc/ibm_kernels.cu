@@ -545,6 +545,13 @@ __device__ __forceinline__ void interp0_tile_block(const BoxGeom &box, int nm, c
     }
 }
 
+__global__ void __launch_bounds__(ROWS_THREADS) k_interp0_tiles(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
+                                                                 const int *__restrict__ tile_list,
+                                                                 const int *__restrict__ tile_count, int cap,
+                                                                 DevState *st, int warm) {
+    interp0_tile_block(box, nm, m, ba, tile_list, tile_count, cap, st, blockIdx.x, warm);
+}
+
 // One cycle of steps l = 1..4 (Sec. 2.2) in matrix form:
 //   h_out_k = h_in_k + U_k - I[u* + S h_in](X_k) = h_in_k + r0_k - sum_j A_kj h_in_j.
 // One warp per marker, entries of the row in order per lane, xor-shuffle sum.
@@ -845,10 +852,13 @@ cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const Bo
 }
 
 cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
-                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s) {
+                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s, bool by_tile) {
     const int ntiles = box.tx * box.ty * box.tz;  // list 1 (rows of A) follows list 0
-    k_interp0_rows<<<nm, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
-                                               tile_count + ntiles, cap, st, warm);
+    if (by_tile)
+        k_interp0_tiles<<<ntiles, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list, tile_count, cap, st, warm);
+    else
+        k_interp0_rows<<<nm, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
+                                                   tile_count + ntiles, cap, st, warm);
     return cudaGetLastError();
 }
 

@@ -5,10 +5,10 @@
 
 namespace turret {
 
-// Register budget variants of the collide+stream launches, chosen by the
-// autotuner with the tile: MINB resident 256-thread blocks per SM, i.e. at most
-// 64 registers per thread for MINB = 4 (some spilling of the batched kernel's
-// descriptor values) and 80 for MINB = 3 (no spilling, fewer resident warps).
+// Register budget variants of the collide+stream launches (two cells per
+// thread), chosen by the autotuner with the tile: MINB resident 256-thread
+// blocks per SM, i.e. at most 128 registers per thread for MINB = 2 (no
+// spilling) and 85 for MINB = 3 (spills, more resident warps).
 // K1 over one window with a chosen tile (the autotuner's timing kernel): the
 // same cells and arithmetic as k_collide_stream, no window-slot carry.
 template <int ST, int MODE, int MINB>
@@ -18,8 +18,8 @@ __global__ void __launch_bounds__(256, MINB) k_collide_tiled(Geom g, const typen
                                                        float *__restrict__ utop_out, const DevState *st, int slot,
                                                        const float *__restrict__ hbox, BoxGeom box, int tx) {
     int cx, cy, cz;
-    tile_coords(blockIdx.x, tx, g.nx, g.ny, cx, cy, cz);
-    k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, cx, cy, cz);
+    tile_coords(blockIdx.x, tx, g.nx, g.ny, 2, cx, cy, cz);
+    k1_pair<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, cx, cy, cz);
 }
 
 // ---------------------------------------------------------------------------
@@ -39,14 +39,14 @@ __device__ __forceinline__ void batch_k1_run(const RunDesc &R, int p, int lb) {
     const BodySlot &S = R.st->s[p];
     int cx, cy, cz;
     if (PHASE == PHASE_BULK) {
-        tile_coords(lb, R.tx, g.nx, g.ny, cx, cy, cz);
-        k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+        tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
+        k1_pair<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
     } else if (R.split) {
-        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_MARGIN, box.By + 2 * NEAR_MARGIN, cx, cy, cz);
+        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_MARGIN, box.By + 2 * NEAR_MARGIN, 1, cx, cy, cz);
         k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
     } else {
-        tile_coords(lb, R.tx, g.nx, g.ny, cx, cy, cz);
-        k1_cell<ST, K1_ALLF>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+        tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
+        k1_pair<ST, K1_ALLF>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
     }
 }
 
@@ -110,7 +110,7 @@ static cudaError_t tiled_t(const Geom &g, const void *src, void *dst, const floa
                            int threads, int tx, cudaStream_t s) {
     using T = typename Codec<ST>::T;
     const int ty = threads / tx;
-    const unsigned nb = (unsigned)(((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty) * g.nz);
+    const unsigned nb = (unsigned)(((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty) * ((g.nz + 1) / 2));
     if (has_box)
         k_collide_tiled<ST, K1_ALLF, MINB><<<nb, threads, 0, s>>>(g, (const T *)src, (T *)dst, utop_in, utop_out, st, slot, hbox, box, tx);
     else
@@ -131,30 +131,30 @@ static cudaError_t tiled_m(const Geom &g, int storage, const void *src, void *ds
 
 bool valid_tile(int threads, int tx, int minb) {
     return (threads == 64 || threads == 128 || threads == 256) && (tx == 16 || tx == 32 || tx == 64 || tx == 128) &&
-           tx <= threads && (minb == 3 || minb == 4);
+           tx <= threads && (minb == 2 || minb == 3);
 }
 
 cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                  float *utop_out, const DevState *st, int slot, const float *hbox,
                                  const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s) {
     if (!valid_tile(threads, tx, minb)) return cudaErrorInvalidValue;
-    if (minb == 3) return tiled_m<3>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
-    return tiled_m<4>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+    if (minb == 2) return tiled_m<2>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
+    return tiled_m<3>(g, storage, src, dst, utop_in, utop_out, st, slot, hbox, box, has_box, threads, tx, s);
 }
 
-static int tile_blocks(int ex, int ey, int ez, int threads, int tx) {
+static int tile_blocks(int ex, int ey, int ez, int threads, int tx, int pz) {
     const int ty = threads / tx;
-    return ((ex + tx - 1) / tx) * ((ey + ty - 1) / ty) * ez;
+    return ((ex + tx - 1) / tx) * ((ey + ty - 1) / ty) * ((ez + pz - 1) / pz);
 }
 
 int blocks_bulk(const RunDesc &r, int threads) {
-    return r.split ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx) : 0;
+    return r.split ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2) : 0;
 }
 
 int blocks_near(const RunDesc &r, int threads) {
-    if (!r.split) return tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx);
+    if (!r.split) return tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2);
     return tile_blocks(r.box.Bx + 2 * NEAR_MARGIN, r.box.By + 2 * NEAR_MARGIN, r.box.Bz + 2 * NEAR_MARGIN, threads,
-                       r.tx);
+                       r.tx, 1);
 }
 
 int blocks_box_moments_bin(const RunDesc &r) {
@@ -166,15 +166,15 @@ cudaError_t launch_batch_collide(int phase, const RunDesc *runs, const int *pref
     if (nblocks <= 0) return cudaSuccess;
     if (phase == PHASE_NEAR)
         k_batch_collide<PHASE_NEAR, 1><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
-    else if (minb == 3)
-        k_batch_collide<PHASE_BULK, 3><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+    else if (minb == 2)
+        k_batch_collide<PHASE_BULK, 2><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
     else
-        k_batch_collide<PHASE_BULK, 4><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+        k_batch_collide<PHASE_BULK, 3><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
     return cudaGetLastError();
 }
 
 bool is_batch_bulk_kernel(const void *fn) {
-    return fn == (const void *)k_batch_collide<PHASE_BULK, 3> || fn == (const void *)k_batch_collide<PHASE_BULK, 4>;
+    return fn == (const void *)k_batch_collide<PHASE_BULK, 2> || fn == (const void *)k_batch_collide<PHASE_BULK, 3>;
 }
 
 cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,

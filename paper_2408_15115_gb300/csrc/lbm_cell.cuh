@@ -351,9 +351,11 @@ __device__ __forceinline__ int rel_axis(int c, int lo, int lo_w, int margin, int
 // FAR and NEAR together cover the window once.
 enum { K1_ALL = 0, K1_ALLF = 1, K1_FAR = 2, K1_NEAR = 3 };
 
-// One cell of K1.  (cx, cy, cz): window coordinates (x, y, logical z) for
-// ALL / ALLF / FAR, coordinates within the near region for NEAR; out-of-range
-// coordinates return.  S is the window slot of the pulled time level.
+// One cell of K1 (scalar arithmetic; the near-region launch, which is small
+// and on the critical path, runs one cell per thread).  (cx, cy, cz): window
+// coordinates (x, y, logical z) for ALL / ALLF / FAR, coordinates within the
+// near region for NEAR; out-of-range coordinates return.  S is the window
+// slot of the pulled time level.
 template <int ST, int MODE>
 __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
                                         typename Codec<ST>::T *__restrict__ dst, const float *__restrict__ utop_in,
@@ -422,16 +424,379 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
     for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i]);
 }
 
+// ---------------------------------------------------------------------------
+// K1 on a pair of cells (x, y, z) and (x, y, z + 1) per thread.  Every FP32
+// operation of the moments and the collision is issued once for both cells
+// as a packed f32x2 instruction (per lane the same correctly rounded
+// operation); the x/y source indices, boundary flags and region tests are
+// shared.  A cell's result never depends on the other cell of its pair.
+typedef float2 f2;
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 padd(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 psub(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }  // exact product
+__device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+
+template <bool SC>
+__device__ __forceinline__ f2 pwsum3(f2 a, f2 b, f2 c) {
+    return SC ? pfma(F2(4.0f), b, padd(a, c)) : padd(padd(a, b), c);
+}
+
+struct Mom2 {
+    f2 drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
+};
+
+template <int ST>
+__device__ __forceinline__ Mom2 moments27x2(const f2 q[27]) {
+    constexpr bool SC = Codec<ST>::scaled;
+    f2 A0[9], A1[9], A2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const f2 a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
+        A0[k] = pwsum3<SC>(a, b, c);
+        A1[k] = psub(c, a);
+        A2[k] = padd(c, a);
+    }
+    f2 B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez) {
+        const int k = 3 * ez;
+        B00[ez] = pwsum3<SC>(A0[k], A0[k + 1], A0[k + 2]);
+        B01[ez] = psub(A0[k + 2], A0[k]);
+        B02[ez] = padd(A0[k + 2], A0[k]);
+        B10[ez] = pwsum3<SC>(A1[k], A1[k + 1], A1[k + 2]);
+        B11[ez] = psub(A1[k + 2], A1[k]);
+        B20[ez] = pwsum3<SC>(A2[k], A2[k + 1], A2[k + 2]);
+    }
+    Mom2 m;
+    m.drho = pwsum3<SC>(B00[0], B00[1], B00[2]);
+    m.jz = psub(B00[2], B00[0]);
+    m.pzz = padd(B00[2], B00[0]);
+    m.jy = pwsum3<SC>(B01[0], B01[1], B01[2]);
+    m.pyz = psub(B01[2], B01[0]);
+    m.pyy = pwsum3<SC>(B02[0], B02[1], B02[2]);
+    m.jx = pwsum3<SC>(B10[0], B10[1], B10[2]);
+    m.pxz = psub(B10[2], B10[0]);
+    m.pxy = pwsum3<SC>(B11[0], B11[1], B11[2]);
+    m.pxx = pwsum3<SC>(B20[0], B20[1], B20[2]);
+    if (SC && Codec<ST>::K != 1.0f) {
+        const f2 ik = F2(1.0f / Codec<ST>::K);
+        m.drho = pmul(m.drho, ik); m.jx = pmul(m.jx, ik); m.jy = pmul(m.jy, ik); m.jz = pmul(m.jz, ik);
+        m.pxx = pmul(m.pxx, ik); m.pyy = pmul(m.pyy, ik); m.pzz = pmul(m.pzz, ik);
+        m.pxy = pmul(m.pxy, ik); m.pxz = pmul(m.pxz, ik); m.pyz = pmul(m.pyz, ik);
+    }
+    return m;
+}
+
+struct Macro2 {
+    f2 drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;  // P: scaled by 216
+};
+
+__device__ __forceinline__ Macro2 macro_of2(const Mom2 &m) {
+    Macro2 M;
+    M.drho = pmul(m.drho, F2(INV_SCALE));
+    M.rho = padd(F2(1.0f), M.drho);
+    const f2 den = padd(F2(SCALE), m.drho);
+    const f2 ir = make_float2(__frcp_rn(den.x), __frcp_rn(den.y));
+    M.ux = pmul(m.jx, ir);
+    M.uy = pmul(m.jy, ir);
+    M.uz = pmul(m.jz, ir);
+    const f2 d3 = pmul(m.drho, F2(1.0f / 3.0f));
+    M.Pxx = psub(psub(m.pxx, d3), pmul(m.jx, M.ux));
+    M.Pyy = psub(psub(m.pyy, d3), pmul(m.jy, M.uy));
+    M.Pzz = psub(psub(m.pzz, d3), pmul(m.jz, M.uz));
+    M.Pxy = psub(m.pxy, pmul(m.jx, M.uy));
+    M.Pxz = psub(m.pxz, pmul(m.jx, M.uz));
+    M.Pyz = psub(m.pyz, pmul(m.jy, M.uz));
+    return M;
+}
+
+struct AxisF2 {
+    f2 a[3], X[3], Xp[3];
+};
+
+template <bool SC>
+__device__ __forceinline__ AxisF2 axis_of2(f2 u) {
+    AxisF2 f;
+    const f2 u2 = pmul(u, u);
+    f.a[0] = pmul(F2(3.0f), psub(u2, u));
+    f.a[1] = pmul(F2(-1.5f), u2);
+    f.a[2] = pmul(F2(3.0f), padd(u2, u));
+    f.X[0] = padd(F2(1.0f), f.a[0]);
+    f.X[1] = SC ? padd(F2(1.0f), f.a[1]) : pmul(F2(4.0f), padd(F2(1.0f), f.a[1]));
+    f.X[2] = padd(F2(1.0f), f.a[2]);
+    f.Xp[0] = pfma(F2(6.0f), u, F2(-3.0f));
+    f.Xp[1] = pmul(F2(SC ? -3.0f : -12.0f), u);
+    f.Xp[2] = pfma(F2(6.0f), u, F2(3.0f));
+    return f;
+}
+
+// c * W_i (rho E + drho) (SC: c (rho E + drho)) into s, or added to s; c per lane.
+template <bool SC>
+__device__ __forceinline__ void add_eq_dev2(const AxisF2 &fx, const AxisF2 &fy, const AxisF2 &fz, f2 rho, f2 drho,
+                                            f2 c, f2 s[27], bool first) {
+    f2 cw[4];  // c W for W = 1, 4, 16, 64
+    cw[0] = c;
+    if (!SC) {
+        cw[1] = pmul(c, F2(4.0f));
+        cw[2] = pmul(c, F2(16.0f));
+        cw[3] = pmul(c, F2(64.0f));
+    }
+    f2 sxy[9];
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = pfma(fx.a[ex], fy.a[ey], padd(fx.a[ex], fy.a[ey]));
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = k + 9 * ez;
+            const int lw = (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
+            const f2 E = pfma(sxy[k], fz.a[ez], padd(sxy[k], fz.a[ez]));
+            const f2 v = pmul(SC ? c : cw[lw], pfma(E, rho, drho));
+            s[i] = first ? v : padd(s[i], v);
+        }
+}
+
+// Post-collision populations of two cells in the storage domain of ST.
+// forced lanes take (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
+// f0(u + tau h) (scheme 1); other lanes f0(u) (their h is zero, and their
+// scheme-0 weights are 1 and 0, so the shifted term adds an exact zero).
+template <int ST>
+__device__ __forceinline__ void collide_pair(const Macro2 &M, f2 omega, f2 tau, bool anyforced, bool fa, bool fb,
+                                             f2 h[3], int scheme, f2 s[27]) {
+    constexpr bool SC = Codec<ST>::scaled;
+    constexpr float K = Codec<ST>::K;
+    const AxisF2 fx = axis_of2<SC>(M.ux), fy = axis_of2<SC>(M.uy), fz = axis_of2<SC>(M.uz);
+    if (!anyforced) {
+        add_eq_dev2<SC>(fx, fy, fz, M.rho, M.drho, F2(K), s, true);
+    } else {
+        const AxisF2 vx = axis_of2<SC>(pfma(tau, h[0], M.ux)), vy = axis_of2<SC>(pfma(tau, h[1], M.uy)),
+                     vz = axis_of2<SC>(pfma(tau, h[2], M.uz));
+        if (scheme == 1) {
+            add_eq_dev2<SC>(vx, vy, vz, M.rho, M.drho, F2(K), s, true);
+        } else {
+            const f2 w1 = pmul(F2(K), psub(F2(1.0f), omega)), w2 = pmul(F2(K), omega);
+            const f2 c1 = make_float2(fa ? w1.x : K, fb ? w1.y : K);
+            const f2 c2 = make_float2(fa ? w2.x : 0.0f, fb ? w2.y : 0.0f);
+            add_eq_dev2<SC>(fx, fy, fz, M.rho, M.drho, c1, s, true);
+            add_eq_dev2<SC>(vx, vy, vz, M.rho, M.drho, c2, s, false);
+        }
+    }
+    const f2 om1 = pmul(psub(F2(1.0f), omega), F2(INV_SCALE * K));
+    const f2 hom = pmul(F2(0.5f), om1);
+    const f2 hxx = pmul(hom, M.Pxx), hyy = pmul(hom, M.Pyy), hzz = pmul(hom, M.Pzz);
+    const f2 pxy = pmul(om1, M.Pxy), pxz = pmul(om1, M.Pxz), pyz = pmul(om1, M.Pyz);
+    const float xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};
+    f2 cY[3], cZ[3], bY[3], aY[3], bZ[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        cY[e] = pmul(hyy, F2(xpp[e]));
+        cZ[e] = pmul(hzz, F2(xpp[e]));
+        bY[e] = pmul(pyz, fy.Xp[e]);
+        aY[e] = pmul(pxy, fy.Xp[e]);
+        bZ[e] = pmul(pxz, fz.Xp[e]);
+    }
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 3; ++ey) {
+            const f2 G0 = pmul(hxx, pmul(fy.X[ey], fz.X[ez]));
+            const f2 G1 = pfma(cY[ey], fz.X[ez], pfma(fy.X[ey], cZ[ez], pmul(bY[ey], fz.Xp[ez])));
+            const f2 G2 = pfma(aY[ey], fz.X[ez], pmul(fy.X[ey], bZ[ez]));
+#pragma unroll
+            for (int ex = 0; ex < 3; ++ex) {
+                const int i = ex + 3 * ey + 9 * ez;
+                s[i] = pfma(F2(xpp[ex]), G0, pfma(fx.X[ex], G1, pfma(fx.Xp[ex], G2, s[i])));
+            }
+        }
+}
+
+// Source plane of logical plane zl for velocity index ez (= xi_z + 1): 0 and
+// the physical plane, 1 bounce-back, 2 pressure ghost, 3 the entering plane.
+__device__ __forceinline__ int src_z(const Geom &g, int zl, int ez, int ring, int reseed, int &sz) {
+    int zs = zl - (ez - 1), flag = 0;
+    if (zs < 0) {
+        if (g.bc_bottom == BC_PERIODIC) zs += g.nz; else flag = 1;
+    } else if (zs >= g.nz) {
+        if (g.bc_top == BC_PERIODIC) zs -= g.nz;
+        else flag = (g.bc_top == BC_PRESSURE) ? 2 : 1;
+    }
+    sz = flag ? 0 : zphys(zs, ring, g.nz);
+    if (flag == 0 && sz == reseed) flag = 3;
+    return flag;
+}
+
+// Pull the 27 populations of two cells (x, y, za) and (x, y, zb) (window
+// coordinates, both inside the window); interior and periodic pairs take 54
+// plain loads, any other pair the per-cell rule of pull27.
+template <int ST>
+__device__ __forceinline__ void pull27x2(const Geom &g, const typename Codec<ST>::T *__restrict__ f, int x, int y,
+                                         int za, int zb, int ring, int reseed, const float *__restrict__ utop,
+                                         f2 q[27]) {
+    int sx[3], sy[3], bxf[3], byf[3], sa[3], sb[3], ba[3], bb[3];
+    int flags = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        bxf[e] = src_axis(x, e, g.nx, g.bc_x, sx[e]);
+        byf[e] = src_axis(y, e, g.ny, g.bc_y, sy[e]);
+        ba[e] = src_z(g, za, e, ring, reseed, sa[e]);
+        bb[e] = src_z(g, zb, e, ring, reseed, sb[e]);
+        flags |= bxf[e] | byf[e] | ba[e] | bb[e];
+    }
+    const int nx = g.nx, plane = (int)g.plane;
+    const size_t ncell = (size_t)g.ncell;
+    if (flags == 0) {
+#pragma unroll
+        for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+            for (int ey = 0; ey < 3; ++ey) {
+                const int yr = sy[ey] * nx;
+                const typename Codec<ST>::T *pa = f + (sa[ez] * plane + yr);
+                const typename Codec<ST>::T *pb = f + (sb[ez] * plane + yr);
+#pragma unroll
+                for (int ex = 0; ex < 3; ++ex) {
+                    const int i = ex + 3 * ey + 9 * ez;
+                    q[i].x = Codec<ST>::load(pa + i * ncell + sx[ex]);
+                    q[i].y = Codec<ST>::load(pb + i * ncell + sx[ex]);
+                }
+            }
+        return;
+    }
+    float qa[27];
+    pull27<ST>(g, f, x, y, za, ring, reseed, utop, qa);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) q[i].x = qa[i];
+    pull27<ST>(g, f, x, y, zb, ring, reseed, utop, qa);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) q[i].y = qa[i];
+}
+
+// K1 for the cell pair (cx, cy, cz), (cx, cy, cz + 1): window coordinates for
+// ALL / ALLF / FAR, near-region coordinates for NEAR; cells outside the
+// window (or the mode's region) are not written, and a pair with none
+// inside returns.
+template <int ST, int MODE>
+__device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
+                                        typename Codec<ST>::T *__restrict__ dst, const float *__restrict__ utop_in,
+                                        float *__restrict__ utop_out, const BodySlot &S,
+                                        const float *__restrict__ hbox, const BoxGeom &box, int cx, int cy, int cz) {
+    const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
+    int x, y, z[2];
+    bool on[2];
+    if (MODE == K1_NEAR) {
+        if (cx >= box.Bx + 2 * NEAR_MARGIN || cy >= box.By + 2 * NEAR_MARGIN) return;
+        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_MARGIN + cx;
+        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_MARGIN + cy;
+        if (perx) { x += (x < 0) ? g.nx : 0; x -= (x >= g.nx) ? g.nx : 0; } else if (x < 0 || x >= g.nx) return;
+        if (pery) { y += (y < 0) ? g.ny : 0; y -= (y >= g.ny) ? g.ny : 0; } else if (y < 0 || y >= g.ny) return;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            int zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_MARGIN + cz + l;
+            on[l] = cz + l < box.Bz + 2 * NEAR_MARGIN;
+            if (perz) { zl += (zl < 0) ? g.nz : 0; zl -= (zl >= g.nz) ? g.nz : 0; }
+            else on[l] = on[l] && zl >= 0 && zl < g.nz;
+            z[l] = on[l] ? zl : 0;
+        }
+    } else {
+        x = cx;
+        y = cy;
+        if (x >= g.nx || y >= g.ny) return;
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            on[l] = cz + l < g.nz;
+            z[l] = on[l] ? cz + l : 0;
+        }
+        if (MODE == K1_FAR) {
+            // the z tests first: the planes are the same for a whole block
+            bool xy_checked = false, in_xy = false;
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const int rz = rel_axis(z[l], S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
+                if (on[l] && (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN)) {
+                    if (!xy_checked) {
+                        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
+                        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
+                        in_xy = (unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
+                                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN);
+                        xy_checked = true;
+                    }
+                    if (in_xy) on[l] = false;
+                }
+            }
+        }
+    }
+    if (!on[0] && !on[1]) return;
+    // a missing cell shares its partner's plane (loads in bounds, no store)
+    if (!on[0]) z[0] = z[1];
+    if (!on[1]) z[1] = z[0];
+    const int ring = S.ring;
+    f2 q[27];
+    pull27x2<ST>(g, src, x, y, z[0], z[1], ring, S.reseed, utop_in, q);
+    const f2 omega = make_float2(omega_of(g, z[0]), omega_of(g, z[1]));
+    bool forced[2] = {false, false};
+    f2 h[3] = {F2(0.0f), F2(0.0f), F2(0.0f)};
+    f2 tau = F2(1.0f);
+    if (MODE == K1_ALLF || MODE == K1_NEAR) {
+        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], 0, g.nx, perx);
+        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], 0, g.ny, pery);
+        if ((unsigned)rx < (unsigned)box.Bx && (unsigned)ry < (unsigned)box.By) {
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                const int rz = rel_axis(z[l], S.box_lo[2], S.box_lo_w[2], 0, g.nz, perz);
+                if (on[l] && (unsigned)rz < (unsigned)box.Bz) {
+                    const size_t b = ((size_t)rz * box.By + ry) * box.Bx + rx;
+                    const float h0 = __ldg(hbox + b), h1 = __ldg(hbox + box.nbox + b), h2 = __ldg(hbox + 2 * box.nbox + b);
+                    if (l == 0) { h[0].x = h0; h[1].x = h1; h[2].x = h2; }
+                    else { h[0].y = h0; h[1].y = h1; h[2].y = h2; }
+                    forced[l] = true;
+                }
+            }
+        }
+        tau = make_float2(tau_of(g, z[0]), tau_of(g, z[1]));
+    }
+    const Macro2 M = macro_of2(moments27x2<ST>(q));
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+        if (on[l] && z[l] == g.nz - 1) {
+            const size_t c = (size_t)y * g.nx + x;
+            utop_out[c] = l ? M.ux.y : M.ux.x;
+            utop_out[g.plane + c] = l ? M.uy.y : M.uy.x;
+            utop_out[2 * g.plane + c] = l ? M.uz.y : M.uz.x;
+        }
+    collide_pair<ST>(M, omega, tau, forced[0] || forced[1], forced[0], forced[1], h,
+                     (MODE == K1_ALLF || MODE == K1_NEAR) ? g.force_scheme : 0, q);
+    const size_t ncell = (size_t)g.ncell;
+    const int row = y * g.nx + x;
+    typename Codec<ST>::T *da = dst + (zphys(z[0], ring, g.nz) * (int)g.plane + row);
+    typename Codec<ST>::T *db = dst + (zphys(z[1], ring, g.nz) * (int)g.plane + row);
+    if (on[0] && on[1]) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            Codec<ST>::store(da + i * ncell, q[i].x);
+            Codec<ST>::store(db + i * ncell, q[i].y);
+        }
+    } else if (on[0]) {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) Codec<ST>::store(da + i * ncell, q[i].x);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) Codec<ST>::store(db + i * ncell, q[i].y);
+    }
+}
+
 // Tile of a 1-D block of blockDim.x threads over (x, y): tx threads along x,
-// blockDim.x / tx rows along y, one plane; block b of a region ex x ey x ez,
-// x fastest.
-__device__ __forceinline__ void tile_coords(int b, int tx, int ex, int ey, int &cx, int &cy, int &cz) {
+// blockDim.x / tx rows along y, one plane (pz = 1) or pair of planes (pz = 2);
+// block b of a region ex x ey x ez (ceil(ez / pz) plane groups), x fastest.
+// cz is the first plane.
+__device__ __forceinline__ void tile_coords(int b, int tx, int ex, int ey, int pz, int &cx, int &cy, int &cz) {
     const int ty = blockDim.x / tx;
     const int gx = (ex + tx - 1) / tx, gy = (ey + ty - 1) / ty;
     const int bx = b % gx, rest = b / gx;
     cx = bx * tx + (int)threadIdx.x % tx;
     cy = (rest % gy) * ty + (int)threadIdx.x / tx;
-    cz = rest / gy;
+    cz = pz * (rest / gy);
 }
 
 // ---------------------------------------------------------------------------

@@ -16,8 +16,12 @@ __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename C
         st->s[slot_out] = st->s[slot];
         st->s[slot_out].reseed = -1;
     }
-    k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, blockIdx.x * 32 + threadIdx.x,
-                      blockIdx.y * 4 + threadIdx.y, blockIdx.z);
+    if (MODE == K1_NEAR)  // small, on the critical path: one cell per thread
+        k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, blockIdx.x * 32 + threadIdx.x,
+                          blockIdx.y * 4 + threadIdx.y, blockIdx.z);
+    else  // the window: a pair of planes per thread
+        k1_pair<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, blockIdx.x * 32 + threadIdx.x,
+                          blockIdx.y * 4 + threadIdx.y, 2 * blockIdx.z);
 }
 
 
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_box_moments_bin(Geom g, const ty
 // ---------------------------------------------------------------------------
 // Launchers.
 static dim3 cell_grid(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz); }
+// collide+stream over the window: one thread per pair of planes
+static dim3 pair_grid(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2); }
 static dim3 near_grid(const BoxGeom &b) {
     const int ex = b.Bx + 2 * NEAR_MARGIN, ey = b.By + 2 * NEAR_MARGIN, ez = b.Bz + 2 * NEAR_MARGIN;
     return dim3((ex + 31) / 32, (ey + 3) / 4, ez);
@@ -106,11 +112,11 @@ static cudaError_t collide_t(const Geom &g, const void *src, void *dst, const fl
     if (region == REGION_NEAR)
         k_collide_stream<ST, K1_NEAR><<<near_grid(box), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     else if (region == REGION_FAR)
-        k_collide_stream<ST, K1_FAR><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
+        k_collide_stream<ST, K1_FAR><<<pair_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     else if (has_box)
-        k_collide_stream<ST, K1_ALLF><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
+        k_collide_stream<ST, K1_ALLF><<<pair_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     else
-        k_collide_stream<ST, K1_ALL><<<cell_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
+        k_collide_stream<ST, K1_ALL><<<pair_grid(g), blk, 0, s>>>(g, fs, fd, utop_in, utop_out, st, slot, slot_out, hbox, box);
     return cudaGetLastError();
 }
 

@@ -7,11 +7,11 @@
 // region fits the window:
 //
 //   caller stream: --fork--> collide+stream, far cells ------------------> join
-//   side stream  :       \-> collide+stream, near cells -> particle update
-//                           + markers -> support moments + tile lists
-//                           -> interpolation + rows of A -> (h <- h + r0 - A h)
-//                           x (n-1) -> spread h_imm(t+1) ---------------------^
-//   aux stream   :                         \-> F, T (FP64) ---------------^
+//   side stream  :       \-> collide+stream, near cells -+-> support moments
+//                           + tile lists -> interpolation + rows of A
+//                           -> (h <- h + r0 - A h) x (n-1) -> spread h_imm(t+1) --^
+//   aux stream   :       \-> [prediction] -> particle update + markers -/
+//                                                    ... -> F, T (FP64) ----^
 //
 // The near region (support box grown by two cells) contains every cell the
 // next support-box pull reads, so the immersed-boundary chain only waits for
@@ -104,8 +104,10 @@ extern "C" size_t lbm_workspace_bytes(const turret_window *win, turret_storage s
 
 static void release(turret_ctx *c) {
     if (!c) return;
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (c->graph_ready[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->multi_ready[k]) cudaGraphExecDestroy(c->graph_multi[k]);
+    }
     if (c->side) cudaStreamDestroy(c->side);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -113,6 +115,10 @@ static void release(turret_ctx *c) {
     if (c->ev_red) cudaEventDestroy(c->ev_red);
     if (c->ev_red_done) cudaEventDestroy(c->ev_red_done);
     if (c->ev_pred) cudaEventDestroy(c->ev_pred);
+    cudaEvent_t *xs[6] = {c->ev_far, c->ev_near, c->ev_pm, c->ev_ired, c->ev_redd, c->ev_spread};
+    for (cudaEvent_t *x : xs)
+        for (int k = 0; k < 2; ++k)
+            if (x[k]) cudaEventDestroy(x[k]);
     if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
 }
@@ -137,6 +143,10 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     c = new turret_ctx();
     c->side = c->aux = nullptr;
     c->ev_fork = c->ev_join = c->ev_red = c->ev_red_done = c->ev_pred = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        c->ev_far[k] = c->ev_near[k] = c->ev_pm[k] = c->ev_ired[k] = c->ev_redd[k] = c->ev_spread[k] = nullptr;
+        c->multi_ready[k] = false;
+    }
     c->pred_mode = 0;
     c->pred_opts = 0;
     c->pred_eps = 0.0f;
@@ -194,6 +204,11 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_red_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_pred, cudaEventDisableTiming);
+    {
+        cudaEvent_t *xs[6] = {c->ev_far, c->ev_near, c->ev_pm, c->ev_ired, c->ev_redd, c->ev_spread};
+        for (cudaEvent_t *x : xs)
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&x[k], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tau_z, c->tau_host.data(), c->tau_host.size() * sizeof(float), cudaMemcpyHostToDevice,
                             c->stream);
@@ -222,7 +237,9 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
 static void drop_graphs(turret_ctx *c) {
     for (int k = 0; k < 2; ++k) {
         if (c->graph_ready[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->multi_ready[k]) cudaGraphExecDestroy(c->graph_multi[k]);
         c->graph_ready[k] = false;
+        c->multi_ready[k] = false;
     }
 }
 
@@ -429,24 +446,10 @@ extern "C" size_t ibm_workspace_bytes(const turret_ctx *c, const double *V, int6
 // lists, the surface force and torque, and n IBM cycles -> h_imm(t+1).
 // advance = 0: the same at the current time level (slot `slot`) without
 // moving the particle (set-up of t = 0).
-static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float *utop_in, int slot, int advance,
-                                    cudaStream_t s) {
+// The IBM cycles of one step (the paper's n - 1 cycles from r0, or the
+// warm-started adaptive ones) on stream s.
+static cudaError_t enqueue_cycles(turret_ctx *c, int warm, cudaStream_t s) {
     const int nm = c->nm;
-    const int so = advance ? (slot ^ 1) : slot;
-    const bool branch = (s == c->side);  // reduce F, T on the aux branch
-    CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, slot, advance, c->mk, s));
-    CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base, c->mk.seg,
-                              c->tile_list, c->tile_count, c->cap, c->dstate, c->body.rmin, c->body.rmax, s));
-    const int warm = (advance && c->body.predictor != 0 && (c->body.pred_opts & PRED_WARM)) ? 1 : 0;
-    CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, warm, s));
-    if (branch) {
-        CE(cudaEventRecord(c->ev_red, s));
-        CE(cudaStreamWaitEvent(c->aux, c->ev_red, 0));
-        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, c->aux));
-        CE(cudaEventRecord(c->ev_red_done, c->aux));
-    } else {
-        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, s));
-    }
     if (!warm) {
         // the paper's cycles: h^0 = r0, then cycles 1 .. n-1 alternating so
         // that the last one writes hl
@@ -469,6 +472,31 @@ static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float
             src = dst;
         }
     }
+    return cudaSuccess;
+}
+
+// pm_done: when non-null, the particle/marker update was already enqueued
+// (on the aux stream, beside the near collide+stream) and this event marks it.
+static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float *utop_in, int slot, int advance,
+                                    cudaStream_t s, cudaEvent_t pm_done = nullptr) {
+    const int nm = c->nm;
+    const int so = advance ? (slot ^ 1) : slot;
+    const bool branch = (s == c->side);  // reduce F, T on the aux branch
+    if (pm_done) CE(cudaStreamWaitEvent(s, pm_done, 0));
+    else CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, slot, advance, c->mk, s));
+    CE(launch_box_moments_bin(c->geom, c->storage, fsrc, utop_in, c->dstate, so, c->box, c->ba, nm, c->mk.base, c->mk.seg,
+                              c->tile_list, c->tile_count, c->cap, c->dstate, c->body.rmin, c->body.rmax, s));
+    const int warm = (advance && c->body.predictor != 0 && (c->body.pred_opts & PRED_WARM)) ? 1 : 0;
+    CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, warm, s));
+    if (branch) {
+        CE(cudaEventRecord(c->ev_red, s));
+        CE(cudaStreamWaitEvent(c->aux, c->ev_red, 0));
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, c->aux));
+        CE(cudaEventRecord(c->ev_red_done, c->aux));
+    } else {
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, so, c->body, s));
+    }
+    CE(enqueue_cycles(c, warm, s));
     CE(launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, s));
     if (branch) CE(cudaStreamWaitEvent(s, c->ev_red_done, 0));
     return cudaSuccess;
@@ -484,28 +512,94 @@ static cudaError_t enqueue_step(turret_ctx *c, int p) {
     const bool predict = c->body.predictor != 0;
     const MlpDev *net = (c->body.predictor == 2) ? mlp_device_view(c->net) : nullptr;
     if (c->split) {
+        // the prediction and the particle/marker update (which reads only the
+        // body state) run on the aux stream beside the near collide+stream
         CE(cudaEventRecord(c->ev_fork, c->stream));
         CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        if (predict) {  // the prediction overlaps the near collide+stream
-            CE(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-            CE(launch_predict(net, c->dstate, p, c->body.predictor, c->aux));
-            CE(cudaEventRecord(c->ev_pred, c->aux));
-        }
+        CE(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        if (predict) CE(launch_predict(net, c->dstate, p, c->body.predictor, c->aux));
+        CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, p, 1, c->mk, c->aux));
+        CE(cudaEventRecord(c->ev_pred, c->aux));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_FAR, c->stream));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_NEAR, c->side));
-        if (predict) CE(cudaStreamWaitEvent(c->side, c->ev_pred, 0));
     } else {
         if (predict) CE(launch_predict(net, c->dstate, p, c->body.predictor, c->stream));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_ALL, c->stream));
     }
-    CE(enqueue_coupling(c, c->f[1 - p], c->utop[p], p, 1, chain));
+    CE(enqueue_coupling(c, c->f[1 - p], c->utop[p], p, 1, chain, c->split ? c->ev_pred : nullptr));
     if (c->split) {
         CE(cudaEventRecord(c->ev_join, c->side));
         CE(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
+    return cudaSuccess;
+}
+
+// Steps t .. t+K-1 (parity p0 first) as one capture with the exact cross-step
+// dependencies (split windows only), so the immersed-boundary chain of step
+// t overlaps the far-cell collide+stream of step t+1:
+//   far(t)    after near(t-1) [its near-region cells of f*(t-1)] and pm(t-1)
+//             [the window slot of t];
+//   pm(t)     (prediction + particle/marker update, aux) after far(t-1) and
+//             near(t-1) [they read the slot pm(t) writes] and spread(t-1)
+//             [the marker arrays pm(t) rewrites], and reduce(t-1) [F, T];
+//   near(t)   after far(t-1) [its far-cell sources and the buffer it writes];
+//   moments(t) after near(t) and pm(t); the chain then as in one step;
+//   reduce(t) (aux) after interpolation(t).
+// Each event is recorded once per step parity; a wait always refers to the
+// step the dependency names.  Per-step results equal those of one-step graphs.
+static cudaError_t enqueue_steps_pipelined(turret_ctx *c, int p0, int K) {
+    const Geom &G = c->geom;
+    const int nm = c->nm;
+    const bool predict = c->body.predictor != 0;
+    const MlpDev *net = (c->body.predictor == 2) ? mlp_device_view(c->net) : nullptr;
+    CE(cudaEventRecord(c->ev_fork, c->stream));
+    CE(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    CE(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    int p = p0;
+    for (int k = 0; k < K; ++k, p ^= 1) {
+        const int q = p ^ 1;
+        const bool first = k == 0;
+        // caller stream: the far cells of step t
+        if (!first) {
+            CE(cudaStreamWaitEvent(c->stream, c->ev_near[q], 0));
+            CE(cudaStreamWaitEvent(c->stream, c->ev_pm[q], 0));
+        }
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[q], c->utop[q], c->utop[p], c->dstate, p, -1, c->ba.h,
+                                 c->box, true, REGION_FAR, c->stream));
+        CE(cudaEventRecord(c->ev_far[p], c->stream));
+        // aux: prediction and particle/marker update
+        if (!first) {
+            CE(cudaStreamWaitEvent(c->aux, c->ev_far[q], 0));
+            CE(cudaStreamWaitEvent(c->aux, c->ev_spread[q], 0));
+        }
+        if (predict) CE(launch_predict(net, c->dstate, p, c->body.predictor, c->aux));
+        CE(launch_particle_markers(G, c->body, c->box, c->dstate, p, 1, c->mk, c->aux));
+        CE(cudaEventRecord(c->ev_pm[p], c->aux));
+        // side: the near cells, then the immersed-boundary chain
+        if (!first) CE(cudaStreamWaitEvent(c->side, c->ev_far[q], 0));
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[q], c->utop[q], c->utop[p], c->dstate, p, -1, c->ba.h,
+                                 c->box, true, REGION_NEAR, c->side));
+        CE(cudaEventRecord(c->ev_near[p], c->side));
+        CE(cudaStreamWaitEvent(c->side, c->ev_pm[p], 0));
+        CE(launch_box_moments_bin(G, c->storage, c->f[q], c->utop[p], c->dstate, q, c->box, c->ba, nm, c->mk.base,
+                                  c->mk.seg, c->tile_list, c->tile_count, c->cap, c->dstate, c->body.rmin,
+                                  c->body.rmax, c->side));
+        const int warm = (c->body.predictor != 0 && (c->body.pred_opts & PRED_WARM)) ? 1 : 0;
+        CE(launch_interp0(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->dstate, warm, c->side));
+        CE(cudaEventRecord(c->ev_ired[p], c->side));
+        CE(cudaStreamWaitEvent(c->aux, c->ev_ired[p], 0));
+        CE(launch_reduce_ft(nm, c->mk, c->dstate, q, c->body, c->aux));
+        CE(cudaEventRecord(c->ev_redd[p], c->aux));
+        CE(enqueue_cycles(c, warm, c->side));
+        CE(launch_spread(c->box, nm, c->mk, c->ba, c->tile_list, c->tile_count, c->cap, c->side));
+        CE(cudaEventRecord(c->ev_spread[p], c->side));
+    }
+    const int last = p ^ 1;
+    CE(cudaStreamWaitEvent(c->stream, c->ev_spread[last], 0));
+    CE(cudaStreamWaitEvent(c->stream, c->ev_redd[last], 0));
     return cudaSuccess;
 }
 
@@ -633,7 +727,7 @@ static void set_node_priorities(const turret_ctx *c, cudaGraph_t gr) {
     if (cudaGraphGetNodes(gr, nullptr, &n) != cudaSuccess || n == 0) return;
     std::vector<cudaGraphNode_t> nodes(n);
     if (cudaGraphGetNodes(gr, nodes.data(), &n) != cudaSuccess) return;
-    const dim3 bulk((c->geom.nx + 31) / 32, (c->geom.ny + 3) / 4, c->geom.nz);
+    const dim3 bulk((c->geom.nx + 31) / 32, (c->geom.ny + 3) / 4, (c->geom.nz + 1) / 2);  // plane pairs
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
@@ -649,27 +743,48 @@ static void set_node_priorities(const turret_ctx *c, cudaGraph_t gr) {
     cudaGetLastError();  // priorities are a hint; never fail a step on them
 }
 
+// Steps per replay of the pipelined multi-step graph (even: the parity after
+// a replay is the one before it).
+constexpr int PIPE_STEPS = 8;
+
+static cudaError_t capture(turret_ctx *c, int p, int K, cudaGraphExec_t *out) {
+    cudaGraph_t gr;
+    CE(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = (K == 1) ? enqueue_step(c, p) : enqueue_steps_pipelined(c, p, K);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+    if (e != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(gr);
+        return e;
+    }
+    CE(e2);
+    set_node_priorities(c, gr);
+    e = cudaGraphInstantiateWithFlags(out, gr, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(gr);
+    return e;
+}
+
 extern "C" turret_status step(turret_ctx *c, int64_t n) {
     if (!c) return fail(c, TURRET_EINVAL, "NULL context");
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
     const bool graphs = (c->stream != nullptr) && !c->flags.no_graph;
-    for (int64_t k = 0; k < n; ++k) {
+    int64_t k = 0;
+    if (graphs && c->has_particle && c->split) {
+        // whole groups of PIPE_STEPS steps as one pipelined graph
+        for (; n - k >= PIPE_STEPS; k += PIPE_STEPS) {
+            const int p = (int)(c->step & 1);
+            if (!c->multi_ready[p]) {
+                CK(capture(c, p, PIPE_STEPS, &c->graph_multi[p]), "multi-step capture");
+                c->multi_ready[p] = true;
+            }
+            CK(cudaGraphLaunch(c->graph_multi[p], c->stream), "graph launch");
+            c->step += PIPE_STEPS;
+        }
+    }
+    for (; k < n; ++k) {
         const int p = (int)(c->step & 1);
         if (graphs) {
             if (!c->graph_ready[p]) {
-                cudaGraph_t gr;
-                CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-                cudaError_t e = enqueue_step(c, p);
-                cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
-                if (e != cudaSuccess) {
-                    if (e2 == cudaSuccess) cudaGraphDestroy(gr);
-                    return cuda_fail(c, e, "capture enqueue");
-                }
-                CK(e2, "end capture");
-                set_node_priorities(c, gr);
-                e = cudaGraphInstantiateWithFlags(&c->graph[p], gr, cudaGraphInstantiateFlagUseNodePriority);
-                cudaGraphDestroy(gr);
-                CK(e, "graph instantiate");
+                CK(capture(c, p, 1, &c->graph[p]), "capture");
                 c->graph_ready[p] = true;
             }
             CK(cudaGraphLaunch(c->graph[p], c->stream), "graph launch");

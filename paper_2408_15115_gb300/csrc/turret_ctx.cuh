@@ -18,6 +18,8 @@ struct turret_ctx {
     cudaStream_t side;    // internal high-priority stream of the immersed-boundary chain
     cudaStream_t aux;     // internal stream of the FP64 force/torque reduction
     cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done, ev_pred;
+    // cross-step events of multi-step graphs, by step parity
+    cudaEvent_t ev_far[2], ev_near[2], ev_pm[2], ev_ired[2], ev_redd[2], ev_spread[2];
     turret::Geom geom;
     // fluid workspace
     void *f[2];
@@ -49,6 +51,8 @@ struct turret_ctx {
     long long step;
     cudaGraphExec_t graph[2];
     bool graph_ready[2];
+    cudaGraphExec_t graph_multi[2];  // PIPE_STEPS steps per replay, by starting parity
+    bool multi_ready[2];
     std::string err;
 };
 

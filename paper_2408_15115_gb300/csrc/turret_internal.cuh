@@ -264,7 +264,7 @@ cudaError_t launch_macro(const Geom &g, int storage, const void *src, const floa
                          int slot, float *out, bool pops, cudaStream_t s);
 // K1 over one window with a 1-D block of `threads` and tile width tx (timing
 // of tile candidates; same cells and arithmetic as launch_collide_stream).
-// minb: register-budget variant (3: <= 80 registers, 4: <= 64 registers).
+// minb: register-budget variant (2: <= 128 registers, 3: <= 85 registers).
 bool valid_tile(int threads, int tx, int minb);
 cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                  float *utop_out, const DevState *st, int slot, const float *hbox,
@@ -292,7 +292,8 @@ cudaError_t launch_particle_markers(const Geom &g, const BodyConst &bc, const Bo
 // l = 0 interpolation of u* and sigma, the surface traction per marker, and
 // the row k of the interaction matrix A (one warp per marker).
 cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays ba, const int *tile_list,
-                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s);
+                           const int *tile_count, int cap, DevState *st, int warm, cudaStream_t s,
+                           bool by_tile = false);
 // One IBM cycle in matrix form: h_out = h_in + r0 - A h_in (= steps l = 1..4).
 cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out, float *h_final, int last,
                          DevState *st, int cyc, int adaptive, float eps, cudaStream_t s);

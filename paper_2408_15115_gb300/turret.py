@@ -364,7 +364,7 @@ class Batch:
         if rc != 0:
             raise TurretError(rc, self._L.turret_batch_last_error(None).decode())
         self.b = b
-        self.tiles = (128, 3, [32] * n)
+        self.tiles = (128, 2, [32] * n)
 
     def _check(self, rc):
         if rc != 0:

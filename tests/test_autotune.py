@@ -22,9 +22,9 @@ def _timer_table(calls):
     def timer(handle, threads, tx, minb):
         calls.append((handle.name, threads, tx, minb))
         if handle.name == "b":
-            base = 400.0 if (threads, minb) == (128, 3) else 480.0
+            base = 400.0 if (threads, minb) == (128, 2) else 480.0
             return base - (10.0 if tx == 64 else 0.0)
-        base = 40.0 if (threads, minb) == (256, 4) else 44.0
+        base = 40.0 if (threads, minb) == (256, 3) else 44.0
         return base - (1.0 if tx == 128 else 0.0)
     return timer
 
@@ -40,8 +40,8 @@ def test_one_timing_per_class_and_candidate(tmp_path):
 def test_batch_wide_choice_minimises_weighted_time(tmp_path):
     calls = []
     ch = AT.tune(_runs(), _timer_table(calls), cache_path=str(tmp_path / "c.json"), device_name="dev")
-    # weighted: b dominates (1.77M cells), so (128, 3) wins over a's favourite (256, 4)
-    assert (ch.threads, ch.minb) == (128, 3)
+    # weighted: b dominates (1.77M cells), so (128, 2) wins over a's favourite (256, 3)
+    assert (ch.threads, ch.minb) == (128, 2)
     assert ch.tx == [128, 64, 128]
     # predicted time = sum over runs of the chosen candidates' us
     assert abs(ch.predicted_us - (43.0 + 390.0 + 43.0)) < 1e-9
@@ -58,7 +58,7 @@ def test_cache_round_trip_and_device_separation(tmp_path):
     assert data["version"] == AT.CACHE_VERSION
     assert set(data["devices"]["dev"]) == {"k1/nx=64/f32", "k1/nx=96/f16"}
     # timings are stored per million cells
-    v = data["devices"]["dev"]["k1/nx=64/f32"][AT.cand_key(256, 128, 4)]
+    v = data["devices"]["dev"]["k1/nx=64/f32"][AT.cand_key(256, 128, 3)]
     assert abs(v - 39.0 * 1e6 / 64 ** 3) < 1e-9
     AT.tune(_runs(), _timer_table(calls), cache_path=path, device_name="other")
     assert len(calls) == 2 * n1

@@ -79,7 +79,7 @@ def test_batched_runs_equal_runs_alone_bitwise(alone_40):
     b.close()
 
 
-@pytest.mark.parametrize("threads,minb,tx", [(256, 4, [64, 128, 16, 32]), (64, 3, [32, 64, 16, 64])])
+@pytest.mark.parametrize("threads,minb,tx", [(256, 3, [64, 128, 16, 32]), (64, 2, [32, 64, 16, 64])])
 def test_launch_shape_does_not_change_results(alone_40, threads, minb, tx):
     from paper_2408_15115_gb300 import turret as T
     runs = _runs()
@@ -112,7 +112,7 @@ def test_autotune_picks_a_valid_shape_and_caches(tmp_path):
     b = T.Batch(runs)
     cache = str(tmp_path / "tiles.json")
     c1 = b.autotune(cache_path=cache, reps=3)
-    assert c1.threads in (128, 256) and c1.minb in (3, 4) and len(c1.tx) == 4
+    assert c1.threads in (128, 256) and c1.minb in (2, 3) and len(c1.tx) == 4
     # timing left every run unchanged
     for t, ref in zip(runs, before):
         _assert_same(_snapshot(t), ref)
@@ -142,7 +142,7 @@ def test_batch_rejects_invalid_run_lists():
     runs[0].step(1)
     b = T.Batch(runs)
     with pytest.raises(T.TurretError):
-        b.set_tiles(128, 3, [48, 32])
+        b.set_tiles(128, 2, [48, 32])
     runs[0].step(1)  # one run stepped alone to the other parity: the batch refuses to step
     with pytest.raises(T.TurretError) as e:
         b.step(1)

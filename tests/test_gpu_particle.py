@@ -73,12 +73,18 @@ def test_sliding_window_follows_particle():
 
 
 def test_determinism_and_graph_equivalence():
+    # two runs with the pipelined 8-step graphs (30 = 3 x 8 + 6 one-step
+    # graphs), one with direct launches, one stepping one graph at a time
     V, T = I.sphere(4, 6.0)
     runs = []
-    for flags in ({}, {}, {"no_graph": 1}):
+    for flags, one in (({}, False), ({}, False), ({"no_graph": 1}, False), ({}, True)):
         t, _ = make_pair(24, 24, 32, 0.05, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=4, flags=flags,
                          particle=(V, T, (11.6, 12.3, 16.4), (0, 0, 0), (0, 0.001, 0)))
-        t.step(30)
+        if one:
+            for _ in range(30):
+                t.step(1)
+        else:
+            t.step(30)
         runs.append((t.populations().cpu().numpy(), t.state()))
     for other in runs[1:]:
         assert np.array_equal(runs[0][0], other[0])
