@@ -56,6 +56,35 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+class Ranks:
+    """Replica bookkeeping of a multi-GPU run (one independent window per
+    rank, no data-path collective): a barrier around the timed region and the
+    maximum of a scalar over ranks.  device None: CPU tensors (gloo)."""
+
+    def __init__(self, world, device=None):
+        self.world = world
+        self.device = device
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return float(x)
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_glups(world, cells, steps, ms_max):
+    """Cells updated by all ranks per second over the slowest rank's time."""
+    return world * cells * steps / (ms_max / 1e3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -337,18 +366,9 @@ def run_ours(args):
     cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
     K, W = args.steps, args.warmup
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    ranks = Ranks(world, dev)
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     # ---- device-resident timed steps ------------------------------------
     t = configs.make_turret(cfg, device=dev)
@@ -369,7 +389,7 @@ def run_ours(args):
     clocks = clk.summary()
     state = t.state()
     kps = state["kernels_per_step"]
-    value = world * cells * K / (ms / 1e3) / 1e9
+    value = whole_job_glups(world, cells, K, ms)
 
     # ---- the fused collide+stream kernel alone (roofline) -------------------
     t.fluid_step(W)
