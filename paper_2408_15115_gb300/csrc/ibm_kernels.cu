@@ -350,10 +350,12 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
 }
 
 
+template <int NT>
 __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const MarkerArrays &m, const BoxArrays &ba,
                                               const int *__restrict__ wlist, const int *__restrict__ wcount,
                                               int cap, DevState *st, int k, int warm) {
-    __shared__ int wc[ROWS_WARPS];
+    constexpr int NW = NT / 32;
+    __shared__ int wc[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MRec rk = m.rec[k];
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
@@ -365,7 +367,7 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
     float *arow = m.aval + (size_t)k * ROWCAP;
     int *irow = m.aidx + (size_t)k * ROWCAP;
     int len = 0;
-    for (int base = 0; base < cnt; base += ROWS_THREADS) {
+    for (int base = 0; base < cnt; base += NT) {
         const int ii = base + tid;
         bool hit = false;
         float a = 0.0f;
@@ -385,7 +387,7 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
         int off = len;
         int tot = 0;
 #pragma unroll
-        for (int w = 0; w < ROWS_WARPS; ++w) {
+        for (int w = 0; w < NW; ++w) {
             if (w < warp) off += wc[w];
             tot += wc[w];
         }
@@ -405,11 +407,15 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
     }
 }
 
-__global__ void __launch_bounds__(ROWS_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m, BoxArrays ba,
-                                                                const int *__restrict__ wlist,
-                                                                const int *__restrict__ wcount, int cap,
-                                                                DevState *st, int warm) {
-    interp0_block(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x, warm);
+// 64 threads per marker: the blocks sit on the SMs beside the bulk
+// collide+stream for the latency of their loads, so idle threads are costly.
+constexpr int ROWS_MARKER_THREADS = 64;
+
+__global__ void __launch_bounds__(ROWS_MARKER_THREADS) k_interp0_rows(BoxGeom box, int nm, MarkerArrays m,
+                                                                      BoxArrays ba, const int *__restrict__ wlist,
+                                                                      const int *__restrict__ wcount, int cap,
+                                                                      DevState *st, int warm) {
+    interp0_block<ROWS_MARKER_THREADS>(box, nm, m, ba, wlist, wcount, cap, st, blockIdx.x, warm);
 }
 
 // The same step l = 0 and rows of A with one block per TILE^3 tile of the
@@ -857,7 +863,7 @@ cudaError_t launch_interp0(const BoxGeom &box, int nm, MarkerArrays m, BoxArrays
     if (by_tile)
         k_interp0_tiles<<<ntiles, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list, tile_count, cap, st, warm);
     else
-        k_interp0_rows<<<nm, ROWS_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
+        k_interp0_rows<<<nm, ROWS_MARKER_THREADS, 0, s>>>(box, nm, m, ba, tile_list + (size_t)ntiles * cap,
                                                    tile_count + ntiles, cap, st, warm);
     return cudaGetLastError();
 }

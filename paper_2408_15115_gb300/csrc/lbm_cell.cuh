@@ -824,7 +824,7 @@ __device__ __forceinline__ int find_run(const int *__restrict__ prefix, int nrun
 // with warp ballots; no atomics): list 0, the markers whose 4x4x4 stencil
 // overlaps the tile (spreading); list 1, those whose stencil overlaps the
 // stencil of any marker based in the tile (rows of A).
-constexpr int MB_THREADS = 256;
+constexpr int MB_THREADS = 128;
 
 template <int ST>
 __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>::T *__restrict__ src,
