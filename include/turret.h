@@ -304,7 +304,7 @@ typedef struct {
 } turret_adamw;
 
 /* Device workspace for a network trained on batches of up to batch_cap rows
- * (0 for batch_cap outside 1 .. 2^20).                                      */
+ * (0 for batch_cap outside 1 .. 16384).                                     */
 TURRET_API size_t mlp_workspace_bytes(int32_t batch_cap);
 /* Creates a network with the host parameters `params` [TURRET_MLP_NPARAM],
  * identity standardisation and zero optimiser moments; waits.               */

@@ -60,12 +60,21 @@ struct GemmArgs {
     int lda, ldb, ldc, ldo, ldz;
     int ta, tb;
     int M, N, K;
+    int kslice;         // > 0: block z sums K range [z kslice, (z+1) kslice) into part[z][M][N]
+    float *part;
 };
 enum { EPI_STORE = 0, EPI_GELU = 1, EPI_DGELU = 2 };
+// split-K of the weight-gradient products (reductions over the batch): slices
+// of KSLICE rows, partial sums added in slice order by k_sum_slices
+constexpr int KSLICE = 256, MAX_SLICES = 64;
 constexpr int GBM = 64, GBN = 64, GBK = 32, GTHREADS = 128;
 
 __device__ __forceinline__ void epilogue(const GemmArgs &g, int epi, int m, int n, float acc) {
     if (m >= g.M || n >= g.N) return;
+    if (g.kslice > 0) {  // partial sum of this block's K slice
+        g.part[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc;
+        return;
+    }
     float v = acc + (g.bias ? g.bias[n] : 0.0f);
     if (epi == EPI_DGELU) v *= gelu_prime_f(g.Zg[(size_t)m * g.ldz + n]);
     g.C[(size_t)m * g.ldc + n] = v;
@@ -95,7 +104,9 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmArgs g, int epi) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) sacc[i][j] = 0.0f;
-    for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    const int kbeg = g.kslice > 0 ? blockIdx.z * g.kslice : 0;
+    const int kend = g.kslice > 0 ? min(g.K, kbeg + g.kslice) : g.K;
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
         // stage the A and B tiles (any layout -> [row][k]), zero outside the matrices
 #pragma unroll 4
         for (int e = tid; e < GBM * GBK; e += GTHREADS) {
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmArgs g, int epi) {
             if (g.ta) { k = e / GBM; m = e % GBM; } else { m = e / GBK; k = e % GBK; }
             const int gm = m0 + m, gk = k0 + k;
             float v = 0.0f;
-            if (gm < g.M && gk < g.K) v = g.ta ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+            if (gm < g.M && gk < kend) v = g.ta ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
             if constexpr (TC) As[m][k] = __float2bfloat16_rn(v); else As[m][k] = v;
         }
 #pragma unroll 4
@@ -112,7 +123,7 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmArgs g, int epi) {
             if (g.tb) { k = e / GBN; n = e % GBN; } else { n = e / GBK; k = e % GBK; }
             const int gn = n0 + n, gk = k0 + k;
             float v = 0.0f;
-            if (gn < g.N && gk < g.K) v = g.tb ? g.B[(size_t)gk * g.ldb + gn] : g.B[(size_t)gn * g.ldb + gk];
+            if (gn < g.N && gk < kend) v = g.tb ? g.B[(size_t)gk * g.ldb + gn] : g.B[(size_t)gn * g.ldb + gk];
             if constexpr (TC) Bs[n][k] = __float2bfloat16_rn(v); else Bs[n][k] = v;
         }
         __syncthreads();
@@ -211,13 +222,24 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float *__restrict__
     if (threadIdx.x == 0) *loss = part[0] / (double)total;
 }
 
-// Bias gradient: column sums of dZ [n][ld] over the n rows, in row order.
-__global__ void k_colsum(const float *__restrict__ dz, int n, int ncol, int ld, float *__restrict__ out) {
+// Bias gradient, first pass: column sums of dZ [n][ld] over the rows of
+// slice blockIdx.y (KSLICE rows, in row order) into part[slice][ncol].
+__global__ void k_colsum(const float *__restrict__ dz, int n, int ncol, int ld, float *__restrict__ part) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncol) return;
+    const int r0 = blockIdx.y * KSLICE, r1 = min(n, r0 + KSLICE);
     float s = 0.0f;
-    for (int r = 0; r < n; ++r) s += dz[(size_t)r * ld + c];
-    out[c] = s;
+    for (int r = r0; r < r1; ++r) s += dz[(size_t)r * ld + c];
+    part[(size_t)blockIdx.y * ncol + c] = s;
+}
+
+// Sum of nsl partial results part[z][count] in slice order z = 0, 1, ...
+__global__ void k_sum_slices(const float *__restrict__ part, int nsl, int count, float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = part[i];
+    for (int z = 1; z < nsl; ++z) s += part[(size_t)z * count + i];
+    out[i] = s;
 }
 
 // Offsets of the flat parameter vector (W1 b1 W2 b2 W3 b3 W4 b4).
@@ -580,6 +602,7 @@ struct turret_mlp {
     __nv_bfloat16 *Wb;
     float *norm;  // mean_x [34], std_x [34], mean_y [6], std_y [6]
     float *X0, *T, *Y, *dY, *Z[3], *A[3], *D[2];
+    float *part;  // split-K partial sums [MAX_SLICES][128][128]
     double *loss;
     long long adam_step;
     std::string err;
@@ -619,6 +642,7 @@ void carve_mlp(MCarver &cv, int cap, turret_mlp *m) {
     }
     for (int l = 0; l < 2; ++l) M.D[l] = (float *)cv.take(c * MLP_H * 4);
     M.loss = (double *)cv.take(8);
+    M.part = (float *)cv.take((size_t)MAX_SLICES * MLP_H * MLP_H * 4);
 }
 
 turret_status mfail(turret_mlp *m, turret_status s, const std::string &msg) {
@@ -633,7 +657,8 @@ turret_status mfail(turret_mlp *m, turret_status s, const std::string &msg) {
     } while (0)
 
 cudaError_t gemm(const turret_mlp *m, const GemmArgs &g, int epi) {
-    const dim3 grid((g.M + GBM - 1) / GBM, (g.N + GBN - 1) / GBN);
+    const dim3 grid((g.M + GBM - 1) / GBM, (g.N + GBN - 1) / GBN,
+                    g.kslice > 0 ? (g.K + g.kslice - 1) / g.kslice : 1);
     if (m->precision == 0) k_gemm<true><<<grid, GTHREADS, 0, m->stream>>>(g, epi);
     else k_gemm<false><<<grid, GTHREADS, 0, m->stream>>>(g, epi);
     return cudaGetLastError();
@@ -682,10 +707,18 @@ cudaError_t backward(turret_mlp *m, int n) {
     const float *dz = m->dY;  // gradient of the current layer's output
     int nout = MLP_OUT;
     for (int l = 3; l >= 0; --l) {
-        // dW_l = dz^T a_{l-1} ([nout][kin]), db_l = column sums of dz
+        // dW_l = dz^T a_{l-1} ([nout][kin]), db_l = column sums of dz; both
+        // reduce over the batch: KSLICE-row slices, partial sums added in order
+        const int nsl = (n + KSLICE - 1) / KSLICE;
         GemmArgs g = gargs(dz, nout, 1, acts[l], kin[l], 1, m->G + offW[l], kin[l], nout, kin[l], n);
+        g.kslice = KSLICE;
+        g.part = m->part;
         if ((e = gemm(m, g, EPI_STORE)) != cudaSuccess) return e;
-        k_colsum<<<(nout + 127) / 128, 128, 0, m->stream>>>(dz, n, nout, nout, m->G + offB[l]);
+        k_sum_slices<<<(nout * kin[l] + 255) / 256, 256, 0, m->stream>>>(m->part, nsl, nout * kin[l], m->G + offW[l]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_colsum<<<dim3((nout + 127) / 128, nsl), 128, 0, m->stream>>>(dz, n, nout, nout, m->part);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_sum_slices<<<(nout + 255) / 256, 256, 0, m->stream>>>(m->part, nsl, nout, m->G + offB[l]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (l == 0) break;
         // dz_{l-1} = (dz W_l) * gelu'(z_{l-1})
@@ -717,7 +750,7 @@ cudaError_t refresh(turret_mlp *m) {
 }  // namespace
 
 extern "C" size_t mlp_workspace_bytes(int32_t batch_cap) {
-    if (batch_cap < 1 || batch_cap > (1 << 20)) return 0;
+    if (batch_cap < 1 || batch_cap > MAX_SLICES * KSLICE) return 0;
     MCarver cv{nullptr, 0};
     carve_mlp(cv, batch_cap, nullptr);
     return cv.off + 256;
