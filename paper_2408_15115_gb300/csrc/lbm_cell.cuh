@@ -103,18 +103,23 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
     }
     const int nx = g.nx, plane = (int)g.plane, ncell = (int)g.ncell;
     if ((bxf[0] | bxf[2] | byf[0] | byf[2] | bzf[0] | bzf[1] | bzf[2]) == 0) {
-        // interior (or periodic) cell: 27 plain loads, 32-bit offsets
+        // interior (or periodic) cell: 27 plain loads, each from one of nine
+        // per-thread (x, y) column pointers plus a 32-bit offset (population,
+        // plane) that is uniform over a block whose cells share z
+        const typename Codec<ST>::T *P[3][3];
+#pragma unroll
+        for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+            for (int ex = 0; ex < 3; ++ex) P[ey][ex] = f + (sy[ey] * nx + sx[ex]);
 #pragma unroll
         for (int ez = 0; ez < 3; ++ez)
 #pragma unroll
-            for (int ey = 0; ey < 3; ++ey) {
-                const int row = szp[ez] * plane + sy[ey] * nx;
+            for (int ey = 0; ey < 3; ++ey)
 #pragma unroll
                 for (int ex = 0; ex < 3; ++ex) {
                     const int i = ex + 3 * ey + 9 * ez;
-                    q[i] = Codec<ST>::load(f + i * ncell + row + sx[ex]);
+                    q[i] = Codec<ST>::load(P[ey][ex] + (i * ncell + szp[ez] * plane));
                 }
-            }
         return;
     }
     const int zo = zphys(zl, ring, g.nz);
@@ -418,10 +423,11 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
         collide_factored<ST>(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
     else
         collide_factored<ST>(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
-    const int own = zphys(zl, ring, g.nz) * (int)g.plane + y * g.nx + x;
+    const int oz = zphys(zl, ring, g.nz) * (int)g.plane;
     const int ncell = (int)g.ncell;
+    typename Codec<ST>::T *d = dst + (y * g.nx + x);
 #pragma unroll
-    for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + i * ncell + own, q[i]);
+    for (int i = 0; i < 27; ++i) Codec<ST>::store(d + (i * ncell + oz), q[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,23 +651,27 @@ __device__ __forceinline__ void pull27x2(const Geom &g, const typename Codec<ST>
         bb[e] = src_z(g, zb, e, ring, reseed, sb[e]);
         flags |= bxf[e] | byf[e] | ba[e] | bb[e];
     }
-    const int nx = g.nx, plane = (int)g.plane;
-    const size_t ncell = (size_t)g.ncell;
+    const int nx = g.nx, plane = (int)g.plane, ncell = (int)g.ncell;  // 27 ncell < 2^31
     if (flags == 0) {
+        // nine per-thread (x, y) column pointers; the (population, plane)
+        // offsets are uniform over a block whose pairs share z
+        const typename Codec<ST>::T *P[3][3];
 #pragma unroll
-        for (int ez = 0; ez < 3; ++ez)
+        for (int ey = 0; ey < 3; ++ey)
 #pragma unroll
-            for (int ey = 0; ey < 3; ++ey) {
-                const int yr = sy[ey] * nx;
-                const typename Codec<ST>::T *pa = f + (sa[ez] * plane + yr);
-                const typename Codec<ST>::T *pb = f + (sb[ez] * plane + yr);
+            for (int ex = 0; ex < 3; ++ex) P[ey][ex] = f + (sy[ey] * nx + sx[ex]);
+#pragma unroll
+        for (int ez = 0; ez < 3; ++ez) {
+            const int oa = sa[ez] * plane, ob = sb[ez] * plane;
+#pragma unroll
+            for (int ey = 0; ey < 3; ++ey)
 #pragma unroll
                 for (int ex = 0; ex < 3; ++ex) {
                     const int i = ex + 3 * ey + 9 * ez;
-                    q[i].x = Codec<ST>::load(pa + i * ncell + sx[ex]);
-                    q[i].y = Codec<ST>::load(pb + i * ncell + sx[ex]);
+                    q[i].x = Codec<ST>::load(P[ey][ex] + (i * ncell + oa));
+                    q[i].y = Codec<ST>::load(P[ey][ex] + (i * ncell + ob));
                 }
-            }
+        }
         return;
     }
     float qa[27];
@@ -767,22 +777,21 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
         }
     collide_pair<ST>(M, omega, tau, forced[0] || forced[1], forced[0], forced[1], h,
                      (MODE == K1_ALLF || MODE == K1_NEAR) ? g.force_scheme : 0, q);
-    const size_t ncell = (size_t)g.ncell;
-    const int row = y * g.nx + x;
-    typename Codec<ST>::T *da = dst + (zphys(z[0], ring, g.nz) * (int)g.plane + row);
-    typename Codec<ST>::T *db = dst + (zphys(z[1], ring, g.nz) * (int)g.plane + row);
+    const int ncell = (int)g.ncell;
+    const int oa = zphys(z[0], ring, g.nz) * (int)g.plane, ob = zphys(z[1], ring, g.nz) * (int)g.plane;
+    typename Codec<ST>::T *d = dst + (y * g.nx + x);
     if (on[0] && on[1]) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            Codec<ST>::store(da + i * ncell, q[i].x);
-            Codec<ST>::store(db + i * ncell, q[i].y);
+            Codec<ST>::store(d + (i * ncell + oa), q[i].x);
+            Codec<ST>::store(d + (i * ncell + ob), q[i].y);
         }
     } else if (on[0]) {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) Codec<ST>::store(da + i * ncell, q[i].x);
+        for (int i = 0; i < 27; ++i) Codec<ST>::store(d + (i * ncell + oa), q[i].x);
     } else {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) Codec<ST>::store(db + i * ncell, q[i].y);
+        for (int i = 0; i < 27; ++i) Codec<ST>::store(d + (i * ncell + ob), q[i].y);
     }
 }
 
