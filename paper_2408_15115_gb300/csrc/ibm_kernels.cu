@@ -355,7 +355,8 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
                                               const int *__restrict__ wlist, const int *__restrict__ wcount,
                                               int cap, DevState *st, int k, int warm) {
     constexpr int NW = NT / 32;
-    __shared__ int wc[NW];
+    constexpr int CU = 4;
+    __shared__ int wc[CU][NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const MRec rk = m.rec[k];
     const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
@@ -367,38 +368,56 @@ __device__ __forceinline__ void interp0_block(const BoxGeom &box, int nm, const 
     float *arow = m.aval + (size_t)k * ROWCAP;
     int *irow = m.aidx + (size_t)k * ROWCAP;
     int len = 0;
-    for (int base = 0; base < cnt; base += NT) {
-        const int ii = base + tid;
-        bool hit = false;
-        float a = 0.0f;
-        int j = 0;
-        if (ii < cnt) {
-            j = __ldg(list + ii);
-            const MRec rj = m.rec[j];
-            const int dx = (rj.base & 1023) - bx, dy = ((rj.base >> 10) & 1023) - by, dz = ((rj.base >> 20) & 1023) - bz;
-            if (dx >= -3 && dx <= 3 && dy >= -3 && dy <= 3 && dz >= -3 && dz <= 3) {
-                a = m.dS[j] * overlap4(rk.wx, rj.wx, dx) * overlap4(rk.wy, rj.wy, dy) * overlap4(rk.wz, rj.wz, dz);
-                hit = true;
-            }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) wc[warp] = __popc(bal);
-        __syncthreads();
-        int off = len;
-        int tot = 0;
+    // CU chunks of NT candidates per pass: their loads are issued together and
+    // their hits are compacted chunk after chunk (list order, as one chunk at a time)
+    for (int base = 0; base < cnt; base += CU * NT) {
+        bool hit[CU];
+        float a[CU];
+        int j[CU];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            if (w < warp) off += wc[w];
-            tot += wc[w];
+        for (int u = 0; u < CU; ++u) {
+            const int ii = base + u * NT + tid;
+            j[u] = ii < cnt ? __ldg(list + ii) : -1;
         }
-        if (hit) {
-            const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            if (pos < ROWCAP) {
-                arow[pos] = a;
-                irow[pos] = j;
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            hit[u] = false;
+            a[u] = 0.0f;
+            if (j[u] >= 0) {
+                const MRec rj = m.rec[j[u]];
+                const int dx = (rj.base & 1023) - bx, dy = ((rj.base >> 10) & 1023) - by,
+                          dz = ((rj.base >> 20) & 1023) - bz;
+                if (dx >= -3 && dx <= 3 && dy >= -3 && dy <= 3 && dz >= -3 && dz <= 3) {
+                    a[u] = m.dS[j[u]] * overlap4(rk.wx, rj.wx, dx) * overlap4(rk.wy, rj.wy, dy) *
+                           overlap4(rk.wz, rj.wz, dz);
+                    hit[u] = true;
+                }
             }
         }
-        len += tot;
+        unsigned bal[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            bal[u] = __ballot_sync(0xffffffffu, hit[u]);
+            if (lane == 0) wc[u][warp] = __popc(bal[u]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            int off = len, tot = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                if (w < warp) off += wc[u][w];
+                tot += wc[u][w];
+            }
+            if (hit[u]) {
+                const int pos = off + __popc(bal[u] & ((1u << lane) - 1u));
+                if (pos < ROWCAP) {
+                    arow[pos] = a[u];
+                    irow[pos] = j[u];
+                }
+            }
+            len += tot;
+        }
         __syncthreads();
     }
     if (tid == 0) {
@@ -590,12 +609,33 @@ __device__ __forceinline__ void cycle_block(int nm, const MarkerArrays &m, const
             const float *arow = m.aval + (size_t)k * ROWCAP;
             const int *irow = m.aidx + (size_t)k * ROWCAP;
             float ax = 0.0f, ay = 0.0f, az = 0.0f;
-            for (int e = lane; e < len; e += 32) {
-                const float a = arow[e];
-                const int j = irow[e];
-                ax = fmaf(a, h_in[j], ax);
-                ay = fmaf(a, h_in[nm + j], ay);
-                az = fmaf(a, h_in[2 * nm + j], az);
+            // lane l adds entries l, l + 32, l + 64, ... in that order; the loads of
+            // four of them are issued together (two memory round trips per 128
+            // entries instead of two per 32), the first four beside the row length
+            constexpr int U = 4;
+            for (int e0 = 0; e0 == 0 || e0 < len; e0 += 32 * U) {
+                float a[U], hx[U], hy[U], hz[U];
+                int j[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + 32 * u + lane;
+                    a[u] = e < ROWCAP ? arow[e] : 0.0f;
+                    const int jj = e < ROWCAP ? irow[e] : k;
+                    j[u] = (unsigned)jj < (unsigned)nm ? jj : k;  // entries past the row: any valid index
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    hx[u] = h_in[j[u]];
+                    hy[u] = h_in[nm + j[u]];
+                    hz[u] = h_in[2 * nm + j[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (e0 + 32 * u + lane < len) {
+                        ax = fmaf(a[u], hx[u], ax);
+                        ay = fmaf(a[u], hy[u], ay);
+                        az = fmaf(a[u], hz[u], az);
+                    }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {

@@ -871,57 +871,71 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
                 return;
             }
         }
-        // one barrier per chunk: the warp counts alternate between two buffers
-        __shared__ int wcount[2][2][NW];
+        // CU chunks of MB_THREADS markers per pass: their loads are issued
+        // together and their hits compacted chunk after chunk (marker order);
+        // one barrier per pass, the warp counts alternating between two buffers
+        constexpr int CU = 4;
+        __shared__ int wcount[2][CU][2][NW];
         const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
         const int nseg = (nm + MARKER_SEG - 1) / MARKER_SEG;
         int tot[2] = {0, 0};  // identical in every thread
         int par = 0;
-        for (int chunk = 0; chunk < nm; chunk += MB_THREADS) {
-            // skip chunks whose segments' stencil bases all miss [t0 - 3, t0 + 6]
-            bool reach = false;
-            for (int sg = chunk / MARKER_SEG; sg < nseg && sg * MARKER_SEG < chunk + MB_THREADS; ++sg) {
-                const int *bb = mseg + 6 * sg;
-                bool in = true;
+        for (int group = 0; group < nm; group += CU * MB_THREADS) {
+            int pb[CU];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) in = in && __ldg(bb + 3 + a) + 3 >= t0[a] && __ldg(bb + a) <= t0[a] + TILE + 2;
-                reach = reach || in;
+            for (int u = 0; u < CU; ++u) {
+                const int chunk = group + u * MB_THREADS;
+                // skip chunks whose segments' stencil bases all miss [t0 - 3, t0 + 6]
+                bool reach = false;
+                for (int sg = chunk / MARKER_SEG; sg < nseg && sg * MARKER_SEG < chunk + MB_THREADS; ++sg) {
+                    const int *bb = mseg + 6 * sg;
+                    bool in = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        in = in && __ldg(bb + 3 + a) + 3 >= t0[a] && __ldg(bb + a) <= t0[a] + TILE + 2;
+                    reach = reach || in;
+                }
+                const int k = chunk + tid;
+                const int b = k < nm ? __ldg(mbase + k) : -1;  // loaded beside the segment test
+                pb[u] = reach ? b : -1;
             }
-            if (!reach) continue;  // uniform over the block
-            const int k = chunk + tid;
-            bool hit[2] = {false, false};
-            if (k < nm) {
-                const int pb = __ldg(mbase + k);
-                const int b[3] = {pb & 1023, (pb >> 10) & 1023, (pb >> 20) & 1023};
-                hit[0] = hit[1] = true;
+            unsigned bal[CU][2];
+            bool hit[CU][2];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                hit[u][0] = hit[u][1] = pb[u] >= 0;
+                const int b[3] = {pb[u] & 1023, (pb[u] >> 10) & 1023, (pb[u] >> 20) & 1023};
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const bool lo = b[a] + 3 >= t0[a];
-                    hit[0] = hit[0] && lo && (b[a] <= t0[a] + TILE - 1);  // stencil overlaps the tile
-                    hit[1] = hit[1] && lo && (b[a] <= t0[a] + TILE + 2);  // ... or a stencil based in it
+                    hit[u][0] = hit[u][0] && lo && (b[a] <= t0[a] + TILE - 1);  // stencil overlaps the tile
+                    hit[u][1] = hit[u][1] && lo && (b[a] <= t0[a] + TILE + 2);  // ... or a stencil based in it
                 }
-            }
-            unsigned bal[2];
 #pragma unroll
-            for (int l = 0; l < 2; ++l) {
-                bal[l] = __ballot_sync(0xffffffffu, hit[l]);
-                if (lane == 0) wcount[par][l][warp] = __popc(bal[l]);
+                for (int l = 0; l < 2; ++l) {
+                    bal[u][l] = __ballot_sync(0xffffffffu, hit[u][l]);
+                    if (lane == 0) wcount[par][u][l][warp] = __popc(bal[u][l]);
+                }
             }
             __syncthreads();
 #pragma unroll
-            for (int l = 0; l < 2; ++l) {
-                int off = tot[l], sum = 0;
-                for (int w = 0; w < NW; ++w) {
-                    const int c = wcount[par][l][w];
-                    off += (w < warp) ? c : 0;
-                    sum += c;
+            for (int u = 0; u < CU; ++u)
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    int off = tot[l], sum = 0;
+                    for (int w = 0; w < NW; ++w) {
+                        const int c = wcount[par][u][l][w];
+                        off += (w < warp) ? c : 0;
+                        sum += c;
+                    }
+                    if (hit[u][l]) {
+                        const int pos = off + __popc(bal[u][l] & ((1u << lane) - 1u));
+                        if (pos < cap)
+                            tile_list[((size_t)l * (box.tx * box.ty * box.tz) + tile) * cap + pos] =
+                                group + u * MB_THREADS + tid;
+                    }
+                    tot[l] += sum;
                 }
-                if (hit[l]) {
-                    const int pos = off + __popc(bal[l] & ((1u << lane) - 1u));
-                    if (pos < cap) tile_list[((size_t)l * (box.tx * box.ty * box.tz) + tile) * cap + pos] = k;
-                }
-                tot[l] += sum;
-            }
             par ^= 1;
         }
         if (tid < 2) {
