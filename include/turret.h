@@ -87,7 +87,12 @@ typedef struct {
  *   renorm_orientation 1: modified Gram-Schmidt of d_0, d_1, d_2 each step.
  *   ibm_cycles: number n of IBM cycles (Sec. 2.2: n = 4).
  *   no_graph 1: launch every kernel of a step directly instead of replaying a
- *               captured CUDA graph (same results; for debugging).           */
+ *               captured CUDA graph (same results; for debugging).
+ *   stochastic_rounding 1 (BF16 storage only): the collide+stream stores
+ *               round each stored value up or down with probability equal to
+ *               its distance from the other neighbour (unbiased rounding),
+ *               the random bits a hash of (element, time step): results stay
+ *               deterministic.  0: round to nearest even.                   */
 typedef struct {
     int32_t force_scheme;
     int32_t rot_form;
@@ -95,6 +100,8 @@ typedef struct {
     int32_t renorm_orientation;
     int32_t ibm_cycles;
     int32_t no_graph;
+    int32_t stochastic_rounding;
+    int32_t pad0;
 } turret_flags;
 
 /* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates

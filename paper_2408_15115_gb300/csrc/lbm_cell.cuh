@@ -33,6 +33,26 @@
 
 namespace turret {
 
+// Stochastic rounding of BF16 stores (Geom::sround): the random bits come from
+// the PCG hash of Jarzynski and Olano, "Hash Functions for GPU Rendering"
+// (JCGT 9(3), 2020) -- a linear congruential step followed by O'Neill's PCG
+// RXS-M-XS output permutation -- applied to a key made of the stored element's
+// index and the time step, so a run is reproducible bit for bit.
+__device__ __forceinline__ unsigned pcg_hash(unsigned v) {
+    const unsigned state = v * 747796405u + 2891336453u;
+    const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+__device__ __forceinline__ unsigned sr_key(int element, long long step) {
+    return (unsigned)element + 0x9E3779B9u * (unsigned)step;
+}
+// bf16 bits of r with its magnitude rounded up with probability equal to the
+// dropped fraction of the last kept bit (16 random bits added below the kept
+// bits, then truncated): unbiased, E[stored] = r.
+__device__ __forceinline__ void store_bf16_sr(__nv_bfloat16 *p, float r, unsigned rnd16) {
+    *reinterpret_cast<unsigned short *>(p) = (unsigned short)((__float_as_uint(r) + rnd16) >> 16);
+}
+
 __device__ __forceinline__ int zphys(int zl, int ring, int nz) {
     int z = zl + ring;
     return z >= nz ? z - nz : z;
@@ -426,6 +446,14 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
     const int oz = zphys(zl, ring, g.nz) * (int)g.plane;
     const int ncell = (int)g.ncell;
     typename Codec<ST>::T *d = dst + (y * g.nx + x);
+    if (ST == ST_BF16 && g.sround) {
+        const int own = oz + y * g.nx + x;
+#pragma unroll
+        for (int i = 0; i < 27; ++i)
+            store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oz)), q[i],
+                          pcg_hash(sr_key(i * ncell + own, S.step)) & 0xffffu);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 27; ++i) Codec<ST>::store(d + (i * ncell + oz), q[i]);
 }
@@ -780,6 +808,17 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
     const int ncell = (int)g.ncell;
     const int oa = zphys(z[0], ring, g.nz) * (int)g.plane, ob = zphys(z[1], ring, g.nz) * (int)g.plane;
     typename Codec<ST>::T *d = dst + (y * g.nx + x);
+    if (ST == ST_BF16 && g.sround) {
+        // one hash per population serves both cells (its low and high halves)
+        const int own = oa + y * g.nx + x;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const unsigned r = pcg_hash(sr_key(i * ncell + own, S.step));
+            if (on[0]) store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oa)), q[i].x, r & 0xffffu);
+            if (on[1]) store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + ob)), q[i].y, r >> 16);
+        }
+        return;
+    }
     if (on[0] && on[1]) {
 #pragma unroll
         for (int i = 0; i < 27; ++i) {

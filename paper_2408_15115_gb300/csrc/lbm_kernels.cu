@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename C
         // carry the body and window to the next time level (no entering plane there)
         st->s[slot_out] = st->s[slot];
         st->s[slot_out].reseed = -1;
+        st->s[slot_out].step += 1;
     }
     if (MODE == K1_NEAR)  // small, on the critical path: one cell per thread
         k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, st->s[slot], hbox, box, blockIdx.x * 32 + threadIdx.x,

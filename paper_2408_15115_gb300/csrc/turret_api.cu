@@ -173,6 +173,7 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     G.ncell = G.plane * win->nz;
     G.tau0 = (float)tau;
     G.force_scheme = 0;
+    G.sround = 0;
     Carver cv{(char *)ws, 0};
     float *tau_z = nullptr;
     carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate, &tau_z);
@@ -246,11 +247,13 @@ static void drop_graphs(turret_ctx *c) {
 extern "C" turret_status lbm_set_flags(turret_ctx *c, const turret_flags *fl) {
     if (!c || !fl) return fail(c, TURRET_EINVAL, "NULL argument");
     if (fl->force_scheme < 0 || fl->force_scheme > 1 || fl->rot_form < 0 || fl->rot_form > 1 || fl->gravity < 0 ||
-        fl->gravity > 1 || fl->ibm_cycles < 1 || fl->ibm_cycles > 64)
+        fl->gravity > 1 || fl->ibm_cycles < 1 || fl->ibm_cycles > 64 || fl->stochastic_rounding < 0 ||
+        fl->stochastic_rounding > 1)
         return fail(c, TURRET_EINVAL, "invalid flags");
     if (c->has_particle) return fail(c, TURRET_ESTATE, "flags must be set before ibm_load_surface");
     c->flags = *fl;
     c->geom.force_scheme = fl->force_scheme;
+    c->geom.sround = (c->storage == ST_BF16 && fl->stochastic_rounding) ? 1 : 0;
     drop_graphs(c);
     return TURRET_OK;
 }
@@ -935,7 +938,8 @@ bool same_config(const CkptHeader &h, const turret_ctx *c) {
     return h.storage == c->storage && h.has_particle == (c->has_particle ? 1 : 0) &&
            h.nm == (c->has_particle ? c->nm : 0) && memcmp(&h.win, &c->win, sizeof(turret_window)) == 0 &&
            h.flags.force_scheme == c->flags.force_scheme && h.flags.rot_form == c->flags.rot_form &&
-           h.flags.gravity == c->flags.gravity && h.flags.ibm_cycles == c->flags.ibm_cycles && h.nu == c->nu &&
+           h.flags.gravity == c->flags.gravity && h.flags.ibm_cycles == c->flags.ibm_cycles &&
+           h.flags.stochastic_rounding == c->flags.stochastic_rounding && h.nu == c->nu &&
            h.kappa == c->kappa && h.g[0] == c->g[0] && h.g[1] == c->g[1] && h.g[2] == c->g[2] &&
            h.nbox == (c->has_particle ? c->box.nbox : 0);
 }

@@ -96,6 +96,7 @@ struct Geom {
     long long ncell;  // nx * ny * nz  (population stride)
     float tau0;
     int force_scheme;
+    int sround;            // 1: BF16 stores round stochastically (counter-based hash)
     const float *tau_z;    // [nz] relaxation time per logical plane (sponge included)
     const float *omega_z;  // [nz] 1 / tau per logical plane
 };

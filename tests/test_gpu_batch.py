@@ -13,9 +13,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _runs():
-    """Four runs: closed box (FP32), sliding periodic window with pressure top
-    and sponge (FP16), a window too narrow to split far/near cells (BF16), and
-    a mixed-boundary box with the literal rotation update (FP32)."""
+    """Five runs: closed box (FP32), sliding periodic window with pressure top
+    and sponge (FP16), a window too narrow to split far/near cells (BF16), a
+    mixed-boundary box with the literal rotation update (FP32), and a sliding
+    window in BF16 with stochastically rounded stores."""
     from paper_2408_15115_gb300 import turret as T
     out = []
     V, Tr = I.sphere(4, 8.0)
@@ -37,6 +38,11 @@ def _runs():
     t = T.Turret(32, 24, 40, 0.04, 3.0, (0, 0, -5e-5), 1, 0, 1, 1, flags={"rot_form": 1})
     t.set_fields(*I.random_state((40, 24, 32), u_amp=0.005, rho_amp=0.0005, kmax=2, seed=12))
     t.load_surface(V, Tr, (15.2, 11.9, 20.0), w0=(0, 0.002, 0.001))
+    out.append(t)
+    V, Tr = I.sphere(4, 8.0)
+    t = T.Turret(24, 24, 48, 0.05, 2.0, (0, 0, -1e-4), 0, 0, 1, 2, sponge=4, slide=1, anchor_frac=0.3,
+                 storage="bf16", flags={"stochastic_rounding": 1})
+    t.load_surface(V, Tr, (11.7, 12.2, 16.0), v0=(0, 0.001, -0.02))
     out.append(t)
     return out
 
@@ -79,7 +85,7 @@ def test_batched_runs_equal_runs_alone_bitwise(alone_40):
     b.close()
 
 
-@pytest.mark.parametrize("threads,minb,tx", [(256, 3, [64, 128, 16, 32]), (64, 2, [32, 64, 16, 64])])
+@pytest.mark.parametrize("threads,minb,tx", [(256, 3, [64, 128, 16, 32, 32]), (64, 2, [32, 64, 16, 64, 16])])
 def test_launch_shape_does_not_change_results(alone_40, threads, minb, tx):
     from paper_2408_15115_gb300 import turret as T
     runs = _runs()
@@ -112,7 +118,7 @@ def test_autotune_picks_a_valid_shape_and_caches(tmp_path):
     b = T.Batch(runs)
     cache = str(tmp_path / "tiles.json")
     c1 = b.autotune(cache_path=cache, reps=3)
-    assert c1.threads in (128, 256) and c1.minb in (2, 3) and len(c1.tx) == 4
+    assert c1.threads in (128, 256) and c1.minb in (2, 3) and len(c1.tx) == len(runs)
     # timing left every run unchanged
     for t, ref in zip(runs, before):
         _assert_same(_snapshot(t), ref)
