@@ -4,8 +4,11 @@
 
 namespace turret {
 
+// Window launches with 16-bit storage: five blocks per SM (<= 102 registers, a
+// few spilled values in L1) measured faster than four; FP32 keeps four (128
+// registers, no spill); the small near-region launch is left unconstrained.
 template <int ST, int MODE>
-__global__ void __launch_bounds__(128) k_collide_stream(Geom g, const typename Codec<ST>::T *__restrict__ src,
+__global__ void __launch_bounds__(128, MODE == K1_NEAR ? 1 : (ST == ST_F32 ? 4 : 5)) k_collide_stream(Geom g, const typename Codec<ST>::T *__restrict__ src,
                                                         typename Codec<ST>::T *__restrict__ dst,
                                                         const float *__restrict__ utop_in,
                                                         float *__restrict__ utop_out, DevState *st, int slot,
