@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100)
+    p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--learned-steps", type=int, default=6000)
     return p.parse_args()
 
 
@@ -347,6 +349,79 @@ def surrogate_leg(dev):
                  "held_out_mean_rel_force_error": {k: float(v.mean()) for k, v in e.items()}}
 
 
+def learned_leg(dev, steps):
+    """The learned-predictor workload: the irregular d = 32 particle (6252
+    markers) in the 256 x 256 x 512 window at Re ~ 1000, its force/torque
+    network trained on trajectories of the three single-particle workloads
+    (sphere box, prolate and irregular turret windows), run beside the same
+    window with the paper's predictor.  Reports the step rate of both, how
+    often the network drove the step, the drag and settling velocity of the
+    network run against the paper run (mean over the last third), and the
+    one-step force error of the network against linear extrapolation on the
+    paper run's own trajectory (never seen in training)."""
+    import time as _t
+
+    import numpy as np
+    import torch
+
+    from paper_2408_15115_gb300 import configs
+    from paper_2408_15115_gb300 import surrogate as S
+
+    t0 = _t.perf_counter()
+    recs = []
+    for cfg, n in ((configs.sphere_box(), 500), (configs.prolate_turret(), 2000),
+                   (configs.irregular_turret(storage="f32"), 1500)):
+        t = configs.make_turret(cfg, device=dev)
+        t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
+        recs.append(S.record(t, n))
+        t.close()
+    x, y = S.dataset(recs)
+    torch.cuda.synchronize(dev)
+    t1 = _t.perf_counter()
+    net, hist = S.train(x, y, epochs=60, batch=1024, lr=1e-3, weight_decay=1e-4, device=dev)
+    torch.cuda.synchronize(dev)
+    t2 = _t.perf_counter()
+    res = {"workload": "irregular_256x256x512_turret", "storage": "f32", "steps": steps,
+           "train_pairs": int(x.shape[0]), "collect_s": t1 - t0, "train_s": t2 - t1, "final_train_loss": hist[-1]}
+    hists = {}
+    for mode in ("paper", "mlp"):
+        cfg = configs.irregular_large(storage="f32")
+        t = configs.make_turret(cfg, device=dev)
+        if mode == "mlp":
+            # the network is used while its running error is at most that of
+            # linear extrapolation (the plain predictor) on the same time levels
+            t.set_predictor("mlp", net, resid_theta=1.0, relative=True)
+        t.set_log(steps + 1)
+        t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
+        h, tot_ms = [], 0.0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(steps // 100):
+            ev0.record(t.stream)
+            t.step(100)
+            ev1.record(t.stream)
+            torch.cuda.synchronize(dev)
+            tot_ms += ev0.elapsed_time(ev1)
+            st = t.state()
+            h.append((st["F"][2], st["v"][2]))
+        hists[mode] = np.array(h)
+        entry = {"us_per_step": 1e3 * tot_ms / (100 * (steps // 100)),
+                 "particle_steps_per_s": 100 * (steps // 100) / (tot_ms / 1e3)}
+        if mode == "mlp":
+            ps = t.predictor_stats()
+            entry.update({"network_predictions": ps["net_steps"], "fallbacks": ps["fallbacks"]})
+        else:
+            xt, yt = S.dataset([t.log_records()])
+            e = S.offline_errors(net, xt, yt)
+            res["paper_run_one_step_rel_force_error"] = {k: float(v.mean()) for k, v in e.items()}
+        res[mode] = entry
+        t.close()
+    late = slice(2 * len(hists["paper"]) // 3, None)
+    a, b = hists["mlp"][late].mean(0), hists["paper"][late].mean(0)
+    res["mlp_vs_paper_rel_dev"] = {"drag": float(abs(a[0] / b[0] - 1.0)), "settling_velocity": float(abs(a[1] / b[1] - 1.0))}
+    net.close()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -448,6 +523,8 @@ def run_ours(args):
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = ensemble_leg(dev, args.ensemble_steps, max(W, 3),
                                        os.path.join(ROOT, "paper_2408_15115_gb300", "_build", "tiles.json"))
+    if world == 1 and not args.no_learned:
+        out["learned_predictor"] = learned_leg(dev, args.learned_steps)
     if world == 1 and not args.no_cpu_baseline:
         v, cores, n, dt = oracle_sample(cfg)
         out["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",

@@ -359,10 +359,15 @@ TURRET_API const char *mlp_last_error(const turret_mlp *m);
  *       (w(t+1) = w(t+1/2) + (J/m)^-1 T^/(2m) in the literal rotation form);
  *   TURRET_PRED_WARM: start the IBM cycles from the previous step's
  *       Lagrangian force and run at most ibm_cycles of them, skipping the
- *       rest once the slip max_k |U_k - I[u* + S h](X_k)| is below slip_eps.
+ *       rest once the slip max_k |U_k - I[u* + S h](X_k)| is below slip_eps;
+ *   TURRET_PRED_REL: resid_theta is a ratio: the network's prediction is used
+ *       while the running mean (weight 1/8 per time level) of its error is at
+ *       most resid_theta times the running mean of linear extrapolation's
+ *       error on the same time levels.
  * Takes effect for the following steps (a batch copies it when created).    */
 #define TURRET_PRED_WARM 1
 #define TURRET_PRED_VEL 2
+#define TURRET_PRED_REL 4
 TURRET_API turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const turret_mlp *net, int32_t options,
                                               double slip_eps, double resid_theta);
 

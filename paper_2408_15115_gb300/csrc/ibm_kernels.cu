@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArray
 // linear one), the force/torque history, and the trajectory record of time
 // level st->s[slot] (when a log is attached).
 __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ ft, DevState *st, int slot,
-                                             int predictor, double theta, double *__restrict__ log,
+                                             int predictor, int opts, double theta, double *__restrict__ log,
                                              long long log_cap) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double a = 0.0;
@@ -717,7 +717,20 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
     if (predictor != 0 && P.net_ok) {  // the network's own accuracy decides the fallback
         resid_net = rel_err(P.Fnet);
         P.resid_net = resid_net;
-        P.fallback = !(resid_net <= theta);
+        if (opts & PRED_REL) {
+            // relative rule: running means of the network's error and of linear
+            // extrapolation's error on the same time levels; the network is used
+            // while its mean is at most theta times the linear one
+            double Flin[3];
+            for (int q = 0; q < 3; ++q) Flin[q] = 2.0 * P.Fh[0][q] - P.Fh[1][q];
+            const double rl = rel_err(Flin);
+            const bool first = P.ema_lin == 0.0 && P.ema_net == 0.0;
+            P.ema_net = first ? resid_net : P.ema_net + 0.125 * (resid_net - P.ema_net);
+            P.ema_lin = first ? rl : P.ema_lin + 0.125 * (rl - P.ema_lin);
+            P.fallback = !(P.ema_net <= theta * P.ema_lin);
+        } else {
+            P.fallback = !(resid_net <= theta);
+        }
         P.net_ok = 0;
     }
     for (int h = 3; h > 0; --h)
@@ -751,9 +764,9 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
 }
 
 __global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st, int slot,
-                                                   int predictor, double theta, double *__restrict__ log,
-                                                   long long log_cap) {
-    reduce_block(nm, ft, st, slot, predictor, theta, log, log_cap);
+                                                   int predictor, int opts, double theta,
+                                                   double *__restrict__ log, long long log_cap) {
+    reduce_block(nm, ft, st, slot, predictor, opts, theta, log, log_cap);
 }
 
 constexpr int SPREAD_SLICES = 8;                               // candidate slices per tile
@@ -880,7 +893,7 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_batch_cycle(const RunDesc
 
 __global__ void __launch_bounds__(192) k_batch_reduce_ft(const RunDesc *__restrict__ runs, int slot) {
     const RunDesc &R = runs[blockIdx.x];
-    reduce_block(R.nm, R.m.ft, R.st, slot, R.bc.predictor, R.bc.resid_theta, R.bc.log, R.bc.log_cap);
+    reduce_block(R.nm, R.m.ft, R.st, slot, R.bc.predictor, R.bc.pred_opts, R.bc.resid_theta, R.bc.log, R.bc.log_cap);
 }
 
 __global__ void __launch_bounds__(SPREAD_THREADS) k_batch_spread(const RunDesc *__restrict__ runs,
@@ -916,7 +929,7 @@ cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out
 }
 
 cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, int slot, const BodyConst &bc, cudaStream_t s) {
-    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st, slot, bc.predictor, bc.resid_theta, bc.log, bc.log_cap);
+    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st, slot, bc.predictor, bc.pred_opts, bc.resid_theta, bc.log, bc.log_cap);
     return cudaGetLastError();
 }
 

@@ -803,7 +803,8 @@ extern "C" turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const
                                               double slip_eps, double resid_theta) {
     if (!c) return fail(c, TURRET_EINVAL, "NULL context");
     if (mode < 0 || mode > 2) return fail(c, TURRET_EINVAL, "predictor mode must be 0, 1 or 2");
-    if (options < 0 || options > (PRED_WARM | PRED_VEL)) return fail(c, TURRET_EINVAL, "invalid predictor options");
+    if (options < 0 || options > (PRED_WARM | PRED_VEL | PRED_REL))
+        return fail(c, TURRET_EINVAL, "invalid predictor options");
     if (mode == 2 && !net) return fail(c, TURRET_EINVAL, "the network predictor needs a network");
     if (!(slip_eps >= 0.0) || !(resid_theta > 0.0)) return fail(c, TURRET_EINVAL, "invalid tolerances");
     c->pred_mode = mode;

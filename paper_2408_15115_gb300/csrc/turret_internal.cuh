@@ -57,6 +57,7 @@ struct Predictor {
     double Fnet[3], Tnet[3];    // the network's prediction (made whenever it can run)
     double resid;               // |F - Fhat| / |F| of the last checked prediction
     double resid_net;           // |F - Fnet| / |F| of the network's last prediction
+    double ema_net, ema_lin;    // running means (weight 1/8) of the network's and of linear extrapolation's error
     unsigned int slip[8];       // per IBM cycle: max over markers of |U - I[u* + S h]| (float bits)
     int hist_n;                 // valid history entries, 0..4
     int fallback;               // 1: the next prediction is the linear one
@@ -78,7 +79,7 @@ struct DevState {
     Predictor pr;
 };
 
-enum { PRED_WARM = 1, PRED_VEL = 2 };
+enum { PRED_WARM = 1, PRED_VEL = 2, PRED_REL = 4 };
 
 // Trajectory record written after the force of each time level j is known:
 // d(j) [9], v(j-1/2) [3], w(j-1/2) [3], F(j) [3], T(j) [3], j, |F - Fhat| / |F|
@@ -122,7 +123,8 @@ struct BodyConst {
     // 1, 2 the marker velocities are predicted at t + 1 and the IBM cycles
     // start from the previous h and stop once the slip is below slip_eps
     int predictor;
-    int pred_opts;       // PRED_WARM: warm-started adaptive cycles; PRED_VEL: marker velocities at t + 1
+    int pred_opts;       // PRED_WARM: warm-started adaptive cycles; PRED_VEL: marker velocities at t + 1;
+                         // PRED_REL: resid_theta is relative to linear extrapolation's error
     float slip_eps;
     double resid_theta;  // fall back to the linear prediction above this relative error
     double *log;         // trajectory records [log_cap][LOG_REC], or null

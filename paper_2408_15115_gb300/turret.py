@@ -290,12 +290,14 @@ class Turret:
     PREDICTORS = {"paper": 0, "linear": 1, "mlp": 2}
     LOG_REC = 32
 
-    def set_predictor(self, mode="paper", net=None, warm=False, velocity=True, slip_eps=1e-4, resid_theta=0.5):
+    def set_predictor(self, mode="paper", net=None, warm=False, velocity=True, slip_eps=1e-4, resid_theta=0.5,
+                      relative=False):
         """Force/torque predictor: 'paper' (the method as published), 'linear'
         or 'mlp' (with the MLP object `net`); warm: warm-started adaptive IBM
-        cycles; velocity: marker velocities at t + 1.  See turret_set_predictor."""
+        cycles; velocity: marker velocities at t + 1; relative: resid_theta is
+        a ratio to linear extrapolation's running error.  See turret_set_predictor."""
         self._net = net
-        opts = (1 if warm else 0) | (2 if velocity else 0)
+        opts = (1 if warm else 0) | (2 if velocity else 0) | (4 if relative else 0)
         self._check(self._L.turret_set_predictor(self.ctx, self.PREDICTORS[mode], net.m if net is not None else None,
                                                  opts, float(slip_eps), float(resid_theta)))
 

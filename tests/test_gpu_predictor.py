@@ -109,6 +109,35 @@ def test_network_prediction_in_the_step_and_fallback(precision, tol):
     net.close()
 
 
+def test_relative_fallback_rule():
+    # relative rule (theta = 1): a network whose outputs are all zero predicts
+    # exactly the linear extrapolation, ties it and is used at every step; a
+    # network with large outputs loses to it and is dropped after one step
+    from paper_2408_15115_gb300 import turret as T
+    zero = T.MLP(I.mlp_init_params(0).astype(np.float32) * 0.0, batch_cap=16)
+    t, c = _turret(kind="oblate", seed=5)
+    t.set_predictor("mlp", zero, resid_theta=1.0, relative=True)
+    _load(t, c)
+    t.step(30)
+    st = t.predictor_stats()
+    assert st["net_steps"] == 30 - 3 and st["fallbacks"] == 3
+    t.close()
+    p = I.mlp_init_params(1).astype(np.float32)
+    p[-6:] = 50.0  # output biases: departures of 50 (standardised) from linear extrapolation
+    bad = T.MLP(p, batch_cap=16)
+    t, c = _turret(kind="oblate", seed=5)
+    t.set_predictor("mlp", bad, resid_theta=1.0, relative=True)
+    t.set_log(64)
+    _load(t, c)
+    t.step(30)
+    made = t.log_records().cpu().numpy()[1:, 29]
+    assert made[3] == 1.0 and np.all(made[4:] == 0.0)
+    assert t.predictor_stats()["net_steps"] == 1
+    t.close()
+    zero.close()
+    bad.close()
+
+
 def _settle(mode, net=None, warm=False, steps=1500):
     t, c = _turret(kind="irregular", seed=7, d=12.0, re=40.0)
     if mode != "paper":
