@@ -119,6 +119,9 @@ typedef struct {
     double area;     /* surface area, sum of the marker areas dS_k          */
     int32_t kernels_per_step;  /* kernel launches one step() enqueues      */
     int32_t pad0;
+    double Fp[3];    /* pressure part of F: sum_k dS_k (-p(X_k)) n_k, with
+                      * p = c_s^2 (rho - 1) the isotropic part of Eq. 10;
+                      * F - Fp is the viscous (shear) part                 */
 } turret_particle_state;
 
 /* ---- fluid ------------------------------------------------------------- */

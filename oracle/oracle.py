@@ -205,7 +205,7 @@ class Sim:
     Boundary codes: bc_x/bc_y 0 periodic, 1 no-slip; bc_bottom/bc_top 0 periodic,
     1 no-slip, 2 constant pressure (top only).  Arrays are (nz, ny, nx, ...)."""
 
-    STATE_FIELDS = 42
+    STATE_FIELDS = 45
 
     def __init__(self, nx, ny, nz, tau, bc_x=0, bc_y=0, bc_bottom=0, bc_top=0, sponge=0, slide=0,
                  anchor_frac=0.25, force_scheme=0, rot_form=0, gravity=0, renorm=0, ibm_cycles=4,
@@ -280,7 +280,8 @@ class Sim:
         lib().orc_particle_state(C.c_void_p(self._s), _p(o))
         return dict(r=o[0:3].copy(), d=o[3:12].reshape(3, 3).copy(), v=o[12:15].copy(), w=o[15:18].copy(),
                     F=o[18:21].copy(), T=o[21:24].copy(), L=o[24:27].copy(), origin=o[27:30].copy(),
-                    step=int(o[30]), volume=o[31], J_over_m=o[32:41].reshape(3, 3).copy(), area=o[41])
+                    step=int(o[30]), volume=o[31], J_over_m=o[32:41].reshape(3, 3).copy(), area=o[41],
+                    Fp=o[42:45].copy())
 
     def markers(self, nm):
         X = np.zeros((nm, 3)); n = np.zeros((nm, 3)); U = np.zeros((nm, 3)); dS = np.zeros(nm); hl = np.zeros((nm, 3))

@@ -387,6 +387,7 @@ typedef struct {
     double *hl;                /* Lagrangian IBM force (last h_{l=0} used for h_imm) */
     double vol, Jm[9], Jminv[9], area;
     double r[3], d[9], v[3], w[3], L[3], F[3], T[3];
+    double Fp[3];              /* pressure part of F: sum_k dS_k (-p(X_k)) n_k */
     int64_t origin[3], step;
     int status;
 } orc_sim;
@@ -692,6 +693,22 @@ static void force_torque(orc_sim *s) {
     orc_grid g = sim_grid(s);
     double *sk = (double *)malloc(sizeof(double) * 9 * (size_t)s->nm);
     orc_interp(&g, s->sig, 9, s->X, s->nm, sk);
+    /* the isotropic part of Eq. (10) alone: p = c_s^2 (rho - 1) per cell from
+     * the same populations, interpolated to the markers; its surface sum is the
+     * pressure force, F - Fp the viscous one */
+    double *pc = (double *)malloc(sizeof(double) * (size_t)s->ncell);
+    for (int64_t c = 0; c < s->ncell; ++c) {
+        double rho = 0.0;
+        for (int i = 0; i < NQ; ++i) rho += s->f[c * NQ + i];
+        pc[c] = (rho - 1.0) / 3.0;
+    }
+    double *pk = (double *)malloc(sizeof(double) * (size_t)s->nm);
+    orc_interp(&g, pc, 1, s->X, s->nm, pk);
+    for (int a = 0; a < 3; ++a) s->Fp[a] = 0.0;
+    for (int64_t k = 0; k < s->nm; ++k)
+        for (int a = 0; a < 3; ++a) s->Fp[a] -= s->dS[k] * pk[k] * s->n[3 * k + a];
+    free(pk);
+    free(pc);
     double C[3] = {s->r[0] - (double)s->origin[0], s->r[1] - (double)s->origin[1], s->r[2] - (double)s->origin[2]};
     for (int a = 0; a < 3; ++a) s->F[a] = s->T[a] = 0.0;
     for (int64_t k = 0; k < s->nm; ++k) {
@@ -855,7 +872,7 @@ int orc_step(orc_sim *s, int n) {
 }
 
 /* Particle state: r[3] (global), d[9] (rows d_i), v[3], w[3], F[3], T[3],
- * L[3], origin[3], step, vol, Jm[9], area  -> 42 doubles. */
+ * L[3], origin[3], step, vol, Jm[9], area, Fp[3]  -> 45 doubles. */
 void orc_particle_state(const orc_sim *s, double *o) {
     int q = 0;
     for (int a = 0; a < 3; ++a) o[q++] = s->r[a];
@@ -870,6 +887,7 @@ void orc_particle_state(const orc_sim *s, double *o) {
     o[q++] = s->vol;
     for (int a = 0; a < 9; ++a) o[q++] = s->Jm[a];
     o[q++] = s->area;
+    for (int a = 0; a < 3; ++a) o[q++] = s->Fp[a];
 }
 
 /* Marker arrays at the current time level (X, n, U: 3 per marker; dS; hl). */

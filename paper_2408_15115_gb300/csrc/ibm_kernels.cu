@@ -314,13 +314,14 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
     const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
     const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
     const size_t N = box.nbox;
-    float acc[9];
+    float acc[10];
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = w0 * ba.u[c * N + c0] + w1 * ba.u[c * N + c1];
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
+    acc[9] = w0 * ba.p[c0] + w1 * ba.p[c1];
 #pragma unroll
-    for (int c = 0; c < 9; ++c)
+    for (int c = 0; c < 10; ++c)
 #pragma unroll
         for (int q = 16; q > 0; q >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], q);
     if (lane == 0) {
@@ -346,6 +347,11 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
         m.ft[3 * nm + k] = r1 * f2 - r2 * f1;
         m.ft[4 * nm + k] = r2 * f0 - r0 * f2;
         m.ft[5 * nm + k] = r0 * f1 - r1 * f0;
+        // the isotropic part -p I of sigma alone: the pressure force
+        const float pdS = -dS * acc[9];
+        m.ft[6 * nm + k] = pdS * nx;
+        m.ft[7 * nm + k] = pdS * ny;
+        m.ft[8 * nm + k] = pdS * nz;
     }
 }
 
@@ -674,8 +680,9 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_cycle(int nm, MarkerArray
     cycle_block(nm, m, h_in, h_out, h_final, last, blockIdx.x, st, cyc, adaptive, eps);
 }
 
-// F = sum_k dS sigma.n, T = sum_k arm x (dS sigma.n) in FP64: warp c sums
-// component c, lane l the markers l, l+32, ... in order, then an xor tree.
+// F = sum_k dS sigma.n, T = sum_k arm x (dS sigma.n) and the pressure part
+// Fp = sum_k -dS p n in FP64: warp c (of 9) sums component c, lane l the
+// markers l, l+32, ... in order, then an xor tree.
 // Then, in thread 0: the relative error of the prediction made for this time
 // level (predictor modes: a large one switches the next prediction to the
 // linear one), the force/torque history, and the trajectory record of time
@@ -689,7 +696,7 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) {
-        if (c < 3) st->F[c] = a; else st->T[c - 3] = a;
+        if (c < 3) st->F[c] = a; else if (c < 6) st->T[c - 3] = a; else st->Fp[c - 6] = a;
         if (!isfinite(a)) atomicCAS(&st->status, 0, STAT_DIVERGED);
     }
     __syncthreads();
@@ -763,7 +770,7 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
     P.logged += 1;
 }
 
-__global__ void __launch_bounds__(192) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st, int slot,
+__global__ void __launch_bounds__(288) k_reduce_ft(int nm, const float *__restrict__ ft, DevState *st, int slot,
                                                    int predictor, int opts, double theta,
                                                    double *__restrict__ log, long long log_cap) {
     reduce_block(nm, ft, st, slot, predictor, opts, theta, log, log_cap);
@@ -891,7 +898,7 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_batch_cycle(const RunDesc
                 last, lb, R.st, cyc, adaptive, R.bc.slip_eps);
 }
 
-__global__ void __launch_bounds__(192) k_batch_reduce_ft(const RunDesc *__restrict__ runs, int slot) {
+__global__ void __launch_bounds__(288) k_batch_reduce_ft(const RunDesc *__restrict__ runs, int slot) {
     const RunDesc &R = runs[blockIdx.x];
     reduce_block(R.nm, R.m.ft, R.st, slot, R.bc.predictor, R.bc.pred_opts, R.bc.resid_theta, R.bc.log, R.bc.log_cap);
 }
@@ -929,7 +936,7 @@ cudaError_t launch_cycle(int nm, MarkerArrays m, const float *h_in, float *h_out
 }
 
 cudaError_t launch_reduce_ft(int nm, MarkerArrays m, DevState *st, int slot, const BodyConst &bc, cudaStream_t s) {
-    k_reduce_ft<<<1, 192, 0, s>>>(nm, m.ft, st, slot, bc.predictor, bc.pred_opts, bc.resid_theta, bc.log, bc.log_cap);
+    k_reduce_ft<<<1, 288, 0, s>>>(nm, m.ft, st, slot, bc.predictor, bc.pred_opts, bc.resid_theta, bc.log, bc.log_cap);
     return cudaGetLastError();
 }
 
@@ -965,7 +972,7 @@ cudaError_t launch_batch_cycle(const RunDesc *runs, const int *prefix, int nruns
 }
 
 cudaError_t launch_batch_reduce_ft(const RunDesc *runs, int nruns, int slot, cudaStream_t s) {
-    k_batch_reduce_ft<<<nruns, 192, 0, s>>>(runs, slot);
+    k_batch_reduce_ft<<<nruns, 288, 0, s>>>(runs, slot);
     return cudaGetLastError();
 }
 

@@ -158,7 +158,7 @@ static turret_status run_spread(const float *X, const float *h, const float *dS,
     memset(&m, 0, sizeof m);
     m.rec = rec;
     BoxArrays ba;
-    ba.u = ba.s = nullptr;
+    ba.u = ba.s = ba.p = nullptr;
     ba.h = field;
     if (launch_spread(L.box, (int)nm, m, ba, list, count, L.cap, s) != cudaSuccess) return TURRET_ECUDA;
     int herr = 0;

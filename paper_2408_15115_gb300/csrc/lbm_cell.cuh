@@ -1006,6 +1006,7 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
         for (int k = 0; k < 3; ++k) ba.u[k * box.nbox + b] = 0.0f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) ba.s[k * box.nbox + b] = 0.0f;
+        ba.p[b] = 0.0f;
         return;
     }
     float q[27];
@@ -1023,6 +1024,7 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
     ba.s[3 * box.nbox + b] = k2 * M.Pxy;
     ba.s[4 * box.nbox + b] = k2 * M.Pxz;
     ba.s[5 * box.nbox + b] = k2 * M.Pyz;
+    ba.p[b] = p;
 }
 
 }  // namespace turret

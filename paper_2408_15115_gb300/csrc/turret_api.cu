@@ -406,7 +406,7 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     m.dS = (const float *)cv.take(nm * 4);
     m.rec = (MRec *)cv.take(nm * sizeof(MRec));
     m.base = (int *)cv.take(nm * 4);
-    m.ft = (float *)cv.take(6 * nm * 4);
+    m.ft = (float *)cv.take(9 * nm * 4);
     m.U = (float *)cv.take(3 * nm * 4);
     m.n = (float *)cv.take(3 * nm * 4);
     m.arm = (float *)cv.take(3 * nm * 4);
@@ -420,6 +420,7 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     BoxArrays ba;
     ba.u = (float *)cv.take(3 * nb * 4);
     ba.s = (float *)cv.take(6 * nb * 4);
+    ba.p = (float *)cv.take(nb * 4);
     ba.h = (float *)cv.take(3 * nb * 4);
     int *tl = (int *)cv.take(2 * ntiles * (size_t)L.cap * 4);  // spreading list, rows-of-A list
     int *tc = (int *)cv.take(2 * ntiles * 4);
@@ -883,6 +884,7 @@ extern "C" turret_status query_particle_state(turret_ctx *c, turret_particle_sta
         out->w[a] = S.w[a];
         out->F[a] = D.F[a];
         out->T[a] = D.T[a];
+        out->Fp[a] = D.Fp[a];
         out->L[a] = S.L[a];
         out->origin[a] = S.origin[a];
     }

@@ -74,6 +74,7 @@ struct Predictor {
 struct DevState {
     BodySlot s[2];
     double F[3], T[3];     // hydrodynamic force / torque at the latest time level
+    double Fp[3];          // the pressure part of F (F - Fp: viscous part)
     int status;
     unsigned int counter;
     Predictor pr;
@@ -150,7 +151,7 @@ struct MarkerArrays {
     const float *dS;   // [nm]
     MRec *rec;         // [nm] stencil records
     int *base;         // [nm] packed stencil bases (copy of rec[k].base, coalesced for binning)
-    float *ft;         // [6][nm] dS sigma.n and its moment about C_m
+    float *ft;         // [9][nm] dS sigma.n, its moment about C_m, and the pressure part -dS p n
     float *U;          // [3][nm] prescribed velocity
     float *n;          // [3][nm] lab-frame normal
     float *arm;        // [3][nm] X_k - C_m
@@ -167,6 +168,7 @@ struct MarkerArrays {
 struct BoxArrays {
     float *u;   // [3][nbox] u*
     float *s;   // [6][nbox] sigma xx yy zz xy xz yz
+    float *p;   // [nbox] pressure c_s^2 (rho - 1)
     float *h;   // [3][nbox] spread force (h_imm after the last cycle)
 };
 

@@ -37,7 +37,7 @@ class ParticleState(C.Structure):
                 ("F", C.c_double * 3), ("T", C.c_double * 3), ("L", C.c_double * 3),
                 ("origin", C.c_int64 * 3), ("step", C.c_int64), ("status", C.c_int32), ("n_markers", C.c_int32),
                 ("volume", C.c_double), ("area", C.c_double), ("kernels_per_step", C.c_int32),
-                ("pad0", C.c_int32)]
+                ("pad0", C.c_int32), ("Fp", C.c_double * 3)]
 
 
 class TurretError(RuntimeError):
@@ -258,7 +258,7 @@ class Turret:
         return dict(r=np.array(s.r), d=np.array(s.d).reshape(3, 3), v=np.array(s.v), w=np.array(s.w),
                     F=np.array(s.F), T=np.array(s.T), L=np.array(s.L), origin=np.array(s.origin),
                     step=int(s.step), status=int(s.status), n_markers=int(s.n_markers), volume=s.volume,
-                    area=s.area, kernels_per_step=int(s.kernels_per_step), rc=rc)
+                    area=s.area, kernels_per_step=int(s.kernels_per_step), Fp=np.array(s.Fp), rc=rc)
 
     def macro(self):
         """(4, nz, ny, nx) float32 tensor: rho, u_x, u_y, u_z of f(t)."""

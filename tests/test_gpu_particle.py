@@ -15,6 +15,8 @@ def _compare_state(t, s, tol_f=1e-4, tol_v=1e-5, r0=None):
     a, b = t.state(), s.state()
     scale_f = max(np.abs(b["F"]).max(), 1e-300)
     assert np.abs(a["F"] - b["F"]).max() / scale_f < tol_f, (a["F"], b["F"])
+    # the pressure part of the force (isotropic part of Eq. 10) alike
+    assert np.abs(a["Fp"] - b["Fp"]).max() / max(scale_f, np.abs(b["Fp"]).max()) < tol_f, (a["Fp"], b["Fp"])
     scale_v = max(np.abs(b["v"]).max(), 1e-300)
     assert np.abs(a["v"] - b["v"]).max() / scale_v < tol_v, (a["v"], b["v"])
     # the position integrates v: the velocity tolerance times the distance travelled

@@ -136,3 +136,35 @@ def test_marker_too_close_to_wall_rejected():
     s.init_fields()
     with pytest.raises(ValueError):
         s.load_particle(V, T, r0=(8.0, 8.0, 3.5))
+
+
+def _linear_pressure_force(nf, a=1e-4, n=20):
+    V, T = I.icosphere(nf, 5.0)
+    s = O.Sim(n, n, n, tau=0.8, kappa=2.0, g=(0, 0, 0))
+    x = np.arange(n, dtype=np.float64)
+    rho = np.broadcast_to(1.0 + 3.0 * a * x[None, None, :], (n, n, n)).copy()
+    s.init_fields(rho, np.zeros((n, n, n, 3)))
+    s.load_particle(V, T, r0=(9.7, 10.2, 9.9))
+    return s.state()
+
+
+def test_pressure_force_of_a_linear_pressure_field():
+    # fluid at rest with rho = 1 + 3 a x, i.e. p = c_s^2 (rho - 1) = a x: the
+    # stress of Eq. 10 is -p I up to the tiny P1 of one streaming step of the
+    # equilibria, so the force is the pressure force, and by the divergence
+    # theorem F = -oint p n dS = -a V e_x (the Peskin kernel interpolates a
+    # linear field exactly; what remains is the surface discretisation, whose
+    # error falls as h^2 with the icosphere's edge h)
+    a = 1e-4
+    st8, st4 = _linear_pressure_force(8, a), _linear_pressure_force(4, a)
+    assert np.abs(st8["F"] - st8["Fp"]).max() < 1e-6 * abs(st8["F"][0])
+    e8 = st8["Fp"][0] / (-a * st8["volume"]) - 1.0
+    e4 = st4["Fp"][0] / (-a * st4["volume"]) - 1.0
+    assert abs(e8) < 5e-3 and 3.0 < e4 / e8 < 5.0  # second order in the edge length
+    assert np.abs(st8["Fp"][1:]).max() < 1e-6 * abs(a) * st8["volume"]
+    # a uniform pressure adds nothing beyond the discretisation residual of oint n dS
+    V, T = I.icosphere(8, 5.0)
+    s2 = O.Sim(20, 20, 20, tau=0.8, kappa=2.0, g=(0, 0, 0))
+    s2.init_fields(np.full((20, 20, 20), 1.003), np.zeros((20, 20, 20, 3)))
+    s2.load_particle(V, T, r0=(9.7, 10.2, 9.9))
+    assert np.abs(s2.state()["Fp"]).max() < 1e-3 * 0.001 * st8["area"]
