@@ -15,9 +15,7 @@ import numpy as np
 from . import inputs as I
 
 
-def cg71_cd(re):
-    """Clift & Gauvin (1971) drag coefficient, Eq. 28."""
-    return 24.0 / re * (1.0 + 0.15 * re ** 0.687) + 0.42 / (1.0 + 4.25e4 * re ** -1.16)
+from .analysis import cg71_cd  # Clift & Gauvin (1971) drag coefficient, Eq. 28
 
 
 def gravity_for(re, d, nu, kappa):
