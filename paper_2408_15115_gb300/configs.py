@@ -13,8 +13,6 @@ import math
 import numpy as np
 
 from . import inputs as I
-
-
 from .analysis import cg71_cd  # Clift & Gauvin (1971) drag coefficient, Eq. 28
 
 
