@@ -360,13 +360,16 @@ static void cross(const double *a, const double *b, double *c) {
 typedef struct {
     int nx, ny, nz;
     int bc_x, bc_y;           /* 0 periodic, 1 no-slip (halfway bounce-back)     */
-    int bc_bottom, bc_top;    /* 0 periodic, 1 no-slip, 2 constant pressure       */
+    int bc_bottom, bc_top;    /* 0 periodic, 1 no-slip, 2 constant pressure (top),
+                               * 3 no-slip wall moving in its plane (uw_*)      */
     int sponge;               /* sponge length in planes below the top            */
     int slide;                /* 1: window follows the particle vertically        */
     double anchor_frac;
     double tau0;              /* tau from nu = c_s^2 (tau - 1/2), Eq. 9           */
     int force_scheme, rot_form, gravity, renorm, ibm_cycles;
     double kappa, g[3];
+    int fixed_position;       /* 1: the centre of mass is held (v = 0), rotation free */
+    double uw_bottom[3], uw_top[3];  /* velocities of moving walls (bc 3)      */
 } orc_params;
 
 typedef struct {
@@ -470,7 +473,12 @@ static void collide_all(orc_sim *s) {
  *   constant-pressure top (READING): the ghost node above the top plane holds
  *     f0(rho = 1, u_top) with u_top the velocity of the top fluid node below
  *     the ghost at the previous collision.
- * A source outside a no-slip face takes precedence over the pressure ghost. */
+ * A source outside a no-slip face takes precedence over the pressure ghost.
+ *   moving wall (bc 3, shear flows; READING, the paper gives no rule): the
+ *     halfway bounce-back of a wall moving with velocity u_w in its plane adds
+ *     the momentum the wall imparts, f_i(x) = f*_{opp i}(x) + 2 w_i rho_w
+ *     (xi_i . u_w) / c_s^2 with rho_w = 1 (the reference density), for every
+ *     population whose source lies beyond that face.                       */
 static void stream_all(orc_sim *s) {
     const int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
 #pragma omp parallel for schedule(static)
@@ -481,6 +489,7 @@ static void stream_all(orc_sim *s) {
                 for (int i = 0; i < NQ; ++i) {
                     int sx = x - g_xi[i][0], sy = y - g_xi[i][1], sz = z - g_xi[i][2];
                     int bb = 0, ghost = 0;
+                    const double *uw = NULL;
                     if (sx < 0 || sx >= nx) {
                         if (s->p.bc_x == 1) bb = 1; else sx = (sx + nx) % nx;
                     }
@@ -488,15 +497,18 @@ static void stream_all(orc_sim *s) {
                         if (s->p.bc_y == 1) bb = 1; else sy = (sy + ny) % ny;
                     }
                     if (sz < 0) {
-                        if (s->p.bc_bottom == 1) bb = 1; else sz = (sz + nz) % nz;
+                        if (s->p.bc_bottom == 1 || s->p.bc_bottom == 3) bb = 1; else sz = (sz + nz) % nz;
+                        if (s->p.bc_bottom == 3) uw = s->p.uw_bottom;
                     } else if (sz >= nz) {
-                        if (s->p.bc_top == 1) bb = 1;
+                        if (s->p.bc_top == 1 || s->p.bc_top == 3) bb = 1;
                         else if (s->p.bc_top == 2) ghost = 1;
                         else sz = sz % nz;
+                        if (s->p.bc_top == 3) uw = s->p.uw_top;
                     }
                     double val;
                     if (bb) {
                         val = s->fpost[c * NQ + (NQ - 1 - i)];
+                        if (uw) val += 6.0 * g_w[i] * (g_xi[i][0] * uw[0] + g_xi[i][1] * uw[1] + g_xi[i][2] * uw[2]);
                     } else if (ghost) {
                         double f0[NQ];
                         orc_feq(1.0, s->utop + 3 * ((int64_t)sy * nx + sx), f0);
@@ -750,7 +762,7 @@ static void advance_particle(orc_sim *s) {
     for (int a = 0; a < 3; ++a) ge[a] = (s->p.gravity == 1 ? 1.0 : 1.0 - 1.0 / s->p.kappa) * s->p.g[a];
     for (int a = 0; a < 3; ++a) {
         double acc = ge[a] + s->F[a] / m;
-        s->v[a] += acc;
+        s->v[a] = s->p.fixed_position ? 0.0 : s->v[a] + acc;
         s->r[a] += s->v[a];
     }
     double src[3], sb[3], wb[3];

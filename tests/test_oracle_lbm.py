@@ -299,3 +299,24 @@ def test_sponge_raises_viscosity_towards_the_top():
         q.init_fields(np.ones((nz, ny, nx)), u)
         q.fluid_step(10)
     assert np.array_equal(s1.velocity(), s2.velocity())
+
+
+@pytest.mark.parametrize("u_bottom,u_top", [((0.0, 0.0, 0.0), (0.02, 0.0, 0.0)), ((0.0, -0.015, 0.0), (0.0, 0.015, 0.0))])
+def test_moving_walls_couette_profile_and_shear_stress(u_bottom, u_top):
+    # steady plane Couette flow between halfway-bounce-back walls at z = -1/2
+    # and z = H - 1/2 moving in their planes: u(z) = u_b + (u_t - u_b)(z + 1/2)/H
+    # (exact for the linear profile), and the shear stress nu (u_t - u_b)/H
+    nz, tau = 16, 0.8
+    s = O.Sim(4, 4, nz, tau, bc_bottom=3, bc_top=3, uw_bottom=u_bottom, uw_top=u_top)
+    s.init_fields()
+    s.fluid_step(10000)  # slowest mode decays as exp(-nu (pi / H)^2 t): e^-38
+    u = s.velocity()
+    ub, ut = np.array(u_bottom), np.array(u_top)
+    z = np.arange(nz)
+    ex = ub[None, :] + (ut - ub)[None, :] * ((z + 0.5) / nz)[:, None]
+    scale = np.abs(ut - ub).max()
+    assert np.abs(u - ex[:, None, None, :]).max() < 1e-10 * scale
+    nu = (tau - 0.5) / 3.0
+    sig = s.stress().reshape(nz, 4, 4, 3, 3)
+    a = int(np.argmax(np.abs(ut - ub)))  # the sheared component
+    assert np.abs(sig[:, :, :, a, 2] - nu * (ut - ub)[a] / nz).max() < 1e-10 * nu * scale / nz

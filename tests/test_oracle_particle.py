@@ -168,3 +168,24 @@ def test_pressure_force_of_a_linear_pressure_field():
     s2.init_fields(np.full((20, 20, 20), 1.003), np.zeros((20, 20, 20, 3)))
     s2.load_particle(V, T, r0=(9.7, 10.2, 9.9))
     assert np.abs(s2.state()["Fp"]).max() < 1e-3 * 0.001 * st8["area"]
+
+
+def test_fixed_position_holds_the_centre_and_leaves_rotation_free():
+    # a sphere under gravity with its centre held: v stays 0 and r does not
+    # move; a torque (shear flow from two moving walls) still spins it up
+    V, T = I.icosphere(3, 3.0)
+    n = 16
+    s = O.Sim(n, n, n, tau=0.8, kappa=2.0, g=(0, 0, -1e-4), bc_bottom=3, bc_top=3, fixed_position=1,
+              uw_bottom=(-0.01, 0, 0), uw_top=(0.01, 0, 0))
+    z = np.arange(n) + 0.5
+    u = np.zeros((n, n, n, 3))
+    u[..., 0] = (-0.01 + 0.02 * z / n)[:, None, None]
+    s.init_fields(None, u)
+    r0 = (8.2, 7.9, 8.1)
+    s.load_particle(V, T, r0=r0)
+    s.step(30)
+    st = s.state()
+    assert np.array_equal(st["v"], np.zeros(3))
+    assert np.abs(st["r"] - np.array(r0)).max() < 1e-12
+    # du_x/dz > 0: the vorticity and the spin are along +y
+    assert st["w"][1] > 0.0 and abs(st["w"][1]) > 10 * max(abs(st["w"][0]), abs(st["w"][2]))
