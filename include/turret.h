@@ -59,12 +59,14 @@ typedef enum { TURRET_D3Q27 = 27 } turret_lattice;
  * q_i / w_i (round to nearest even).  Arithmetic is FP32 in every case.     */
 typedef enum { TURRET_F32 = 0, TURRET_F16 = 1, TURRET_BF16 = 2 } turret_storage;
 
-enum { TURRET_BC_PERIODIC = 0, TURRET_BC_NOSLIP = 1, TURRET_BC_PRESSURE = 2 };
+enum { TURRET_BC_PERIODIC = 0, TURRET_BC_NOSLIP = 1, TURRET_BC_PRESSURE = 2, TURRET_BC_MOVING = 3 };
 
 /* Simulation window (Sec. 2.5, Fig. 1).  bc_x, bc_y: periodic or no-slip
- * (halfway bounce-back).  bc_bottom: periodic or no-slip.  bc_top: periodic,
- * no-slip or constant pressure (ghost plane at rest density with the velocity
- * of the top plane).  sponge_cells: planes below the top over which tau rises
+ * (halfway bounce-back).  bc_bottom: periodic, no-slip or moving wall.
+ * bc_top: periodic, no-slip, constant pressure (ghost plane at rest density
+ * with the velocity of the top plane) or moving wall.  A moving wall is a
+ * no-slip wall sliding in its plane with the velocity set by
+ * lbm_set_wall_velocity (shear flows; not with slide = 1).  sponge_cells: planes below the top over which tau rises
  * linearly to 1 on the top plane.  slide = 1: the window follows the particle
  * vertically as a ring buffer (replaces the re-injection copy of Sec. 2.5);
  * the particle centre is kept within one cell of z = anchor_frac * nz.      */
@@ -88,6 +90,8 @@ typedef struct {
  *   ibm_cycles: number n of IBM cycles (Sec. 2.2: n = 4).
  *   no_graph 1: launch every kernel of a step directly instead of replaying a
  *               captured CUDA graph (same results; for debugging).
+ *   fixed_position 1: the particle's centre is held (v = 0) while its
+ *               rotation stays free (a sphere spun up by a shear flow).
  *   stochastic_rounding 1 (BF16 storage only): the collide+stream stores
  *               round each stored value up or down with probability equal to
  *               its distance from the other neighbour (unbiased rounding),
@@ -101,7 +105,7 @@ typedef struct {
     int32_t ibm_cycles;
     int32_t no_graph;
     int32_t stochastic_rounding;
-    int32_t pad0;
+    int32_t fixed_position;
 } turret_flags;
 
 /* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates
@@ -140,6 +144,13 @@ TURRET_API turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
 
 /* Replaces the reading flags (before ibm_load_surface). */
 TURRET_API turret_status lbm_set_flags(turret_ctx *c, const turret_flags *flags);
+
+/* Velocities (3 doubles each, the normal component must be 0) of the bottom
+ * and top walls of bc TURRET_BC_MOVING.  The halfway bounce-back of a moving
+ * wall adds the momentum it imparts, f_i(x) = f*_{opp i}(x) + 2 w_i (xi_i .
+ * u_w) / c_s^2 (reference density 1), for every population whose source lies
+ * beyond that face.  EINVAL for a normal component or a speed above 0.3.    */
+TURRET_API turret_status lbm_set_wall_velocity(turret_ctx *c, const double u_bottom[3], const double u_top[3]);
 
 /* Sets the state to the equilibrium of the given host fields, as the
  * post-collision populations at t = -1: rho (nz*ny*nx doubles, NULL = 1) and

@@ -67,7 +67,8 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
         if (advance) {
             // ---- 6DOF, Sec. 2.3 (dt = 1, rho_f = 1, m = kappa V) ------------------
             if (lane < 3) {
-                S.v[lane] += bc.g_eff[lane] + s_F[lane] * bc.inv_mass;  // v(t+1/2)
+                // v(t+1/2), or 0 for a held centre
+                S.v[lane] = bc.fixed ? 0.0 : S.v[lane] + bc.g_eff[lane] + s_F[lane] * bc.inv_mass;
                 S.r[lane] += S.v[lane];                                 // r(t+1)
                 if (bc.rot_form == 1) {
                     s_src[lane] = s_T[lane];
@@ -159,7 +160,7 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
         if (pred) {
             if (lane < 3) {
                 s_src[lane] = st->pr.That[lane];
-                s_F[lane] = S.v[lane] + 0.5 * (bc.g_eff[lane] + st->pr.Fhat[lane] * bc.inv_mass);
+                s_F[lane] = bc.fixed ? 0.0 : S.v[lane] + 0.5 * (bc.g_eff[lane] + st->pr.Fhat[lane] * bc.inv_mass);
             }
             __syncwarp();
             if (lane < 3) {

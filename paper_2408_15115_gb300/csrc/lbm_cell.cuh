@@ -102,21 +102,33 @@ __device__ __forceinline__ float ghost_dev(int i, float ux, float uy, float uz) 
 // (halfway), the pressure top reads the ghost equilibrium, periodic faces wrap.
 // A source on the plane that just entered the sliding window (reseed >= 0)
 // holds stale data and reads as the rest equilibrium (deviation 0).
+// The momentum a moving wall imparts to a population it bounces back,
+// 2 w_i (xi_i . u_w) / c_s^2, in the storage domain: 6 W_i (xi . u_w) for the
+// scaled deviations, 6 K (xi . u_w) for the scaled-by-weight forms.
+template <int ST>
+__device__ __forceinline__ float wall_term(int i, const float uw[3]) {
+    const float xu = (float)(i % 3 - 1) * uw[0] + (float)((i / 3) % 3 - 1) * uw[1] + (float)(i / 9 - 1) * uw[2];
+    return 6.0f * (Codec<ST>::scaled ? Codec<ST>::K : Wq(i)) * xu;
+}
+
 template <int ST>
 __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::T *__restrict__ f, int x, int y,
                                        int zl, int ring, int reseed, const float *__restrict__ utop, float q[27]) {
-    int sx[3], sy[3], szp[3], bxf[3], byf[3], bzf[3];
+    int sx[3], sy[3], szp[3], bxf[3], byf[3], bzf[3], mvf[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         bxf[e] = src_axis(x, e, g.nx, g.bc_x, sx[e]);
         byf[e] = src_axis(y, e, g.ny, g.bc_y, sy[e]);
         int zs = zl - (e - 1);
         bzf[e] = 0;
+        mvf[e] = 0;  // 1: the source lies beyond the moving bottom wall, 2: the moving top wall
         if (zs < 0) {
             if (g.bc_bottom == BC_PERIODIC) zs += g.nz; else bzf[e] = 1;
+            if (g.bc_bottom == BC_MOVING) mvf[e] = 1;
         } else if (zs >= g.nz) {
             if (g.bc_top == BC_PERIODIC) zs -= g.nz;
             else bzf[e] = (g.bc_top == BC_PRESSURE) ? 2 : 1;
+            if (g.bc_top == BC_MOVING) mvf[e] = 2;
         }
         szp[e] = bzf[e] ? 0 : zphys(zs, ring, g.nz);
         if (bzf[e] == 0 && szp[e] == reseed) bzf[e] = 3;
@@ -156,6 +168,7 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
                 // value is this one's in every storage domain)
                 if (bxf[ex] == 1 || byf[ey] == 1 || bzf[ez] == 1) {
                     q[i] = own_rest ? 0.0f : Codec<ST>::load(f + (26 - i) * ncell + own);
+                    if (mvf[ez]) q[i] += wall_term<ST>(i, mvf[ez] == 1 ? g.uw_bottom : g.uw_top);
                 } else if (bzf[ez] == 3) {
                     q[i] = 0.0f;
                 } else if (bzf[ez] == 2) {

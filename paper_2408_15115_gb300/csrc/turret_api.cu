@@ -72,7 +72,10 @@ struct Carver {
 static bool valid_window(const turret_window *w) {
     if (!w || w->nx < 1 || w->ny < 1 || w->nz < 1) return false;
     if (w->bc_x < 0 || w->bc_x > 1 || w->bc_y < 0 || w->bc_y > 1) return false;
-    if (w->bc_bottom < 0 || w->bc_bottom > 1 || w->bc_top < 0 || w->bc_top > 2) return false;
+    if (w->bc_bottom < 0 || w->bc_bottom > 3 || w->bc_bottom == TURRET_BC_PRESSURE || w->bc_top < 0 ||
+        w->bc_top > 3)
+        return false;
+    if (w->slide && (w->bc_bottom == TURRET_BC_MOVING || w->bc_top == TURRET_BC_MOVING)) return false;
     if ((w->bc_bottom == TURRET_BC_PERIODIC) != (w->bc_top == TURRET_BC_PERIODIC)) return false;
     if (w->sponge_cells < 0 || w->sponge_cells > w->nz) return false;
     if (w->slide && (w->bc_bottom == TURRET_BC_PERIODIC)) return false;
@@ -174,6 +177,7 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     G.tau0 = (float)tau;
     G.force_scheme = 0;
     G.sround = 0;
+    for (int a = 0; a < 3; ++a) G.uw_bottom[a] = G.uw_top[a] = 0.0f;
     Carver cv{(char *)ws, 0};
     float *tau_z = nullptr;
     carve_fluid(cv, win, c->storage, c->f, c->utop, &c->dstate, &tau_z);
@@ -248,12 +252,26 @@ extern "C" turret_status lbm_set_flags(turret_ctx *c, const turret_flags *fl) {
     if (!c || !fl) return fail(c, TURRET_EINVAL, "NULL argument");
     if (fl->force_scheme < 0 || fl->force_scheme > 1 || fl->rot_form < 0 || fl->rot_form > 1 || fl->gravity < 0 ||
         fl->gravity > 1 || fl->ibm_cycles < 1 || fl->ibm_cycles > 64 || fl->stochastic_rounding < 0 ||
-        fl->stochastic_rounding > 1)
+        fl->stochastic_rounding > 1 || fl->fixed_position < 0 || fl->fixed_position > 1)
         return fail(c, TURRET_EINVAL, "invalid flags");
     if (c->has_particle) return fail(c, TURRET_ESTATE, "flags must be set before ibm_load_surface");
     c->flags = *fl;
     c->geom.force_scheme = fl->force_scheme;
     c->geom.sround = (c->storage == ST_BF16 && fl->stochastic_rounding) ? 1 : 0;
+    drop_graphs(c);
+    return TURRET_OK;
+}
+
+extern "C" turret_status lbm_set_wall_velocity(turret_ctx *c, const double u_bottom[3], const double u_top[3]) {
+    if (!c || !u_bottom || !u_top) return fail(c, TURRET_EINVAL, "NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(u_bottom[a]) || !isfinite(u_top[a]) || fabs(u_bottom[a]) > 0.3 || fabs(u_top[a]) > 0.3)
+            return fail(c, TURRET_EINVAL, "wall speed must be finite and below 0.3");
+    if (u_bottom[2] != 0.0 || u_top[2] != 0.0) return fail(c, TURRET_EINVAL, "walls move in their plane only");
+    for (int a = 0; a < 3; ++a) {
+        c->geom.uw_bottom[a] = (float)u_bottom[a];
+        c->geom.uw_top[a] = (float)u_top[a];
+    }
     drop_graphs(c);
     return TURRET_OK;
 }
@@ -658,6 +676,7 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     for (int a = 0; a < 3; ++a) B.g_eff[a] = (c->flags.gravity == 1 ? 1.0 : 1.0 - 1.0 / c->kappa) * c->g[a];
     B.anchor_z = c->win.anchor_frac * c->win.nz;
     B.rot_form = c->flags.rot_form;
+    B.fixed = c->flags.fixed_position;
     B.renorm = c->flags.renorm_orientation;
     B.slide = c->win.slide;
     B.nm = L.nm;

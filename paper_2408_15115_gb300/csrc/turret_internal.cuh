@@ -21,7 +21,7 @@
 
 namespace turret {
 
-enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_PRESSURE = 2 };
+enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_PRESSURE = 2, BC_MOVING = 3 };
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 enum { STAT_OK = 0, STAT_DIVERGED = 5, STAT_DOMAIN = 7, STAT_OVERFLOW = 8 };
 
@@ -99,6 +99,7 @@ struct Geom {
     float tau0;
     int force_scheme;
     int sround;            // 1: BF16 stores round stochastically (counter-based hash)
+    float uw_bottom[3], uw_top[3];  // velocities of moving walls (BC_MOVING)
     const float *tau_z;    // [nz] relaxation time per logical plane (sponge included)
     const float *omega_z;  // [nz] 1 / tau per logical plane
 };
@@ -116,6 +117,7 @@ struct BodyConst {
     double g_eff[3];
     double anchor_z;   // window z the centre is kept near
     int rot_form, renorm, slide;
+    int fixed;         // 1: the centre is held (v = 0), rotation free
     int nm;            // markers
     int rc;            // ceil of the bounding radius of the markers about C_m
     float rmin, rmax;  // smallest and largest marker distance from C_m

@@ -29,7 +29,7 @@ class Window(C.Structure):
 class Flags(C.Structure):
     _fields_ = [("force_scheme", C.c_int32), ("rot_form", C.c_int32), ("gravity", C.c_int32),
                 ("renorm_orientation", C.c_int32), ("ibm_cycles", C.c_int32), ("no_graph", C.c_int32),
-                ("stochastic_rounding", C.c_int32), ("pad0", C.c_int32)]
+                ("stochastic_rounding", C.c_int32), ("fixed_position", C.c_int32)]
 
 
 class ParticleState(C.Structure):
@@ -77,6 +77,8 @@ def lib():
                                vp, C.c_size_t, vp]
         L.lbm_set_flags.restype = C.c_int
         L.lbm_set_flags.argtypes = [vp, C.POINTER(Flags)]
+        L.lbm_set_wall_velocity.restype = C.c_int
+        L.lbm_set_wall_velocity.argtypes = [vp, _dp, _dp]
         L.lbm_set_fields.restype = C.c_int
         L.lbm_set_fields.argtypes = [vp, _dp, _dp]
         L.ibm_workspace_bytes.restype = C.c_size_t
@@ -223,6 +225,12 @@ class Turret:
     def _check(self, rc):
         if rc != 0:
             raise TurretError(rc, self._L.turret_last_error(self.ctx).decode())
+
+    def set_wall_velocity(self, u_bottom=(0.0, 0.0, 0.0), u_top=(0.0, 0.0, 0.0)):
+        """Velocities of moving bottom / top walls (window bc 3), in their plane."""
+        ub = (C.c_double * 3)(*u_bottom)
+        ut = (C.c_double * 3)(*u_top)
+        self._check(self._L.lbm_set_wall_velocity(self.ctx, ub, ut))
 
     def set_fields(self, rho=None, u=None):
         rp = _arr(rho).ctypes.data_as(_dp) if rho is not None else None

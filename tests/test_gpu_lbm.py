@@ -93,3 +93,30 @@ def test_full_size_window_one_step():
     s.fluid_step(2)
     u, _ = gpu_velocity(t)
     assert rel_max(u, s.velocity()) < 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", TOL_U_F32), ("f16", 2e-3)])
+def test_moving_walls_100_steps(storage, tol):
+    # shear between a bottom and a top wall moving in their planes (bc 3), on a
+    # seeded random flow: the moving-wall bounce-back against the oracle
+    nz, ny, nx = SHAPE
+    walls = ((-0.02, 0.01, 0.0), (0.03, -0.005, 0.0))
+    t, s = make_pair(nx, ny, nz, 0.03, (0, 0, 3, 3), fields=_fields(SHAPE, 5), walls=walls, storage=storage)
+    t.step(100)
+    s.fluid_step(100)
+    u, _ = gpu_velocity(t)
+    err = rel_max(u, s.velocity())
+    assert err < tol, err
+
+
+def test_moving_walls_reject_bad_velocities():
+    from paper_2408_15115_gb300 import turret as T
+    t = T.Turret(8, 8, 8, 0.1, 1.0, (0, 0, 0), 0, 0, 3, 3)
+    with pytest.raises(T.TurretError):
+        t.set_wall_velocity((0, 0, 0.01), (0, 0, 0))  # normal component
+    with pytest.raises(T.TurretError):
+        t.set_wall_velocity((0.5, 0, 0), (0, 0, 0))  # too fast
+    with pytest.raises(T.TurretError):
+        T.Turret(8, 8, 8, 0.1, 1.0, (0, 0, 0), 0, 0, 3, 2, slide=1, anchor_frac=0.3)  # no sliding window
+    t.close()
+

@@ -115,3 +115,59 @@ def test_stokes_settling_cfg1_drag_and_velocity_vs_oracle():
     a, b = t.state(), s.state()
     assert abs(a["F"][2] - b["F"][2]) / abs(b["F"][2]) < 5e-3
     assert abs(a["v"][2] - b["v"][2]) / abs(b["v"][2]) < 5e-3
+
+
+def test_held_sphere_in_shear_flow_vs_oracle():
+    # a sphere with its centre held in the shear between two moving walls:
+    # force, torque and the spin-up of its rotation against the oracle
+    n = 24
+    V, T = I.sphere(4, 6.0)
+    z = np.arange(n) + 0.5
+    u = np.zeros((n, n, n, 3))
+    u[..., 0] = (-0.01 + 0.02 * z / n)[:, None, None]
+    t, s = make_pair(n, n, n, 0.1, (0, 0, 3, 3), kappa=2.0, g=(0, 0, -1e-5), flags={"fixed_position": 1},
+                     fields=(None, u), walls=((-0.01, 0, 0), (0.01, 0, 0)),
+                     particle=(V, T, (11.6, 11.3, 11.8), (0, 0, 0), (0, 0, 0)))
+    t.step(60)
+    s.step(60)
+    a, b = _compare_state(t, s)
+    assert np.array_equal(a["v"], np.zeros(3)) and np.abs(a["r"] - np.array([11.6, 11.3, 11.8])).max() < 1e-12
+    assert np.abs(a["w"] - b["w"]).max() < 1e-4 * np.abs(b["w"]).max()
+    assert np.abs(a["T"] - b["T"]).max() < 1e-4 * np.abs(b["T"]).max()
+
+
+def test_sphere_spin_up_in_shear_flow_follows_feuillebois_lasek():
+    # the free-rotation validation: a sphere (d = 8, 252 markers) held at the
+    # centre of a 48^3 box whose bottom and top walls move at -U and +U in x
+    # (shear rate G = 2U/H, Re_G = 4 G r^2 / nu ~ 0.26), released from rest in
+    # the fully developed shear: its angular velocity about y rises to the
+    # fluid's G/2 along the unsteady-Stokes response of Eq. B.2 (a sudden
+    # torque on a sphere at rest, normalised by its terminal value)
+    from paper_2408_15115_gb300 import analysis as A
+    from paper_2408_15115_gb300 import turret as Tu
+    n, U, nu, kappa = 48, 0.01, 0.1, 2.0
+    V, T = I.sphere(5, 8.0)
+    t = Tu.Turret(n, n, n, nu, kappa, (0, 0, 0), 0, 0, 3, 3, flags={"fixed_position": 1})
+    t.set_wall_velocity((-U, 0, 0), (U, 0, 0))
+    z = np.arange(n) + 0.5
+    u = np.zeros((n, n, n, 3))
+    u[..., 0] = (-U + 2 * U * z / n)[:, None, None]
+    t.set_fields(None, u)
+    t.load_surface(V, T, (n / 2 - 0.5, n / 2 - 0.5, n / 2 - 0.5))
+    wf = U / n  # G / 2
+    ts, w = [], []
+    for k in range(150):
+        t.step(20)
+        st = t.state()
+        ts.append(20 * (k + 1))
+        w.append(st["w"])
+    w = np.array(w) / wf
+    r = (3.0 * st["volume"] / (4.0 * np.pi)) ** (1.0 / 3.0)
+    model = A.fl78_rotation_exact(r, nu, kappa, 1.0, np.array(ts)) * 8.0 * np.pi * nu * r ** 3
+    t.close()
+    print("w_y / (G/2) at t = 20, 100, 3000: %.4f %.4f %.4f; model %.4f %.4f %.4f" %
+          (w[0, 1], w[4, 1], w[-1, 1], model[0], model[4], model[-1]))
+    assert abs(w[-1, 1] - 1.0) < 1e-2            # terminal: the fluid's rotation rate G/2
+    assert np.abs(w[:, 1] - model).max() < 0.05  # the spin-up follows Eq. B.2
+    assert np.abs(w[:, [0, 2]]).max() < 1e-3     # about y only
+
