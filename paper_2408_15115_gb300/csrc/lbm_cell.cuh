@@ -948,8 +948,7 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
                     reach = reach || in;
                 }
                 const int k = chunk + tid;
-                const int b = k < nm ? __ldg(mbase + k) : -1;  // loaded beside the segment test
-                pb[u] = reach ? b : -1;
+                pb[u] = (reach && k < nm) ? __ldg(mbase + k) : -1;  // culled chunks load nothing
             }
             unsigned bal[CU][2];
             bool hit[CU][2];
