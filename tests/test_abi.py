@@ -66,3 +66,23 @@ def test_host_side_validation_without_gpu(libpath):
     assert rc == 1 and b"tau" in lib.turret_last_error(None)
     rc = lib.lbm_init(ctypes.byref(ctx), ctypes.byref(w), 19, 0.1, 1.0, g, 0, None, 0, None)
     assert rc == 1
+
+
+def test_window_limits_and_degenerate_windows(libpath):
+    # 32-bit population offsets: 27 nx ny nz <= 2^31 cells is the largest window
+    lib = T.lib()
+    size = lambda *a: lib.lbm_workspace_bytes(ctypes.byref(T.Window(*a)), 0)
+    n_max = (1 << 31) // 27  # 79,536,431 cells
+    assert size(512, 512, n_max // (512 * 512), 0, 0, 1, 2, 0, 0, 0, 0.25) > 0   # 512 x 512 x 303
+    assert size(512, 512, n_max // (512 * 512) + 1, 0, 0, 1, 2, 0, 0, 0, 0.25) == 0
+    assert size(1, 1, 1, 0, 0, 0, 0, 0, 0, 0, 0.25) > 0          # a single periodic cell
+    for bad in ((0, 16, 16, 0, 0, 1, 2, 0, 0, 0, 0.25),         # empty
+                (16, 16, 70000, 0, 0, 1, 2, 0, 0, 0, 0.25),     # more planes than a launch allows
+                (16, 16, 16, 0, 0, 2, 2, 0, 0, 0, 0.25),        # pressure at the bottom
+                (16, 16, 16, 0, 0, 1, 2, 17, 0, 0, 0.25),       # sponge deeper than the window
+                (16, 16, 16, 0, 0, 3, 3, 0, 1, 0, 0.25),        # moving walls in a sliding window
+                (16, 16, 16, 0, 0, 1, 2, 0, 1, 0, 1.0),         # anchor outside (0, 1)
+                (16, 16, 16, 2, 0, 1, 2, 0, 0, 0, 0.25)):       # unknown lateral code
+        assert size(*bad) == 0, bad
+    w = T.Window(16, 16, 16, 0, 0, 0, 0, 0, 0, 0, 0.25)
+    assert lib.lbm_workspace_bytes(ctypes.byref(w), 3) == 0     # unknown storage
