@@ -370,6 +370,10 @@ typedef struct {
     double kappa, g[3];
     int fixed_position;       /* 1: the centre of mass is held (v = 0), rotation free */
     double uw_bottom[3], uw_top[3];  /* velocities of moving walls (bc 3)      */
+    /* re-injection copy of Sec. 2.5 (slide = 0; trigger 0 = off): once the
+     * centre's window z drops below `trigger`, the planes [zf - below, zf +
+     * above) around it (zf = floor of that z) move up by target - zf */
+    int reinject_trigger, reinject_target, reinject_below, reinject_above;
 } orc_params;
 
 typedef struct {
@@ -826,6 +830,32 @@ static void slide_window(orc_sim *s) {
     }
 }
 
+/* Re-injection copy, Sec. 2.5, as printed in spirit (READING: the block
+ * extents and the jump are parameters; the paper gives ~60% of h, elongated
+ * above the particle): when the centre's window z = r_z - origin_z has fallen
+ * below the trigger plane, the post-collision planes [zf - below, zf + above)
+ * (zf = floor z, clipped to the window) are copied up by dz = target - zf
+ * (planes that would leave the top are dropped) and the window origin moves
+ * down by dz, so the particle keeps its global position and lands at the
+ * target plane.  Fluid outside the copied block is left as it was.  Done on
+ * f*(t) after the particle update, like the ring slide.                     */
+static void reinject(orc_sim *s) {
+    if (s->p.slide || s->p.reinject_trigger <= 0) return;
+    const int nz = s->p.nz;
+    const double zc = s->r[2] - (double)s->origin[2];
+    if (!(zc < (double)s->p.reinject_trigger)) return;
+    const int zf = (int)floor(zc);
+    const int dz = s->p.reinject_target - zf;
+    if (dz <= 0) return;
+    int z0 = zf - s->p.reinject_below, z1 = zf + s->p.reinject_above;
+    if (z0 < 0) z0 = 0;
+    if (z1 > nz - dz) z1 = nz - dz;
+    const int64_t plane = (int64_t)s->p.nx * s->p.ny * NQ;
+    if (z1 > z0)
+        memmove(s->fpost + plane * (z0 + dz), s->fpost + plane * z0, sizeof(double) * (size_t)(plane * (z1 - z0)));
+    s->origin[2] -= dz;
+}
+
 /* Particle definition.  verts: body mesh (any origin; re-centred on its centre
  * of mass, body frame = lab frame at t = 0), tris: outward CCW triangles.
  * r0: centre of mass in window coordinates at t = 0; v0, w0: v(-1/2),
@@ -871,6 +901,7 @@ int orc_step(orc_sim *s, int n) {
         collide_all(s);                                /* (1) collide with h_imm(t) */
         if (s->has_particle) advance_particle(s);      /* (2) particle(t+1) from F(t), T(t) */
         if (s->has_particle) slide_window(s);
+        if (s->has_particle) reinject(s);
         stream_all(s);                                 /* (1) stream -> f(t+1) */
         fields_from_f(s);                              /* (3) u*, sigma at t+1 */
         s->step++;
