@@ -385,6 +385,19 @@ TURRET_API const char *mlp_last_error(const turret_mlp *m);
 TURRET_API turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const turret_mlp *net, int32_t options,
                                               double slip_eps, double resid_theta);
 
+/* The re-injection copy of Sec. 2.5 instead of a sliding window (windows
+ * with slide = 0; trigger 0 switches it off): once the particle centre's
+ * window z falls below the plane `trigger`, the post-collision planes
+ * [zf - below, zf + above) around it (zf = floor of that z, clipped to the
+ * window; planes that would leave the top are dropped) are copied up by
+ * target - zf and the window origin moves down by as much, so the particle
+ * keeps its global position and lands at plane `target`; the rest of the
+ * fluid is left as it was.  Steps then run without the far/near split (one
+ * collide+stream launch over the window).  EINVAL unless
+ * 0 < trigger < target < nz and below + above <= nz.                       */
+TURRET_API turret_status turret_set_reinjection(turret_ctx *c, int32_t trigger, int32_t target, int32_t below,
+                                                int32_t above);
+
 /* Trajectory log: after the force of each time level j is known, record
  * (n mod capacity), n the count of records written so far, of the caller's
  * device array records [capacity][TURRET_LOG_REC] doubles receives d(j) [9]

@@ -162,6 +162,7 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     c->win = *win;
     memset(&c->flags, 0, sizeof c->flags);
     c->flags.ibm_cycles = 4;
+    c->reinject = Reinject{0, 0, 0, 0};
     c->storage = (int)st;
     c->nu = nu;
     c->tau0 = tau;
@@ -530,6 +531,20 @@ static cudaError_t enqueue_step(turret_ctx *c, int p) {
     if (!c->has_particle)
         return launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
                                      1 - p, nullptr, c->box, false, REGION_ALL, c->stream);
+    if (c->reinject.trigger > 0) {
+        // re-injection copy: collide+stream over the whole window, the particle
+        // and marker update, the copy of f*(t) (the buffer of f*(t-1) stages
+        // it) with the window shift, then the chain
+        if (c->body.predictor != 0)
+            CE(launch_predict(c->body.predictor == 2 ? mlp_device_view(c->net) : nullptr, c->dstate, p,
+                              c->body.predictor, c->stream));
+        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
+                                 c->ba.h, c->box, true, REGION_ALL, c->stream));
+        CE(launch_particle_markers(G, c->body, c->box, c->dstate, p, 1, c->mk, c->stream));
+        CE(launch_reinject(G, c->storage, c->f[1 - p], c->f[p], c->dstate, 1 - p, c->reinject, c->stream));
+        CE(cudaEventRecord(c->ev_pred, c->stream));
+        return enqueue_coupling(c, c->f[1 - p], c->utop[p], p, 1, c->stream, c->ev_pred);
+    }
     cudaStream_t chain = c->split ? c->side : c->stream;
     const bool predict = c->body.predictor != 0;
     const MlpDev *net = (c->body.predictor == 2) ? mlp_device_view(c->net) : nullptr;
@@ -791,7 +806,7 @@ extern "C" turret_status step(turret_ctx *c, int64_t n) {
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
     const bool graphs = (c->stream != nullptr) && !c->flags.no_graph;
     int64_t k = 0;
-    if (graphs && c->has_particle && c->split) {
+    if (graphs && c->has_particle && c->split && c->reinject.trigger == 0) {
         // whole groups of PIPE_STEPS steps as one pipelined graph
         for (; n - k >= PIPE_STEPS; k += PIPE_STEPS) {
             const int p = (int)(c->step & 1);
@@ -836,6 +851,21 @@ extern "C" turret_status turret_set_predictor(turret_ctx *c, int32_t mode, const
     c->body.predictor = mode;
     c->body.slip_eps = c->pred_eps;
     c->body.resid_theta = resid_theta;
+    drop_graphs(c);
+    return TURRET_OK;
+}
+
+extern "C" turret_status turret_set_reinjection(turret_ctx *c, int32_t trigger, int32_t target, int32_t below,
+                                                int32_t above) {
+    if (!c) return fail(c, TURRET_EINVAL, "NULL context");
+    if (trigger != 0) {
+        if (c->win.slide || c->win.bc_bottom == TURRET_BC_PERIODIC)
+            return fail(c, TURRET_EINVAL, "re-injection needs a window without slide and a closed bottom");
+        if (!(trigger > 0 && trigger < target && target < c->win.nz) || below < 0 || above < 0 ||
+            below + above > c->win.nz)
+            return fail(c, TURRET_EINVAL, "need 0 < trigger < target < nz and a block inside the window");
+    }
+    c->reinject = Reinject{trigger, target, below, above};
     drop_graphs(c);
     return TURRET_OK;
 }

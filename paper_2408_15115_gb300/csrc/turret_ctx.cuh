@@ -47,6 +47,8 @@ struct turret_ctx {
     const turret_mlp *net;
     double *log;
     long long log_cap;
+    // re-injection copy (Sec. 2.5) instead of the ring window; trigger 0 = off
+    turret::Reinject reinject;
     // stepping
     long long step;
     cudaGraphExec_t graph[2];

@@ -265,6 +265,15 @@ constexpr int NEAR_MARGIN = 2;
 cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                   float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
                                   const BoxGeom &box, bool has_box, int region, cudaStream_t s);
+// Re-injection copy of Sec. 2.5 (windows without slide): once the centre's
+// window z in slot `slot` is below trigger, the post-collision planes
+// [zf - below, zf + above) (zf its floor, clipped) move up by target - zf
+// (staged through the other population buffer) and the slot's origin down.
+struct Reinject {
+    int trigger, target, below, above;
+};
+cudaError_t launch_reinject(const Geom &g, int storage, void *buf, void *stage, DevState *st, int slot,
+                            const Reinject &rj, cudaStream_t s);
 cudaError_t launch_init_equilibrium(const Geom &g, int storage, void *dst, const double *drho, const double *u,
                                     float *utop, cudaStream_t s);
 cudaError_t launch_macro(const Geom &g, int storage, const void *src, const float *utop_in, const DevState *st,

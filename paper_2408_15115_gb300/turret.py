@@ -142,6 +142,8 @@ def lib():
         L.turret_set_predictor.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_double, C.c_double]
         L.turret_set_log.restype = C.c_int
         L.turret_set_log.argtypes = [vp, vp, C.c_int64]
+        L.turret_set_reinjection.restype = C.c_int
+        L.turret_set_reinjection.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         L.turret_query_predictor.restype = C.c_int
         L.turret_query_predictor.argtypes = [vp, C.POINTER(PredictorStats)]
         L.mlp_build_samples.restype = C.c_int
@@ -308,6 +310,10 @@ class Turret:
         opts = (1 if warm else 0) | (2 if velocity else 0) | (4 if relative else 0)
         self._check(self._L.turret_set_predictor(self.ctx, self.PREDICTORS[mode], net.m if net is not None else None,
                                                  opts, float(slip_eps), float(resid_theta)))
+
+    def set_reinjection(self, trigger, target, below, above):
+        """The re-injection copy of Sec. 2.5 (see turret_set_reinjection); trigger 0 = off."""
+        self._check(self._L.turret_set_reinjection(self.ctx, int(trigger), int(target), int(below), int(above)))
 
     def set_log(self, capacity):
         """Attach a device trajectory log of `capacity` records (0 detaches)."""

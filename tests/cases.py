@@ -25,12 +25,13 @@ def gpu_velocity(t):
 
 
 def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anchor=0.25, storage="f32",
-              flags=None, fields=None, particle=None, walls=None):
+              flags=None, fields=None, particle=None, walls=None, reinject=None):
     """Build a (Turret, oracle Sim) pair with identical configuration.
 
     bc = (bc_x, bc_y, bc_bottom, bc_top); fields = (rho, u) or None;
     particle = (verts, tris, r0, v0, w0) or None; walls = (u_bottom, u_top)
-    for moving walls (bc 3) or None."""
+    for moving walls (bc 3) or None; reinject = (trigger, target, below,
+    above) for the re-injection copy or None."""
     from paper_2408_15115_gb300 import turret as T
     flags = dict(flags or {})
     tau = 3 * nu + 0.5
@@ -41,7 +42,10 @@ def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anc
               gravity=flags.get("gravity", 0), renorm=flags.get("renorm_orientation", 0),
               ibm_cycles=flags.get("ibm_cycles", 4), kappa=kappa, g=g,
               fixed_position=flags.get("fixed_position", 0),
-              uw_bottom=walls[0] if walls else (0, 0, 0), uw_top=walls[1] if walls else (0, 0, 0))
+              uw_bottom=walls[0] if walls else (0, 0, 0), uw_top=walls[1] if walls else (0, 0, 0),
+              reinject=reinject or (0, 0, 0, 0))
+    if reinject is not None:
+        t.set_reinjection(*reinject)
     if walls is not None:
         t.set_wall_velocity(*walls)
     if fields is not None:

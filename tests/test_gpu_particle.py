@@ -171,3 +171,19 @@ def test_sphere_spin_up_in_shear_flow_follows_feuillebois_lasek():
     assert np.abs(w[:, 1] - model).max() < 0.05  # the spin-up follows Eq. B.2
     assert np.abs(w[:, [0, 2]]).max() < 1e-3     # about y only
 
+
+@pytest.mark.parametrize("storage,tol_f,tol_v", [("f32", 1e-4, 1e-5), ("f16", 2e-2, 2e-3)])
+def test_reinjection_copy_vs_oracle(storage, tol_f, tol_v):
+    # the re-injection copy of Sec. 2.5: a falling sphere crosses the trigger
+    # plane and the block of fluid around it is copied up with it; the window
+    # origin, the trajectory and the force against the oracle through the event
+    V, T = I.icosphere(3, 3.0)
+    t, s = make_pair(16, 16, 64, 0.1, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=4, storage=storage,
+                     reinject=(22, 40, 12, 14), particle=(V, T, (7.8, 8.1, 22.5), (0, 0, -0.05), (0, 0, 0)))
+    t.step(60)
+    s.step(60)
+    a, b = _compare_state(t, s, tol_f=tol_f, tol_v=tol_v, r0=np.array([7.8, 8.1, 22.5]))
+    assert a["origin"][2] < 0  # re-injected once: the window moved down
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < (TOL_U_F32 if storage == "f32" else 2e-3)
+
