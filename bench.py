@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100)
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--case", default=None, choices=["mlp_train", "ensemble_steps"],
+                   help="run one small workload for a profiler capture instead of the benchmark")
     p.add_argument("--learned-steps", type=int, default=6000)
     return p.parse_args()
 
@@ -533,8 +535,55 @@ def run_ours(args):
     print(json.dumps(out))
 
 
+def run_case(args):
+    """Small fixed workloads for profiler captures: `mlp_train`, three BF16
+    training steps of the surrogate network at batch 4096; `ensemble_steps`,
+    the 64-run ensemble as one batch with tiles (128, 2, 32), 5 + 20 steps in
+    FP32 then 5 + 20 with storage alternating FP32/FP16."""
+    import numpy as np
+    import torch
+
+    from paper_2408_15115_gb300 import build as B
+    from paper_2408_15115_gb300 import configs
+    from paper_2408_15115_gb300 import inputs as I
+    from paper_2408_15115_gb300 import turret as T
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    out = {"case": args.case}
+    if args.case == "mlp_train":
+        net = T.MLP(I.mlp_init_params(0).astype(np.float32), batch_cap=4096, precision="bf16", device=dev)
+        g = torch.Generator(device="cpu").manual_seed(0)
+        x = torch.randn(4096, 34, generator=g).to(dev)
+        y = torch.randn(4096, 6, generator=g).to(dev)
+        for _ in range(3):
+            net.train_step(x, y, want_loss=False)
+        torch.cuda.synchronize(dev)
+        net.close()
+    else:
+        for storage in ("f32", "alternate"):
+            runs = configs.load_ensemble(configs.ensemble(64, seed=4, storage=storage), device=dev)
+            b = T.Batch(runs, device=dev)
+            b.set_tiles(128, 2, [32] * len(runs))
+            b.step(5)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.step(20)
+            e1.record(b.stream)
+            torch.cuda.synchronize(dev)
+            out[storage + "_ms_per_step"] = e0.elapsed_time(e1) / 20
+            b.close()
+            for t in runs:
+                t.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
