@@ -1,7 +1,7 @@
 // lbm_batch.cu -- collide+stream with a chosen tile (the autotuner's timing
 // kernel) and the batched collide+stream and support-moment launches over
 // the (run, block) table of many independent runs.
-#include "lbm_cell.cuh"
+#include "support_moments.cuh"
 
 namespace turret {
 

@@ -81,19 +81,6 @@ __global__ void __launch_bounds__(128) k_macro(Geom g, const typename Codec<ST>:
     out[3 * g.ncell + c] = M.uz;
 }
 
-template <int ST>
-__global__ void __launch_bounds__(MB_THREADS) k_box_moments_bin(Geom g, const typename Codec<ST>::T *__restrict__ src,
-                                                                const float *__restrict__ utop_in,
-                                                                const DevState *__restrict__ st, int slot, BoxGeom box,
-                                                                BoxArrays ba, int nmom, int nm,
-                                                                const int *__restrict__ mbase,
-                                                                const int *__restrict__ mseg,
-                                                                int *__restrict__ tile_list,
-                                                                int *__restrict__ tile_count, int cap, DevState *stw,
-                                                                float rmin, float rmax) {
-    mb_block<ST>(g, src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax,
-                 blockIdx.x);
-}
 
 // ---------------------------------------------------------------------------
 // Launchers.
@@ -134,68 +121,6 @@ cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, v
     }
 }
 
-// Plan of a re-injection from the body slot: the copied planes [z0, z1) and
-// the jump dz (false: no re-injection this step).  Every thread of the three
-// kernels derives the same plan from the same slot (the origin changes last).
-__device__ __forceinline__ bool reinject_plan(const Geom &g, const BodySlot &S, const Reinject &rj, int &z0, int &z1,
-                                              int &dz) {
-    const double zc = S.r[2] - (double)S.origin[2];
-    if (!(zc < (double)rj.trigger)) return false;
-    const int zf = (int)floor(zc);
-    dz = rj.target - zf;
-    if (dz <= 0) return false;
-    z0 = max(zf - rj.below, 0);
-    z1 = min(zf + rj.above, g.nz - dz);
-    return true;
-}
-
-// pass 0: stage[i][z] = buf[i][z]; pass 1: buf[i][z + dz] = stage[i][z], for
-// z in [z0, z1) and every population and cell of a plane (grid-stride: the
-// launch is small, and nearly free on the steps without a re-injection)
-template <typename T>
-__global__ void k_reinject_copy(Geom g, T *__restrict__ buf, T *__restrict__ stage, const DevState *st, int slot,
-                                Reinject rj, int pass) {
-    int z0, z1, dz;
-    if (!reinject_plan(g, st->s[slot], rj, z0, z1, dz) || z1 <= z0) return;
-    const long long per_pop = (long long)(z1 - z0) * g.plane;
-    const long long total = 27 * per_pop;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long i = k / per_pop, r = k - i * per_pop;
-        const size_t from = (size_t)i * g.ncell + (size_t)z0 * g.plane + r;
-        if (pass == 0) stage[from] = buf[from];
-        else buf[from + (size_t)dz * g.plane] = stage[from];
-    }
-}
-
-__global__ void k_reinject_origin(Geom g, DevState *st, int slot, Reinject rj) {
-    int z0, z1, dz;
-    if (threadIdx.x == 0 && reinject_plan(g, st->s[slot], rj, z0, z1, dz)) {
-        BodySlot &S = st->s[slot];
-        S.origin[2] -= dz;
-        S.Ci[2] += dz;
-        S.box_lo[2] += dz;
-        S.box_lo_w[2] += dz;
-    }
-}
-
-template <typename T>
-static cudaError_t reinject_t(const Geom &g, void *buf, void *stage, DevState *st, int slot, const Reinject &rj,
-                              cudaStream_t s) {
-    if (rj.below + rj.above > 0) {
-        k_reinject_copy<T><<<608, 256, 0, s>>>(g, (T *)buf, (T *)stage, st, slot, rj, 0);
-        k_reinject_copy<T><<<608, 256, 0, s>>>(g, (T *)buf, (T *)stage, st, slot, rj, 1);
-    }
-    k_reinject_origin<<<1, 32, 0, s>>>(g, st, slot, rj);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reinject(const Geom &g, int storage, void *buf, void *stage, DevState *st, int slot,
-                            const Reinject &rj, cudaStream_t s) {
-    return storage == ST_F32 ? reinject_t<float>(g, buf, stage, st, slot, rj, s)
-                             : reinject_t<unsigned short>(g, buf, stage, st, slot, rj, s);
-}
-
 cudaError_t launch_init_equilibrium(const Geom &g, int storage, void *dst, const double *drho, const double *u,
                                     float *utop, cudaStream_t s) {
     const unsigned nb = (unsigned)((g.ncell + 255) / 256);
@@ -217,18 +142,5 @@ cudaError_t launch_macro(const Geom &g, int storage, const void *src, const floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_box_moments_bin(const Geom &g, int storage, const void *src, const float *utop_in,
-                                   const DevState *st, int slot, const BoxGeom &box, BoxArrays ba, int nm,
-                                   const int *mbase, const int *mseg, int *tile_list, int *tile_count, int cap,
-                                   DevState *stw, float rmin, float rmax, cudaStream_t s) {
-    const int nmom = (int)((box.nbox + MB_THREADS - 1) / MB_THREADS);
-    const unsigned nb = (unsigned)(nmom + box.tx * box.ty * box.tz);
-    switch (storage) {
-        case ST_F32: k_box_moments_bin<ST_F32><<<nb, MB_THREADS, 0, s>>>(g, (const float *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
-        case ST_F16: k_box_moments_bin<ST_F16><<<nb, MB_THREADS, 0, s>>>(g, (const __half *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
-        default: k_box_moments_bin<ST_BF16><<<nb, MB_THREADS, 0, s>>>(g, (const __nv_bfloat16 *)src, utop_in, st, slot, box, ba, nmom, nm, mbase, mseg, tile_list, tile_count, cap, stw, rmin, rmax); break;
-    }
-    return cudaGetLastError();
-}
 
 }  // namespace turret
