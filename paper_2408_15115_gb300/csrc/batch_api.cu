@@ -41,6 +41,8 @@ struct turret_batch {
     cudaEvent_t ev_fork, ev_join, ev_red, ev_red_done, ev_done, ev_pred;
     std::vector<cudaEvent_t> ev_ctx;  // one per run: the work already on its context's stream
     RunDesc *d_runs;
+    CollideDesc *d_cdesc;             // the collide+stream part of each descriptor
+    std::vector<CollideDesc> h_cdesc;
     int *d_prefix;                    // T_COUNT tables of n + 1 ints
     std::vector<RunDesc> h_runs;
     std::vector<int> h_prefix;
@@ -70,10 +72,13 @@ static turret_status bfail(turret_batch *b, turret_status s, const std::string &
     } while (0)
 
 static size_t prefix_offset(int n) { return ((size_t)n * sizeof(RunDesc) + 255) & ~(size_t)255; }
+static size_t cdesc_offset(int n) {
+    return (prefix_offset(n) + (size_t)T_COUNT * (n + 1) * sizeof(int) + 255) & ~(size_t)255;
+}
 
 extern "C" size_t turret_batch_workspace_bytes(int32_t n) {
     if (n < 1) return 0;
-    return prefix_offset(n) + (size_t)T_COUNT * (n + 1) * sizeof(int) + 256;
+    return cdesc_offset(n) + (size_t)n * sizeof(CollideDesc) + 256;
 }
 
 // Per-phase block tables from the descriptors and the launch shape.
@@ -112,7 +117,26 @@ static void drop_batch_graphs(turret_batch *b) {
 }
 
 static cudaError_t upload(turret_batch *b) {
+    b->h_cdesc.resize(b->n);
+    for (int r = 0; r < b->n; ++r) {
+        const RunDesc &R = b->h_runs[r];
+        CollideDesc &D = b->h_cdesc[r];
+        memset(&D, 0, sizeof D);
+        D.g = R.g;
+        D.box = R.box;
+        for (int k = 0; k < 2; ++k) {
+            D.f[k] = R.f[k];
+            D.utop[k] = R.utop[k];
+        }
+        D.st = R.st;
+        D.hbox = R.ba.h;
+        D.storage = R.storage;
+        D.split = R.split;
+        D.tx = R.tx;
+    }
     CE(cudaMemcpyAsync(b->d_runs, b->h_runs.data(), b->n * sizeof(RunDesc), cudaMemcpyHostToDevice, b->stream));
+    CE(cudaMemcpyAsync(b->d_cdesc, b->h_cdesc.data(), b->n * sizeof(CollideDesc), cudaMemcpyHostToDevice,
+                       b->stream));
     CE(cudaMemcpyAsync(b->d_prefix, b->h_prefix.data(), b->h_prefix.size() * sizeof(int), cudaMemcpyHostToDevice,
                        b->stream));
     return cudaStreamSynchronize(b->stream);
@@ -163,6 +187,7 @@ extern "C" turret_status turret_batch_init(turret_batch **out, turret_ctx *const
     b->graph_ready[0] = b->graph_ready[1] = false;
     b->d_runs = (RunDesc *)ws;
     b->d_prefix = (int *)((char *)ws + prefix_offset(n));
+    b->d_cdesc = (CollideDesc *)((char *)ws + cdesc_offset(n));
     b->threads = 128;
     b->minb = 2;
     b->cycles = ctxs[0]->flags.ibm_cycles;
@@ -258,8 +283,9 @@ static cudaError_t batch_enqueue(turret_batch *b, int p) {
     if (b->predictor) CE(launch_batch_predict(R, n, p, b->aux));
     CE(launch_batch_particle_markers(R, tab(T_PM), n, p, b->total[T_PM], b->aux));
     CE(cudaEventRecord(b->ev_pred, b->aux));
-    CE(launch_batch_collide(PHASE_BULK, R, tab(T_BULK), n, p, b->total[T_BULK], b->threads, b->minb, b->stream));
-    CE(launch_batch_collide(PHASE_NEAR, R, tab(T_NEAR), n, p, b->total[T_NEAR], b->threads, 1, b->side));
+    CE(launch_batch_collide(PHASE_BULK, b->d_cdesc, tab(T_BULK), n, p, b->total[T_BULK], b->threads, b->minb,
+                            b->stream));
+    CE(launch_batch_collide(PHASE_NEAR, b->d_cdesc, tab(T_NEAR), n, p, b->total[T_NEAR], b->threads, 1, b->side));
     CE(cudaStreamWaitEvent(b->side, b->ev_pred, 0));
     CE(launch_batch_box_moments_bin(R, tab(T_MB), n, p, b->total[T_MB], b->side));
     CE(launch_batch_interp0(R, tab(T_IP), n, b->total[T_IP], b->warm, b->side));

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, MINB) k_collide_tiled(Geom g, const typen
 // split (no blocks for the others); PHASE_NEAR: the near region of runs that
 // split, the whole window (with forcing) of runs that do not.
 template <int PHASE, int ST>
-__device__ __forceinline__ void batch_k1_run(const RunDesc &R, int p, int lb) {
+__device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb) {
     using T = typename Codec<ST>::T;
     const Geom g = R.g;
     const BoxGeom box = R.box;
@@ -40,32 +40,55 @@ __device__ __forceinline__ void batch_k1_run(const RunDesc &R, int p, int lb) {
     int cx, cy, cz;
     if (PHASE == PHASE_BULK) {
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
-        k1_pair<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+        k1_pair<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else if (R.split) {
         tile_coords(lb, R.tx, box.Bx + 2 * NEAR_MARGIN, box.By + 2 * NEAR_MARGIN, 1, cx, cy, cz);
-        k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+        k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else {
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
-        k1_pair<ST, K1_ALLF>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.ba.h, box, cx, cy, cz);
+        k1_pair<ST, K1_ALLF>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     }
+}
+
+// Run r of block b (largest r < nruns with prefix[r] <= b) by one warp: each
+// pass reads 32 table entries at once and narrows the range 32-fold by a
+// ballot, so a table of up to 1024 runs takes two dependent loads.
+__device__ __forceinline__ int find_run_warp(const int *__restrict__ prefix, int nruns, int b, int lane) {
+    int lo = 0, span = nruns;
+    while (span > 32) {
+        const int stride = (span + 31) / 32;
+        const int idx = lo + lane * stride;
+        const bool ok = idx < lo + span && __ldg(prefix + idx) <= b;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);  // entry 0 of the range always qualifies
+        lo += (31 - __clz(m)) * stride;
+        span = min(stride, nruns - lo);
+    }
+    const bool ok = lane < span && __ldg(prefix + lo + lane) <= b;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    return lo + (31 - __clz(m));
 }
 
 // The near phase is a small launch on the critical path (no register cap).
 template <int PHASE, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_batch_collide(const RunDesc *__restrict__ runs,
+__global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *__restrict__ runs,
                                                        const int *__restrict__ prefix, int nruns, int p) {
-    // the run's descriptor is staged in shared memory: its fields are then
-    // operands read on use rather than registers held through the cell
-    __shared__ RunDesc R;
-    __shared__ int s_lb;
+    // the run's descriptor is staged in shared memory (one load per thread):
+    // its fields are then operands read on use rather than registers held
+    // through the cell
+    constexpr int NW = (int)(sizeof(CollideDesc) / 4);
+    static_assert(sizeof(CollideDesc) % 4 == 0 && NW <= 128, "descriptor staged by one load per thread");
+    __shared__ CollideDesc R;
+    __shared__ int s_r, s_lb;
     if (threadIdx.x < 32) {
-        int lb;
-        const int r = find_run(prefix, nruns, blockIdx.x, lb);
-        const int *gsrc = reinterpret_cast<const int *>(runs + r);
-        int *sdst = reinterpret_cast<int *>(&R);
-        for (int q = threadIdx.x; q < (int)(sizeof(RunDesc) / 4); q += 32) sdst[q] = __ldg(gsrc + q);
-        if (threadIdx.x == 0) s_lb = lb;
+        const int r = find_run_warp(prefix, nruns, blockIdx.x, threadIdx.x);
+        if (threadIdx.x == 0) {
+            s_r = r;
+            s_lb = blockIdx.x - __ldg(prefix + r);
+        }
     }
+    __syncthreads();
+    if (threadIdx.x < NW)
+        reinterpret_cast<int *>(&R)[threadIdx.x] = __ldg(reinterpret_cast<const int *>(runs + s_r) + threadIdx.x);
     __syncthreads();
     const int lb = s_lb;
     switch (R.storage) {
@@ -161,8 +184,8 @@ int blocks_box_moments_bin(const RunDesc &r) {
     return (int)((r.box.nbox + MB_THREADS - 1) / MB_THREADS) + r.box.tx * r.box.ty * r.box.tz;
 }
 
-cudaError_t launch_batch_collide(int phase, const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
-                                 int threads, int minb, cudaStream_t s) {
+cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *prefix, int nruns, int p,
+                                 int nblocks, int threads, int minb, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     if (phase == PHASE_NEAR)
         k_batch_collide<PHASE_NEAR, 1><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);

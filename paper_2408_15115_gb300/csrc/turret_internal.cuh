@@ -202,6 +202,17 @@ struct RunDesc {
     MlpDev mlp;          // the force/torque network (predictor mode 2)
 };
 enum { PHASE_BULK = 0, PHASE_NEAR = 1 };
+// What a batched collide+stream block needs of its run (staged in shared
+// memory by every block in one load per thread; the full RunDesc is larger).
+struct CollideDesc {
+    Geom g;
+    BoxGeom box;
+    void *f[2];
+    float *utop[2];
+    DevState *st;
+    const float *hbox;
+    int storage, split, tx, pad;
+};
 // h arrays of the IBM cycles, selected per run in batched launches
 enum { HSEL_R0 = 0, HSEL_HL = 1, HSEL_HB = 2 };
 
@@ -286,8 +297,8 @@ cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, vo
                                  float *utop_out, const DevState *st, int slot, const float *hbox,
                                  const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s);
 // Batched K1 of phase PHASE_BULK or PHASE_NEAR over nblocks blocks.
-cudaError_t launch_batch_collide(int phase, const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
-                                 int threads, int minb, cudaStream_t s);
+cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *prefix, int nruns, int p,
+                                 int nblocks, int threads, int minb, cudaStream_t s);
 bool is_batch_bulk_kernel(const void *fn);
 cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,
                                          cudaStream_t s);
