@@ -859,21 +859,12 @@ __global__ void __launch_bounds__(SPREAD_THREADS) k_spread(BoxGeom box, const MR
 // Batched forms: one launch per phase over all runs of a batch, block b of
 // the launch serving block b - prefix[r] of run r (prefix[r] <= b <
 // prefix[r + 1]), with the same block code as the single-run kernels.
-__device__ __forceinline__ int run_of(const int *__restrict__ prefix, int nruns, int b, int &local) {
-    int lo = 0, hi = nruns;  // largest r with prefix[r] <= b
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid;
-    }
-    local = b - __ldg(prefix + lo);
-    return lo;
-}
 
 __global__ void __launch_bounds__(PM_THREADS) k_batch_particle_markers(const RunDesc *__restrict__ runs,
                                                                         const int *__restrict__ prefix, int nruns,
                                                                         int p) {
     int lb;
-    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    const RunDesc &R = runs[block_run(prefix, nruns, lb)];
     pm_block(R.g, R.bc, R.box, R.st, p, 1, R.m, lb);
 }
 
@@ -881,7 +872,7 @@ __global__ void __launch_bounds__(ROWS_THREADS) k_batch_interp0_tiles(const RunD
                                                                       const int *__restrict__ prefix, int nruns,
                                                                       int warm) {
     int lb;
-    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    const RunDesc &R = runs[block_run(prefix, nruns, lb)];
     interp0_tile_block(R.box, R.nm, R.m, R.ba, R.tile_list, R.tile_count, R.cap, R.st, lb, warm);
 }
 
@@ -894,7 +885,7 @@ __global__ void __launch_bounds__(32 * INTERP_WARPS) k_batch_cycle(const RunDesc
                                                                    int sel_in, int sel_out, int sel_final, int last,
                                                                    int cyc, int adaptive) {
     int lb;
-    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    const RunDesc &R = runs[block_run(prefix, nruns, lb)];
     cycle_block(R.nm, R.m, hsel(R.m, sel_in), hsel(R.m, sel_out), sel_final >= 0 ? hsel(R.m, sel_final) : nullptr,
                 last, lb, R.st, cyc, adaptive, R.bc.slip_eps);
 }
@@ -907,7 +898,7 @@ __global__ void __launch_bounds__(288) k_batch_reduce_ft(const RunDesc *__restri
 __global__ void __launch_bounds__(SPREAD_THREADS) k_batch_spread(const RunDesc *__restrict__ runs,
                                                                  const int *__restrict__ prefix, int nruns) {
     int lb;
-    const RunDesc &R = runs[run_of(prefix, nruns, blockIdx.x, lb)];
+    const RunDesc &R = runs[block_run(prefix, nruns, lb)];
     spread_block(R.box, R.m.rec, R.ba, R.tile_list, R.tile_count, R.cap, lb);
 }
 

@@ -50,24 +50,6 @@ __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb
     }
 }
 
-// Run r of block b (largest r < nruns with prefix[r] <= b) by one warp: each
-// pass reads 32 table entries at once and narrows the range 32-fold by a
-// ballot, so a table of up to 1024 runs takes two dependent loads.
-__device__ __forceinline__ int find_run_warp(const int *__restrict__ prefix, int nruns, int b, int lane) {
-    int lo = 0, span = nruns;
-    while (span > 32) {
-        const int stride = (span + 31) / 32;
-        const int idx = lo + lane * stride;
-        const bool ok = idx < lo + span && __ldg(prefix + idx) <= b;
-        const unsigned m = __ballot_sync(0xffffffffu, ok);  // entry 0 of the range always qualifies
-        lo += (31 - __clz(m)) * stride;
-        span = min(stride, nruns - lo);
-    }
-    const bool ok = lane < span && __ldg(prefix + lo + lane) <= b;
-    const unsigned m = __ballot_sync(0xffffffffu, ok);
-    return lo + (31 - __clz(m));
-}
-
 // The near phase is a small launch on the critical path (no register cap).
 template <int PHASE, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *__restrict__ runs,
@@ -78,19 +60,11 @@ __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *
     constexpr int NW = (int)(sizeof(CollideDesc) / 4);
     static_assert(sizeof(CollideDesc) % 4 == 0 && NW <= 128, "descriptor staged by one load per thread");
     __shared__ CollideDesc R;
-    __shared__ int s_r, s_lb;
-    if (threadIdx.x < 32) {
-        const int r = find_run_warp(prefix, nruns, blockIdx.x, threadIdx.x);
-        if (threadIdx.x == 0) {
-            s_r = r;
-            s_lb = blockIdx.x - __ldg(prefix + r);
-        }
-    }
-    __syncthreads();
+    int lb;
+    const int r = block_run(prefix, nruns, lb);
     if (threadIdx.x < NW)
-        reinterpret_cast<int *>(&R)[threadIdx.x] = __ldg(reinterpret_cast<const int *>(runs + s_r) + threadIdx.x);
+        reinterpret_cast<int *>(&R)[threadIdx.x] = __ldg(reinterpret_cast<const int *>(runs + r) + threadIdx.x);
     __syncthreads();
-    const int lb = s_lb;
     switch (R.storage) {
         case ST_F32: batch_k1_run<PHASE, ST_F32>(R, p, lb); break;
         case ST_F16: batch_k1_run<PHASE, ST_F16>(R, p, lb); break;
@@ -105,8 +79,7 @@ __global__ void __launch_bounds__(MB_THREADS) k_batch_box_moments_bin(const RunD
                                                                       const int *__restrict__ prefix, int nruns,
                                                                       int p) {
     int lb;
-    const int r = find_run(prefix, nruns, blockIdx.x, lb);
-    const RunDesc &R = runs[r];
+    const RunDesc &R = runs[block_run(prefix, nruns, lb)];
     const Geom g = R.g;
     const BoxGeom box = R.box;
     const int nmom = (int)((box.nbox + MB_THREADS - 1) / MB_THREADS);

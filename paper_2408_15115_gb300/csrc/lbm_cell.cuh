@@ -860,21 +860,4 @@ __device__ __forceinline__ void tile_coords(int b, int tx, int ex, int ey, int p
     cz = pz * (rest / gy);
 }
 
-// ---------------------------------------------------------------------------
-// Batched K1: one launch over the (run, tile) table of many independent runs.
-// Block b belongs to the run r with prefix[r] <= b < prefix[r + 1]; every run
-// keeps its own storage type, window, boundary conditions, relaxation times
-// and tile, read from its descriptor.  PHASE_BULK: the far cells of runs that
-// split (no blocks for the others); PHASE_NEAR: the near region of runs that
-// split, the whole window (with forcing) of runs that do not.
-__device__ __forceinline__ int find_run(const int *__restrict__ prefix, int nruns, int b, int &local) {
-    int lo = 0, hi = nruns;  // largest r with prefix[r] <= b
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid;
-    }
-    local = b - __ldg(prefix + lo);
-    return lo;
-}
-
 }  // namespace turret

@@ -202,6 +202,41 @@ struct RunDesc {
     MlpDev mlp;          // the force/torque network (predictor mode 2)
 };
 enum { PHASE_BULK = 0, PHASE_NEAR = 1 };
+
+// Run r of block b of a batched launch (largest r < nruns with prefix[r] <=
+// b) by one warp: each pass reads 32 table entries at once and narrows the
+// range 32-fold by a ballot, so a table of up to 1024 runs takes two
+// dependent loads.
+__device__ __forceinline__ int find_run_warp(const int *__restrict__ prefix, int nruns, int b, int lane) {
+    int lo = 0, span = nruns;
+    while (span > 32) {
+        const int stride = (span + 31) / 32;
+        const int idx = lo + lane * stride;
+        const bool ok = idx < lo + span && __ldg(prefix + idx) <= b;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);  // entry 0 of the range always qualifies
+        lo += (31 - __clz(m)) * stride;
+        span = min(stride, nruns - lo);
+    }
+    const bool ok = lane < span && __ldg(prefix + lo + lane) <= b;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    return lo + (31 - __clz(m));
+}
+
+// The run of this block and the block's index within the run, found by warp
+// 0 and shared through shared memory (every thread of the block must call).
+__device__ __forceinline__ int block_run(const int *__restrict__ prefix, int nruns, int &local) {
+    __shared__ int s_run, s_local;
+    if (threadIdx.x < 32) {
+        const int r = find_run_warp(prefix, nruns, blockIdx.x, threadIdx.x);
+        if (threadIdx.x == 0) {
+            s_run = r;
+            s_local = blockIdx.x - __ldg(prefix + r);
+        }
+    }
+    __syncthreads();
+    local = s_local;
+    return s_run;
+}
 // What a batched collide+stream block needs of its run (staged in shared
 // memory by every block in one load per thread; the full RunDesc is larger).
 struct CollideDesc {
