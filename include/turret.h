@@ -92,6 +92,12 @@ typedef struct {
  *               captured CUDA graph (same results; for debugging).
  *   fixed_position 1: the particle's centre is held (v = 0) while its
  *               rotation stays free (a sphere spun up by a shear flow).
+ *   force_eval 0: the surface stress is taken on the surface offset by two
+ *               cells along the marker normals (areas and arms of that
+ *               surface), whose interpolation stencils lie in the fluid
+ *               outside the diffuse interface; 1: at the markers, as printed
+ *               in Sec. 2.2 (which averages in the fluid inside the body and
+ *               gives 2-3 times too small a drag and torque).
  *   stochastic_rounding 1 (BF16 storage only): the collide+stream stores
  *               round each stored value up or down with probability equal to
  *               its distance from the other neighbour (unbiased rounding),
@@ -106,6 +112,8 @@ typedef struct {
     int32_t no_graph;
     int32_t stochastic_rounding;
     int32_t fixed_position;
+    int32_t force_eval;
+    int32_t pad0;
 } turret_flags;
 
 /* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates

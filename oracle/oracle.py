@@ -38,7 +38,7 @@ class OrcParams(C.Structure):
         ("kappa", C.c_double), ("g", C.c_double * 3),
         ("fixed_position", C.c_int), ("uw_bottom", C.c_double * 3), ("uw_top", C.c_double * 3),
         ("reinject_trigger", C.c_int), ("reinject_target", C.c_int), ("reinject_below", C.c_int),
-        ("reinject_above", C.c_int),
+        ("reinject_above", C.c_int), ("force_eval", C.c_int),
     ]
 
 
@@ -210,19 +210,22 @@ class Sim:
     with velocity uw_bottom / uw_top.  fixed_position 1 holds the particle's
     centre (v = 0) and leaves its rotation free.  reinject = (trigger, target,
     below, above): the re-injection copy of Sec. 2.5 (slide 0 only; trigger 0
-    off).  Arrays are (nz, ny, nx, ...)."""
+    off).  force_eval 0: force and torque from the stress on the surface
+    offset by 2 cells along the normals (outside the diffuse interface); 1: the
+    stress interpolated at the markers, as printed in Sec. 2.2.  Arrays are
+    (nz, ny, nx, ...)."""
 
     STATE_FIELDS = 45
 
     def __init__(self, nx, ny, nz, tau, bc_x=0, bc_y=0, bc_bottom=0, bc_top=0, sponge=0, slide=0,
                  anchor_frac=0.25, force_scheme=0, rot_form=0, gravity=0, renorm=0, ibm_cycles=4,
                  kappa=1.0, g=(0.0, 0.0, 0.0), fixed_position=0, uw_bottom=(0.0, 0.0, 0.0), uw_top=(0.0, 0.0, 0.0),
-                 reinject=(0, 0, 0, 0)):
+                 reinject=(0, 0, 0, 0), force_eval=0):
         self.shape = (nz, ny, nx)
         p = OrcParams(nx, ny, nz, bc_x, bc_y, bc_bottom, bc_top, sponge, slide, float(anchor_frac), float(tau),
                       force_scheme, rot_form, gravity, renorm, ibm_cycles, float(kappa), (C.c_double * 3)(*g),
                       int(fixed_position), (C.c_double * 3)(*uw_bottom), (C.c_double * 3)(*uw_top),
-                      *[int(v) for v in reinject])
+                      *[int(v) for v in reinject], int(force_eval))
         self._params = p
         self._s = lib().orc_new(C.byref(p))
 

@@ -374,6 +374,7 @@ typedef struct {
      * centre's window z drops below `trigger`, the planes [zf - below, zf +
      * above) around it (zf = floor of that z) move up by target - zf */
     int reinject_trigger, reinject_target, reinject_below, reinject_above;
+    int force_eval;           /* 0: stress on the offset surface X + 2n (READING, default); 1: at the markers */
 } orc_params;
 
 typedef struct {
@@ -390,6 +391,7 @@ typedef struct {
     int has_particle;
     int64_t nm;
     double *Xb, *nb, *dS;      /* body-frame marker offsets (about C_m), normals, areas */
+    double *dSo;               /* areas of the offset surface Xb + OFFSET nb (same triangles) */
     double *X, *n, *U;         /* current window-frame markers, normals, velocities */
     double *hl;                /* Lagrangian IBM force (last h_{l=0} used for h_imm) */
     double vol, Jm[9], Jminv[9], area;
@@ -436,7 +438,7 @@ orc_sim *orc_new(const orc_params *p) {
 void orc_free(orc_sim *s) {
     if (!s) return;
     free(s->f); free(s->fpost); free(s->h); free(s->u); free(s->sig); free(s->utop); free(s->tau);
-    free(s->Xb); free(s->nb); free(s->dS); free(s->X); free(s->n); free(s->U); free(s->hl);
+    free(s->Xb); free(s->nb); free(s->dS); free(s->dSo); free(s->X); free(s->n); free(s->U); free(s->hl);
     free(s);
 }
 
@@ -688,13 +690,21 @@ static void update_markers(orc_sim *s) {
 
 /* Marker stencils must lie inside the window along non-periodic axes
  * (READING: the paper is silent; anything else would read outside). */
+/* Distance along the outward normal of the surface on which the stress is
+ * evaluated (force_eval 0): the kernel half-width, so that the interpolation
+ * stencil of X + OFFSET n lies entirely on the fluid side of the markers. */
+#define OFFSET 2.0
+
 static int check_support(const orc_sim *s) {
     orc_grid g = sim_grid(s);
     int per[3] = {g.per_x, g.per_y, g.per_z}, n[3] = {g.nx, g.ny, g.nz};
+    const double off = s->p.force_eval == 0 ? OFFSET : 0.0;
     for (int64_t k = 0; k < s->nm; ++k)
         for (int a = 0; a < 3; ++a) {
             if (per[a]) continue;
             int b = (int)floor(s->X[3 * k + a]);
+            if (b - 1 < 0 || b + 2 > n[a] - 1) return -2;
+            b = (int)floor(s->X[3 * k + a] + off * s->n[3 * k + a]);
             if (b - 1 < 0 || b + 2 > n[a] - 1) return -2;
         }
     return 0;
@@ -704,13 +714,28 @@ static int check_support(const orc_sim *s) {
  *   F = sum_k dS_k sigma(X_k) n_k,  sigma(X_k) = sum_x sigma(x) W(x - X_k),
  *   T = sum_k (X_k - C_m) x (dS_k sigma(X_k) n_k).
  * READING: the printed torque "[sigma n] ^ (X_k - C_m)" is -(r x F); we take
- * the physical moment r x F. rho_f = 1.                                      */
+ * the physical moment r x F. rho_f = 1.
+ * READING (force_eval 0, default): the IBM fluid fills the body too, and a
+ * stencil centred on X_k averages the exterior traction with the interior's
+ * (rigid motion: no viscous stress), which was measured 2-3 times too small
+ * (a sphere settling at about twice its confined Stokes velocity, a spinning
+ * sphere feeling 0.45 of its Stokes torque).  The stress is therefore taken on
+ * the offset surface X_k + OFFSET n_k, whose stencils lie on the fluid side,
+ * with that surface's areas dSo_k and arms X_k + OFFSET n_k - C_m: for steady
+ * Stokes flow the stress integral over any surface enclosing the body is the
+ * same, and this one encloses the whole diffuse interface.  force_eval 1: the
+ * formula as printed.  Fp: the pressure part -p I of the same integral.      */
 static void force_torque(orc_sim *s) {
     orc_grid g = sim_grid(s);
+    const int off = s->p.force_eval == 0;
+    double *Xs = (double *)malloc(sizeof(double) * 3 * (size_t)s->nm);
+    for (int64_t k = 0; k < s->nm; ++k)
+        for (int a = 0; a < 3; ++a) Xs[3 * k + a] = s->X[3 * k + a] + (off ? OFFSET * s->n[3 * k + a] : 0.0);
+    const double *area = off ? s->dSo : s->dS;
     double *sk = (double *)malloc(sizeof(double) * 9 * (size_t)s->nm);
-    orc_interp(&g, s->sig, 9, s->X, s->nm, sk);
+    orc_interp(&g, s->sig, 9, Xs, s->nm, sk);
     /* the isotropic part of Eq. (10) alone: p = c_s^2 (rho - 1) per cell from
-     * the same populations, interpolated to the markers; its surface sum is the
+     * the same populations, interpolated likewise; its surface sum is the
      * pressure force, F - Fp the viscous one */
     double *pc = (double *)malloc(sizeof(double) * (size_t)s->ncell);
     for (int64_t c = 0; c < s->ncell; ++c) {
@@ -719,21 +744,17 @@ static void force_torque(orc_sim *s) {
         pc[c] = (rho - 1.0) / 3.0;
     }
     double *pk = (double *)malloc(sizeof(double) * (size_t)s->nm);
-    orc_interp(&g, pc, 1, s->X, s->nm, pk);
-    for (int a = 0; a < 3; ++a) s->Fp[a] = 0.0;
-    for (int64_t k = 0; k < s->nm; ++k)
-        for (int a = 0; a < 3; ++a) s->Fp[a] -= s->dS[k] * pk[k] * s->n[3 * k + a];
-    free(pk);
-    free(pc);
+    orc_interp(&g, pc, 1, Xs, s->nm, pk);
     double C[3] = {s->r[0] - (double)s->origin[0], s->r[1] - (double)s->origin[1], s->r[2] - (double)s->origin[2]};
-    for (int a = 0; a < 3; ++a) s->F[a] = s->T[a] = 0.0;
+    for (int a = 0; a < 3; ++a) s->F[a] = s->T[a] = s->Fp[a] = 0.0;
     for (int64_t k = 0; k < s->nm; ++k) {
         double fk[3], arm[3], tk[3];
         for (int a = 0; a < 3; ++a) {
             fk[a] = 0.0;
             for (int b = 0; b < 3; ++b) fk[a] += sk[9 * k + 3 * a + b] * s->n[3 * k + b];
-            fk[a] *= s->dS[k];
-            arm[a] = s->X[3 * k + a] - C[a];
+            fk[a] *= area[k];
+            arm[a] = Xs[3 * k + a] - C[a];
+            s->Fp[a] -= area[k] * pk[k] * s->n[3 * k + a];
         }
         cross(arm, fk, tk);
         for (int a = 0; a < 3; ++a) {
@@ -741,13 +762,17 @@ static void force_torque(orc_sim *s) {
             s->T[a] += tk[a];
         }
     }
+    free(pk);
+    free(pc);
     free(sk);
+    free(Xs);
 }
 
 static void run_ibm(orc_sim *s) {
     orc_grid g = sim_grid(s);
     orc_ibm(&g, s->u, s->X, s->U, s->dS, s->nm, s->p.ibm_cycles, s->h, s->hl);
 }
+
 
 /* 6DOF update, Sec. 2.3 (leap-frog, Eqs. 22-27), dt = 1, rho_f = 1, m = kappa V:
  *   a = g_eff + F/(kappa V);  v(t+1/2) = v(t-1/2) + a;  r(t+1) = r(t) + v(t+1/2)
@@ -874,6 +899,22 @@ int orc_load_particle(orc_sim *s, const double *verts, int64_t nv, const int32_t
     s->hl = (double *)calloc(3 * (size_t)nv, sizeof(double));
     double com[3];
     if (orc_mesh_props(verts, nv, tris, nt, s->dS, s->nb, &s->vol, com, s->Jm, &s->area) != 0) return -1;
+    /* areas of the offset surface: the same triangles through Xb + OFFSET nb,
+     * one third of each triangle's area to each of its vertices */
+    s->dSo = (double *)calloc((size_t)nv, sizeof(double));
+    for (int64_t t = 0; t < nt; ++t) {
+        double P[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 3; ++a) P[c][a] = verts[3 * tris[3 * t + c] + a] + OFFSET * s->nb[3 * tris[3 * t + c] + a];
+        double e1[3], e2[3], cr[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = P[1][a] - P[0][a];
+            e2[a] = P[2][a] - P[0][a];
+        }
+        cross(e1, e2, cr);
+        const double A = 0.5 * sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (int c = 0; c < 3; ++c) s->dSo[tris[3 * t + c]] += A / 3.0;
+    }
     inv3(s->Jm, s->Jminv);
     for (int64_t k = 0; k < nv; ++k)
         for (int a = 0; a < 3; ++a) s->Xb[3 * k + a] = verts[3 * k + a] - com[a];

@@ -114,26 +114,28 @@ def stokes_terminal_velocity(r, nu, g_drive):
     return g_drive * r * r / (4.5 * nu)
 
 
-def _fl78_coeffs(r, nu, kappa):
+def _fl78_coeffs(r, nu, kappa, inertia=None):
     m = kappa * 4.0 / 3.0 * math.pi * r ** 3
-    I = 0.4 * m * r * r
+    I = 0.4 * m * r * r if inertia is None else float(inertia)
     c0 = 8.0 * math.pi * nu * r ** 3
     return I, c0, c0 * r / (3.0 * math.sqrt(math.pi * nu)), c0 / 3.0
 
 
-def fl78_rotation(r, nu, kappa, torque, t_end, dt, quad=8, history=True):
+def fl78_rotation(r, nu, kappa, torque, t_end, dt, quad=8, history=True, inertia=None):
     """Angular velocity w(t_n) of a sphere of radius r at rest under a
     constant torque (per unit fluid density), by the relation of Eq. B.2:
       I dw/dt = T - 8 pi nu r^3 w - 8 pi nu r^3 r / (3 sqrt(pi nu))
                 int w'(s) (t - s)^(-1/2) ds
               + (8/3) pi nu r^3 int w'(s) exp(nu (t - s) / r^2)
                 erfc(sqrt(nu (t - s) / r^2)) ds,
-    I = 2 m r^2 / 5 with m = kappa (4/3) pi r^3 (rho_f = 1).  Piecewise-linear
+    I = 2 m r^2 / 5 with m = kappa (4/3) pi r^3 (rho_f = 1) unless `inertia`
+    gives it (a body whose hydrodynamic radius r differs from the radius of
+    its mass distribution).  Piecewise-linear
     w; the first history kernel is integrated exactly per interval, the
     second (bounded) one by Gauss-Legendre with `quad` nodes; implicit in the
     new angular velocity.  Terminal value T / (8 pi nu r^3).  Returns (t, w)."""
     from scipy.special import erfcx
-    I, c0, c1, c2 = _fl78_coeffs(r, nu, kappa)
+    I, c0, c1, c2 = _fl78_coeffs(r, nu, kappa, inertia)
     if not history:
         c1 = c2 = 0.0
     xg, wg = np.polynomial.legendre.leggauss(quad)
@@ -161,15 +163,16 @@ def fl78_rotation(r, nu, kappa, torque, t_end, dt, quad=8, history=True):
     return t, w
 
 
-def fl78_rotation_exact(r, nu, kappa, torque, t):
+def fl78_rotation_exact(r, nu, kappa, torque, t, inertia=None):
     """Exact solution of Eq. B.2 from rest for a constant torque.  With
     q = sqrt(nu) / r, L[exp(q^2 t) erfc(q sqrt(t))] = 1 / (sqrt(s)(sqrt(s) + q)),
     so W(s) = T (p + q) / (s P(p)), p = sqrt(s), with the cubic
     P(p) = (I p^2 + c1 sqrt(pi) p + c0)(p + q) - c2 p; by partial fractions over
     its roots p_i, w(t) = T sum_i R_i (1 - E(-p_i, t)) / (-p_i),
-    R_i = (p_i + q) / P'(p_i), E(l, t) = exp(l^2 t) erfc(l sqrt(t))."""
+    R_i = (p_i + q) / P'(p_i), E(l, t) = exp(l^2 t) erfc(l sqrt(t)).
+    `inertia` as in fl78_rotation."""
     from scipy.special import wofz
-    I, c0, c1, c2 = _fl78_coeffs(r, nu, kappa)
+    I, c0, c1, c2 = _fl78_coeffs(r, nu, kappa, inertia)
     q = math.sqrt(nu) / r
     c1p = c1 * math.sqrt(math.pi)
     P = np.array([I, I * q + c1p, c1p * q + c0 - c2, c0 * q])

@@ -241,6 +241,36 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
         r.hdS[0] = r.hdS[1] = r.hdS[2] = 0.0f;
         m.rec[k] = r;
         m.base[k] = r.base;
+        // the stencil of the point of the stress surface, X + F_OFFSET n
+        // (force_eval 0; the marker's own stencil otherwise)
+        if (bc.force_eval == 0) {
+            MRec ro;
+            int bo[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float xr = f_cf[a] + arm[a] + F_OFFSET * nn[a];
+                const float fl = floorf(xr);
+                const float t = xr - fl;
+                int base_rel = (int)fl - 1;
+                int bv = i_ci[a] + base_rel - i_lo[a];
+                float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
+                if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
+                    bv = 0;
+                    base_rel = i_lo[a] - i_ci[a];
+                    w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;
+                    bad = true;
+                }
+                const int abs_base = i_ci[a] + base_rel;
+                if (!per[a] && (abs_base < 0 || abs_base + 3 > n[a] - 1)) bad = true;
+                bo[a] = bv;
+                float *dstw = (a == 0) ? ro.wx : (a == 1) ? ro.wy : ro.wz;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dstw[q] = w4[q];
+            }
+            ro.base = bo[0] | (bo[1] << 10) | (bo[2] << 20);
+            ro.hdS[0] = ro.hdS[1] = ro.hdS[2] = 0.0f;
+            m.reco[k] = ro;
+        }
         if (bad) atomicCAS(&st->status, 0, STAT_DOMAIN);  // the first latched error wins
         for (int a = 0; a < 3; ++a) bbmax[a] = bbv[a];
     }
@@ -305,22 +335,39 @@ constexpr int ROWS_WARPS = ROWS_THREADS / 32;
 // stencil cells per lane, xor-shuffle sums), h^0 = U - I[u*] and the
 // traction dS sigma.n with its moment about C_m.
 // warm: the IBM cycles start from the previous step's h (kept in hl).
+// Two stencil cells of a 4x4x4 stencil per lane: the cell offsets and weights.
+__device__ __forceinline__ void lane_cells(const BoxGeom &box, const MRec &r, int lane, size_t &c0, size_t &c1,
+                                           float &w0, float &w1) {
+    const int bx = r.base & 1023, by = (r.base >> 10) & 1023, bz = (r.base >> 20) & 1023;
+    const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
+    const float wxy = pick4(r.wx, i) * pick4(r.wy, j);
+    w0 = wxy * (kz ? r.wz[1] : r.wz[0]);
+    w1 = wxy * (kz ? r.wz[3] : r.wz[2]);
+    c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
+    c1 = c0 + 2 * (size_t)box.By * box.Bx;
+}
+
+// m.force_eval 0: the stress at the point X + F_OFFSET n of the offset
+// surface, with its area and arm; 1: at the marker, as printed
 __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, const MarkerArrays &m,
                                                    const BoxArrays &ba, int k, const MRec &rk, int lane, int warm) {
-    const int bx = rk.base & 1023, by = (rk.base >> 10) & 1023, bz = (rk.base >> 20) & 1023;
-    const int i = lane & 3, j = (lane >> 2) & 3, kz = lane >> 4;
-    const float wxy = pick4(rk.wx, i) * pick4(rk.wy, j);
-    const float w0 = wxy * (kz ? rk.wz[1] : rk.wz[0]);
-    const float w1 = wxy * (kz ? rk.wz[3] : rk.wz[2]);
-    const size_t c0 = ((size_t)(bz + kz) * box.By + (by + j)) * box.Bx + (bx + i);
-    const size_t c1 = c0 + 2 * (size_t)box.By * box.Bx;
+    const int fe = m.force_eval;
+    size_t c0, c1, d0, d1;
+    float w0, w1, v0, v1;
+    lane_cells(box, rk, lane, c0, c1, w0, w1);
+    if (fe == 0) {
+        const MRec ro = m.reco[k];
+        lane_cells(box, ro, lane, d0, d1, v0, v1);
+    } else {
+        d0 = c0, d1 = c1, v0 = w0, v1 = w1;
+    }
     const size_t N = box.nbox;
     float acc[10];
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = w0 * ba.u[c * N + c0] + w1 * ba.u[c * N + c1];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc[3 + c] = w0 * ba.s[c * N + c0] + w1 * ba.s[c * N + c1];
-    acc[9] = w0 * ba.p[c0] + w1 * ba.p[c1];
+    for (int c = 0; c < 6; ++c) acc[3 + c] = v0 * ba.s[c * N + d0] + v1 * ba.s[c * N + d1];
+    acc[9] = v0 * ba.p[d0] + v1 * ba.p[d1];
 #pragma unroll
     for (int c = 0; c < 10; ++c)
 #pragma unroll
@@ -338,10 +385,12 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
         }
         const float sxx = acc[3], syy = acc[4], szz = acc[5], sxy = acc[6], sxz = acc[7], syz = acc[8];
         const float nx = m.n[k], ny = m.n[nm + k], nz = m.n[2 * nm + k];
-        const float f0 = dS * (sxx * nx + sxy * ny + sxz * nz);
-        const float f1 = dS * (sxy * nx + syy * ny + syz * nz);
-        const float f2 = dS * (sxz * nx + syz * ny + szz * nz);
-        const float r0 = m.arm[k], r1 = m.arm[nm + k], r2 = m.arm[2 * nm + k];
+        const float dA = fe == 0 ? m.dSo[k] : dS;  // area of the surface the stress is taken on
+        const float f0 = dA * (sxx * nx + sxy * ny + sxz * nz);
+        const float f1 = dA * (sxy * nx + syy * ny + syz * nz);
+        const float f2 = dA * (sxz * nx + syz * ny + szz * nz);
+        const float off = fe == 0 ? F_OFFSET : 0.0f;
+        const float r0 = m.arm[k] + off * nx, r1 = m.arm[nm + k] + off * ny, r2 = m.arm[2 * nm + k] + off * nz;
         m.ft[k] = f0;
         m.ft[nm + k] = f1;
         m.ft[2 * nm + k] = f2;
@@ -349,7 +398,7 @@ __device__ __forceinline__ void interp_marker_warp(const BoxGeom &box, int nm, c
         m.ft[4 * nm + k] = r2 * f0 - r0 * f2;
         m.ft[5 * nm + k] = r0 * f1 - r1 * f0;
         // the isotropic part -p I of sigma alone: the pressure force
-        const float pdS = -dS * acc[9];
+        const float pdS = -dA * acc[9];
         m.ft[6 * nm + k] = pdS * nx;
         m.ft[7 * nm + k] = pdS * ny;
         m.ft[8 * nm + k] = pdS * nz;

@@ -253,7 +253,8 @@ extern "C" turret_status lbm_set_flags(turret_ctx *c, const turret_flags *fl) {
     if (!c || !fl) return fail(c, TURRET_EINVAL, "NULL argument");
     if (fl->force_scheme < 0 || fl->force_scheme > 1 || fl->rot_form < 0 || fl->rot_form > 1 || fl->gravity < 0 ||
         fl->gravity > 1 || fl->ibm_cycles < 1 || fl->ibm_cycles > 64 || fl->stochastic_rounding < 0 ||
-        fl->stochastic_rounding > 1 || fl->fixed_position < 0 || fl->fixed_position > 1)
+        fl->stochastic_rounding > 1 || fl->fixed_position < 0 || fl->fixed_position > 1 || fl->force_eval < 0 ||
+        fl->force_eval > 1)
         return fail(c, TURRET_EINVAL, "invalid flags");
     if (c->has_particle) return fail(c, TURRET_ESTATE, "flags must be set before ibm_load_surface");
     c->flags = *fl;
@@ -394,7 +395,8 @@ struct IbmLayout {
 };
 
 // Support box: every marker lies within rc = ceil(bounding radius) of C_m,
-// so all 4x4x4 stencils fit a cube of 2 rc + 6 cells placed at floor(C) - rc - 2.
+// so all 4x4x4 stencils fit a cube of 2 rc + 6 cells placed at floor(C) - rc - 2;
+// rc includes the offset F_OFFSET of the stress surface (its stencils too).
 static bool ibm_layout(const MeshProps &mp, const double *V, int64_t nv, IbmLayout &L) {
     if (nv <= 0 || nv >= (1 << 24)) return false;
     double rb = 0.0, rs = INFINITY;
@@ -406,7 +408,7 @@ static bool ibm_layout(const MeshProps &mp, const double *V, int64_t nv, IbmLayo
     }
     L.rmin = rs;
     L.rmax = rb;
-    L.rc = (int)ceil(rb + 1e-6);
+    L.rc = (int)ceil(rb + F_OFFSET + 1e-6);
     const int B = 2 * L.rc + 6;
     L.box.Bx = L.box.By = L.box.Bz = B;
     L.box.tx = L.box.ty = L.box.tz = (B + TILE - 1) / TILE;
@@ -423,7 +425,9 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     m.Xb = (const float *)cv.take(3 * nm * 4);
     m.nb = (const float *)cv.take(3 * nm * 4);
     m.dS = (const float *)cv.take(nm * 4);
+    m.dSo = (const float *)cv.take(nm * 4);
     m.rec = (MRec *)cv.take(nm * sizeof(MRec));
+    m.reco = (MRec *)cv.take(nm * sizeof(MRec));
     m.base = (int *)cv.take(nm * 4);
     m.ft = (float *)cv.take(9 * nm * 4);
     m.U = (float *)cv.take(3 * nm * 4);
@@ -436,6 +440,7 @@ static size_t carve_ibm(Carver &cv, const IbmLayout &L, turret_ctx *c) {
     m.aidx = (int *)cv.take(nm * (size_t)ROWCAP * 4);
     m.alen = (int *)cv.take(nm * 4);
     m.seg = (int *)cv.take(6 * ((nm + MARKER_SEG - 1) / MARKER_SEG) * 4);
+    m.force_eval = c ? c->flags.force_eval : 0;
     BoxArrays ba;
     ba.u = (float *)cv.take(3 * nb * 4);
     ba.s = (float *)cv.take(6 * nb * 4);
@@ -667,6 +672,9 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
             const int b = (int)floor(X);
             if (b - 1 < 0 || b + 2 > n[a] - 1)
                 return fail(c, TURRET_EINVAL, "a marker is closer than 2 cells to a closed face");
+            const int bo = (int)floor(X + (c->flags.force_eval == 0 ? F_OFFSET * mp.nrm[3 * k + a] : 0.0));
+            if (bo - 1 < 0 || bo + 2 > n[a] - 1)
+                return fail(c, TURRET_EINVAL, "a point of the stress surface is closer than 2 cells to a closed face");
         }
     double Jinv[9];
     if (!inverse3(mp.Jm, Jinv)) return fail(c, TURRET_EINVAL, "singular inertia tensor");
@@ -692,6 +700,7 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     B.anchor_z = c->win.anchor_frac * c->win.nz;
     B.rot_form = c->flags.rot_form;
     B.fixed = c->flags.fixed_position;
+    B.force_eval = c->flags.force_eval;
     B.renorm = c->flags.renorm_orientation;
     B.slide = c->win.slide;
     B.nm = L.nm;
@@ -706,7 +715,7 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     B.log_cap = c->log_cap;
     // static marker data (body frame): offsets from C_m, normals, areas
     const size_t nm = (size_t)L.nm;
-    c->staging.assign(7 * nm, 0.0f);
+    c->staging.assign(8 * nm, 0.0f);
     for (size_t k = 0; k < nm; ++k) {
         for (int a = 0; a < 3; ++a) {
             c->staging[a * nm + k] = (float)(V[3 * k + a] - mp.com[a]);
@@ -714,10 +723,24 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
         }
         c->staging[6 * nm + k] = (float)mp.dS[k];
     }
+    // areas of the offset surface Xb + F_OFFSET nb: the same triangles, one
+    // third of each triangle's area to each of its vertices
+    for (int64_t t = 0; t < nt; ++t) {
+        double P[3][3];
+        for (int e = 0; e < 3; ++e)
+            for (int a = 0; a < 3; ++a) P[e][a] = V[3 * T[3 * t + e] + a] + F_OFFSET * mp.nrm[3 * T[3 * t + e] + a];
+        const double u[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+        const double w[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+        const double cr[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double ar = 0.5 * sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        for (int e = 0; e < 3; ++e) c->staging[7 * nm + T[3 * t + e]] += (float)(ar / 3.0);
+    }
     CK(cudaMemcpyAsync((void *)c->mk.Xb, c->staging.data(), 3 * nm * 4, cudaMemcpyHostToDevice, c->stream), "Xb");
     CK(cudaMemcpyAsync((void *)c->mk.nb, c->staging.data() + 3 * nm, 3 * nm * 4, cudaMemcpyHostToDevice, c->stream),
        "nb");
     CK(cudaMemcpyAsync((void *)c->mk.dS, c->staging.data() + 6 * nm, nm * 4, cudaMemcpyHostToDevice, c->stream), "dS");
+    CK(cudaMemcpyAsync((void *)c->mk.dSo, c->staging.data() + 7 * nm, nm * 4, cudaMemcpyHostToDevice, c->stream),
+       "dSo");
     CK(cudaMemsetAsync(c->ba.h, 0, 3 * (size_t)L.box.nbox * 4, c->stream), "h");
     // rigid-body state at t: r(t), d = I, v(t-1/2) = v0, w(t-1/2) = w0, L = J w0
     CK(cudaMemcpyAsync(&c->host_state, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state");
@@ -991,7 +1014,8 @@ bool same_config(const CkptHeader &h, const turret_ctx *c) {
            h.nm == (c->has_particle ? c->nm : 0) && memcmp(&h.win, &c->win, sizeof(turret_window)) == 0 &&
            h.flags.force_scheme == c->flags.force_scheme && h.flags.rot_form == c->flags.rot_form &&
            h.flags.gravity == c->flags.gravity && h.flags.ibm_cycles == c->flags.ibm_cycles &&
-           h.flags.stochastic_rounding == c->flags.stochastic_rounding && h.nu == c->nu &&
+           h.flags.stochastic_rounding == c->flags.stochastic_rounding &&
+           h.flags.force_eval == c->flags.force_eval && h.nu == c->nu &&
            h.kappa == c->kappa && h.g[0] == c->g[0] && h.g[1] == c->g[1] && h.g[2] == c->g[2] &&
            h.nbox == (c->has_particle ? c->box.nbox : 0);
 }

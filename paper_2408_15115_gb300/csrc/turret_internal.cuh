@@ -118,6 +118,7 @@ struct BodyConst {
     double anchor_z;   // window z the centre is kept near
     int rot_form, renorm, slide;
     int fixed;         // 1: the centre is held (v = 0), rotation free
+    int force_eval;    // 0: stress on the offset surface (default), 1: at the markers
     int nm;            // markers
     int rc;            // ceil of the bounding radius of the markers about C_m
     float rmin, rmax;  // smallest and largest marker distance from C_m
@@ -140,6 +141,10 @@ struct BodyConst {
 // Markers are processed in segments of MARKER_SEG consecutive markers (one
 // block of the marker kernel); each segment's stencil bases have a bounding box.
 constexpr int MARKER_SEG = 128;
+// Offset (cells, along the outward normal) of the surface on which the stress
+// is integrated: the kernel half-width, so its stencils lie outside the
+// diffuse interface.
+constexpr float F_OFFSET = 2.0f;
 
 struct __align__(16) MRec {
     int base;
@@ -151,7 +156,9 @@ struct MarkerArrays {
     const float *Xb;   // [3][nm] body-frame offsets from C_m
     const float *nb;   // [3][nm] body-frame normals
     const float *dS;   // [nm]
+    const float *dSo;  // [nm] areas of the offset surface Xb + F_OFFSET nb (force evaluation)
     MRec *rec;         // [nm] stencil records
+    MRec *reco;        // [nm] stencils of the offset points X + F_OFFSET n (stress interpolation)
     int *base;         // [nm] packed stencil bases (copy of rec[k].base, coalesced for binning)
     float *ft;         // [9][nm] dS sigma.n, its moment about C_m, and the pressure part -dS p n
     float *U;          // [3][nm] prescribed velocity
@@ -165,6 +172,7 @@ struct MarkerArrays {
     int *alen;         // [nm] entries per row
     int *seg;          // [ceil(nm / MARKER_SEG)][6] per segment of MARKER_SEG consecutive
                        // markers: min x, y, z then max x, y, z of the stencil bases
+    int force_eval;    // 0: stress on the offset surface (reco, dSo), 1: at the markers
 };
 
 struct BoxArrays {

@@ -29,7 +29,8 @@ class Window(C.Structure):
 class Flags(C.Structure):
     _fields_ = [("force_scheme", C.c_int32), ("rot_form", C.c_int32), ("gravity", C.c_int32),
                 ("renorm_orientation", C.c_int32), ("ibm_cycles", C.c_int32), ("no_graph", C.c_int32),
-                ("stochastic_rounding", C.c_int32), ("fixed_position", C.c_int32)]
+                ("stochastic_rounding", C.c_int32), ("fixed_position", C.c_int32), ("force_eval", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 class ParticleState(C.Structure):
@@ -219,7 +220,7 @@ class Turret:
             raise TurretError(rc, self._L.turret_last_error(None).decode())
         self.ctx = ctx
         if flags:
-            f = Flags(0, 0, 0, 0, 4, 0, 0, 0)
+            f = Flags(0, 0, 0, 0, 4, 0, 0, 0, 0, 0)
             for k, v in flags.items():
                 setattr(f, k, int(v))
             self._check(self._L.lbm_set_flags(self.ctx, C.byref(f)))

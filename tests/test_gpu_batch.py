@@ -30,7 +30,7 @@ def _runs():
                  storage="f16")
     t.load_surface(V, Tr, (19.6, 20.3, 16.0), v0=(0, 0, -0.08), w0=(0.001, 0, 0))
     out.append(t)
-    V, Tr = I.sphere(4, 10.0)
+    V, Tr = I.sphere(4, 9.0)
     t = T.Turret(20, 20, 40, 0.08, 2.0, (0, 0, -1e-4), 0, 0, 1, 2, sponge=4, storage="bf16")
     t.load_surface(V, Tr, (9.8, 10.1, 20.5), v0=(0.002, 0, -0.01))
     out.append(t)
