@@ -741,8 +741,22 @@ __device__ __forceinline__ void reduce_block(int nm, const float *__restrict__ f
                                              int predictor, int opts, double theta, double *__restrict__ log,
                                              long long log_cap) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a = 0.0;
-    for (int k = lane; k < nm; k += 32) a += (double)ft[c * nm + k];
+    // eight independent partial sums per lane, so that eight loads are in
+    // flight at a time; combined in a fixed order (reproducible)
+    double a8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const float *fc = ft + (size_t)c * nm;
+    int k = lane;
+    for (; k + 7 * 32 < nm; k += 8 * 32) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(fc + k + u * 32);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a8[u] += (double)v[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (k + u * 32 < nm) a8[u] += (double)__ldg(fc + k + u * 32);
+    double a = ((a8[0] + a8[1]) + (a8[2] + a8[3])) + ((a8[4] + a8[5]) + (a8[6] + a8[7]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) {

@@ -42,7 +42,7 @@ __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
         k1_pair<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else if (R.split) {
-        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_MARGIN, box.By + 2 * NEAR_MARGIN, 1, cx, cy, cz);
+        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_GROW, box.By + 2 * NEAR_GROW, 1, cx, cy, cz);
         k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else {
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
@@ -149,7 +149,7 @@ int blocks_bulk(const RunDesc &r, int threads) {
 
 int blocks_near(const RunDesc &r, int threads) {
     if (!r.split) return tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2);
-    return tile_blocks(r.box.Bx + 2 * NEAR_MARGIN, r.box.By + 2 * NEAR_MARGIN, r.box.Bz + 2 * NEAR_MARGIN, threads,
+    return tile_blocks(r.box.Bx + 2 * NEAR_GROW, r.box.By + 2 * NEAR_GROW, r.box.Bz + 2 * NEAR_GROW, threads,
                        r.tx, 1);
 }
 

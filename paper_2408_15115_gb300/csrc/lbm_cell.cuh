@@ -384,7 +384,7 @@ __device__ __forceinline__ int rel_axis(int c, int lo, int lo_w, int margin, int
 //   K1_ALL    every cell, no support box (fluid without particle);
 //   K1_ALLF   every cell, h_imm read on the support box;
 //   K1_FAR    every cell outside the near region (support box grown by
-//             NEAR_MARGIN cells) -- no forcing there;
+//             NEAR_GROW cells) -- no forcing there;
 //   K1_NEAR   the near region only (grid over its extent), with forcing.
 // FAR and NEAR together cover the window once.
 enum { K1_ALL = 0, K1_ALLF = 1, K1_FAR = 2, K1_NEAR = 3 };
@@ -403,10 +403,10 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
     const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
     if (MODE == K1_NEAR) {
         // grid over the near region; map to window cells, skip cells outside closed faces
-        if (cx >= box.Bx + 2 * NEAR_MARGIN || cy >= box.By + 2 * NEAR_MARGIN) return;
-        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_MARGIN + cx;
-        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_MARGIN + cy;
-        zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_MARGIN + cz;
+        if (cx >= box.Bx + 2 * NEAR_GROW || cy >= box.By + 2 * NEAR_GROW) return;
+        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_GROW + cx;
+        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_GROW + cy;
+        zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_GROW + cz;
         if (perx) { x += (x < 0) ? g.nx : 0; x -= (x >= g.nx) ? g.nx : 0; } else if (x < 0 || x >= g.nx) return;
         if (pery) { y += (y < 0) ? g.ny : 0; y -= (y >= g.ny) ? g.ny : 0; } else if (y < 0 || y >= g.ny) return;
         if (perz) { zl += (zl < 0) ? g.nz : 0; zl -= (zl >= g.nz) ? g.nz : 0; } else if (zl < 0 || zl >= g.nz) return;
@@ -417,12 +417,12 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
         if (x >= g.nx || y >= g.ny) return;
         if (MODE == K1_FAR) {
             // the z test first: zl is the same for a whole block (plane)
-            const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
-            if ((unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN)) {
-                const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
-                const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
-                if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
-                    (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN))
+            const int rz = rel_axis(zl, S.box_lo[2], S.box_lo_w[2], NEAR_GROW, g.nz, perz);
+            if ((unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_GROW)) {
+                const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_GROW, g.nx, perx);
+                const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_GROW, g.ny, pery);
+                if ((unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_GROW) &&
+                    (unsigned)ry < (unsigned)(box.By + 2 * NEAR_GROW))
                     return;
             }
         }
@@ -737,15 +737,15 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
     int x, y, z[2];
     bool on[2];
     if (MODE == K1_NEAR) {
-        if (cx >= box.Bx + 2 * NEAR_MARGIN || cy >= box.By + 2 * NEAR_MARGIN) return;
-        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_MARGIN + cx;
-        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_MARGIN + cy;
+        if (cx >= box.Bx + 2 * NEAR_GROW || cy >= box.By + 2 * NEAR_GROW) return;
+        x = (perx ? S.box_lo_w[0] : S.box_lo[0]) - NEAR_GROW + cx;
+        y = (pery ? S.box_lo_w[1] : S.box_lo[1]) - NEAR_GROW + cy;
         if (perx) { x += (x < 0) ? g.nx : 0; x -= (x >= g.nx) ? g.nx : 0; } else if (x < 0 || x >= g.nx) return;
         if (pery) { y += (y < 0) ? g.ny : 0; y -= (y >= g.ny) ? g.ny : 0; } else if (y < 0 || y >= g.ny) return;
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
-            int zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_MARGIN + cz + l;
-            on[l] = cz + l < box.Bz + 2 * NEAR_MARGIN;
+            int zl = (perz ? S.box_lo_w[2] : S.box_lo[2]) - NEAR_GROW + cz + l;
+            on[l] = cz + l < box.Bz + 2 * NEAR_GROW;
             if (perz) { zl += (zl < 0) ? g.nz : 0; zl -= (zl >= g.nz) ? g.nz : 0; }
             else on[l] = on[l] && zl >= 0 && zl < g.nz;
             z[l] = on[l] ? zl : 0;
@@ -764,13 +764,13 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
             bool xy_checked = false, in_xy = false;
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                const int rz = rel_axis(z[l], S.box_lo[2], S.box_lo_w[2], NEAR_MARGIN, g.nz, perz);
-                if (on[l] && (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_MARGIN)) {
+                const int rz = rel_axis(z[l], S.box_lo[2], S.box_lo_w[2], NEAR_GROW, g.nz, perz);
+                if (on[l] && (unsigned)rz < (unsigned)(box.Bz + 2 * NEAR_GROW)) {
                     if (!xy_checked) {
-                        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_MARGIN, g.nx, perx);
-                        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_MARGIN, g.ny, pery);
-                        in_xy = (unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_MARGIN) &&
-                                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_MARGIN);
+                        const int rx = rel_axis(x, S.box_lo[0], S.box_lo_w[0], NEAR_GROW, g.nx, perx);
+                        const int ry = rel_axis(y, S.box_lo[1], S.box_lo_w[1], NEAR_GROW, g.ny, pery);
+                        in_xy = (unsigned)rx < (unsigned)(box.Bx + 2 * NEAR_GROW) &&
+                                (unsigned)ry < (unsigned)(box.By + 2 * NEAR_GROW);
                         xy_checked = true;
                     }
                     if (in_xy) on[l] = false;

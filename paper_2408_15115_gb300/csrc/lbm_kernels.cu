@@ -88,7 +88,7 @@ static dim3 cell_grid(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 3) 
 // collide+stream over the window: one thread per pair of planes
 static dim3 pair_grid(const Geom &g) { return dim3((g.nx + 31) / 32, (g.ny + 3) / 4, (g.nz + 1) / 2); }
 static dim3 near_grid(const BoxGeom &b) {
-    const int ex = b.Bx + 2 * NEAR_MARGIN, ey = b.By + 2 * NEAR_MARGIN, ez = b.Bz + 2 * NEAR_MARGIN;
+    const int ex = b.Bx + 2 * NEAR_GROW, ey = b.By + 2 * NEAR_GROW, ez = b.Bz + 2 * NEAR_GROW;
     return dim3((ex + 31) / 32, (ey + 3) / 4, ez);
 }
 

@@ -10,7 +10,7 @@ namespace turret {
 // K2 + binning, one launch.  Blocks [0, nmom): u* and the stress of Eq. 10,
 // sigma = -p I + (1/(2 tau) - 1) P1 with p = c_s^2 (rho - 1), at every
 // support-box cell, from f(t+1) pulled from the post-collision buffer (box
-// cells outside a closed face get zeros).  Blocks [nmom, nmom + ntiles): for
+// cells outside a closed face get zeros; cells no stencil reads are skipped).  Blocks [nmom, nmom + ntiles): for
 // one TILE^3 tile of the box, two lists in marker order (ordered compaction
 // with warp ballots; no atomics): list 0, the markers whose 4x4x4 stencil
 // overlaps the tile (spreading); list 1, those whose stencil overlaps the
@@ -130,6 +130,24 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
     const int bx = (int)(b % box.Bx);
     const int by = (int)((b / box.Bx) % box.By);
     const int bz = (int)(b / ((long long)box.Bx * box.By));
+    {
+        // The moments are read only inside the 4x4x4 stencils of the markers
+        // (u*) and of the offset points X + F_OFFSET n (sigma, p).  Those points
+        // lie at rmin - F_OFFSET <= |P - C| <= rmax + F_OFFSET, and a stencil
+        // cell within 2 cells of P per axis (2 sqrt 3 in all): cells outside
+        // that shell (the corners of the box, the core of a large body) are
+        // never read and are skipped.
+        const BodySlot &S = st->s[slot];
+        const int bb[3] = {bx, by, bz};
+        float d2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float d = (float)bb[a] - ((float)(S.Ci[a] - S.box_lo[a]) + (float)S.Cf[a]);
+            d2 += d * d;
+        }
+        const float reach = F_OFFSET + 3.4641016f + 0.25f;
+        if (d2 > (rmax + reach) * (rmax + reach) || (rmin > reach && d2 < (rmin - reach) * (rmin - reach))) return;
+    }
     int c[3] = {st->s[slot].box_lo[0] + bx, st->s[slot].box_lo[1] + by, st->s[slot].box_lo[2] + bz};
     const int n[3] = {g.nx, g.ny, g.nz};
     const bool per[3] = {g.bc_x == BC_PERIODIC, g.bc_y == BC_PERIODIC, g.bc_bottom == BC_PERIODIC};

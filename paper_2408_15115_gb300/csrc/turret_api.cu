@@ -662,7 +662,7 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     for (int a = 0; a < 3; ++a) {
         if (per[a] && L.box.Bx > n[a])
             return fail(c, TURRET_EINVAL, "support box wider than the window along a periodic axis");
-        if (per[a] && L.box.Bx + 2 * NEAR_MARGIN > n[a]) split = false;
+        if (per[a] && L.box.Bx + 2 * NEAR_GROW > n[a]) split = false;
     }
     // every marker stencil must start inside the window along closed axes
     for (int64_t k = 0; k < nv; ++k)

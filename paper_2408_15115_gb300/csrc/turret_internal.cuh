@@ -311,9 +311,15 @@ inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 // ---------------------------------------------------------------------------
 // Launchers (lbm_kernels.cu).
 // Collide+stream region: all cells, the cells outside the near region around
-// the particle (support box grown by NEAR_MARGIN), or the near region only.
+// the particle, or the near region only.  The near region is the region of
+// the marker stencils (where h_imm can be nonzero) grown by NEAR_MARGIN cells;
+// the support box reaches F_OFFSET cells beyond the marker stencils (the
+// stress is read on the offset surface), so the near region is the support
+// box grown by NEAR_GROW cells.
 enum { REGION_ALL = 0, REGION_FAR = 1, REGION_NEAR = 2 };
 constexpr int NEAR_MARGIN = 2;
+constexpr int NEAR_GROW = NEAR_MARGIN - 2;
+static_assert(F_OFFSET == 2.0f, "the support box grows by F_OFFSET cells per side");
 // slot_out >= 0: the kernel also copies the window slot to slot_out (with no
 // entering plane) for a following step that has no particle update.
 cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,

@@ -43,7 +43,7 @@ def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anc
               ibm_cycles=flags.get("ibm_cycles", 4), kappa=kappa, g=g,
               fixed_position=flags.get("fixed_position", 0),
               uw_bottom=walls[0] if walls else (0, 0, 0), uw_top=walls[1] if walls else (0, 0, 0),
-              reinject=reinject or (0, 0, 0, 0))
+              reinject=reinject or (0, 0, 0, 0), force_eval=flags.get("force_eval", 0))
     if reinject is not None:
         t.set_reinjection(*reinject)
     if walls is not None:

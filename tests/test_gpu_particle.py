@@ -26,14 +26,16 @@ def _compare_state(t, s, tol_f=1e-4, tol_v=1e-5, r0=None):
     return a, b
 
 
-def test_sphere_in_closed_box_100_steps():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_sphere_in_closed_box_100_steps(force_eval):
     # 32x32x64 closed box, sphere d = 8 (252 markers), kappa 2.5, g along -z,
-    # seeded smooth random initial flow of amplitude 0.01
+    # seeded smooth random initial flow of amplitude 0.01; the force from the
+    # stress on the offset surface (0) and at the markers as printed (1)
     shape = (64, 32, 32)
     V, T = I.sphere(5, 8.0)
     fields = I.random_state(shape, u_amp=0.01, rho_amp=0.001, kmax=4, seed=1)
     t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), fields=fields,
-                     particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
+                     flags={"force_eval": force_eval}, particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
     _compare_state(t, s)
     t.step(100)
     s.step(100)
@@ -156,7 +158,7 @@ def _rotlet_ratio(n, d, nu, freq):
 def test_sphere_spin_up_in_shear_flow_follows_feuillebois_lasek():
     # The free-rotation validation of Sec. 3.1: a sphere (d = 16) held at the
     # centre of a 64^3 box whose bottom and top walls move at -U and +U in x
-    # (shear rate G = 2U/H, Re_G = 4 G r^2 / nu = 0.4), released from rest in
+    # (shear rate G = 2U/H, Re_G = 4 G r^2 / nu = 0.8), released from rest in
     # the developed shear at a high density ratio (kappa 100; the paper's run
     # uses 1000): its angular velocity about y rises to the fluid's G/2 along
     # the response of Eq. B.2 to the sudden torque 8 pi nu r^3 (G/2).  The
