@@ -42,7 +42,14 @@ __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
         k1_pair<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else if (R.split) {
-        tile_coords(lb, R.tx, box.Bx + 2 * NEAR_GROW, box.By + 2 * NEAR_GROW, 1, cx, cy, cz);
+        // the near region (a box of some 20-40 cells a side) as one flat range
+        // of cells, x fastest: every thread has a cell but those of the last block
+        const int ex = box.Bx + 2 * NEAR_GROW, ey = box.By + 2 * NEAR_GROW, ez = box.Bz + 2 * NEAR_GROW;
+        const int i = lb * (int)blockDim.x + (int)threadIdx.x;
+        if (i >= ex * ey * ez) return;
+        cx = i % ex;
+        cy = (i / ex) % ey;
+        cz = i / (ex * ey);
         k1_cell<ST, K1_NEAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, cx, cy, cz);
     } else {
         tile_coords(lb, R.tx, g.nx, g.ny, 2, cx, cy, cz);
@@ -50,7 +57,8 @@ __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb
     }
 }
 
-// The near phase is a small launch on the critical path (no register cap).
+// MINB: resident blocks of 256 threads per SM the register budget is sized
+// for (the near phase of a large batch is thousands of blocks: 2).
 template <int PHASE, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *__restrict__ runs,
                                                        const int *__restrict__ prefix, int nruns, int p) {
@@ -149,8 +157,9 @@ int blocks_bulk(const RunDesc &r, int threads) {
 
 int blocks_near(const RunDesc &r, int threads) {
     if (!r.split) return tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2);
-    return tile_blocks(r.box.Bx + 2 * NEAR_GROW, r.box.By + 2 * NEAR_GROW, r.box.Bz + 2 * NEAR_GROW, threads,
-                       r.tx, 1);
+    const long long cells = (long long)(r.box.Bx + 2 * NEAR_GROW) * (r.box.By + 2 * NEAR_GROW) *
+                            (r.box.Bz + 2 * NEAR_GROW);
+    return (int)((cells + threads - 1) / threads);
 }
 
 int blocks_box_moments_bin(const RunDesc &r) {
@@ -161,7 +170,7 @@ cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *
                                  int nblocks, int threads, int minb, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     if (phase == PHASE_NEAR)
-        k_batch_collide<PHASE_NEAR, 1><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
+        k_batch_collide<PHASE_NEAR, 2><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
     else if (minb == 2)
         k_batch_collide<PHASE_BULK, 2><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
     else
