@@ -119,8 +119,11 @@ typedef struct {
 /* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates
  * (window origin included), d = rows d_0, d_1, d_2 of the orientation matrix M,
  * v, w at t - 1/2 (leap-frog), F, T = hydrodynamic force and torque at t
- * (rho_f = 1), L = angular momentum at t - 1/2, origin = global coordinates of
- * window cell (0, 0, 0), step = t, status = latched device status.           */
+ * (rho_f = 1; the stress integrated over the surface that flags.force_eval
+ * selects: by default the surface offset two cells along the normals, torque
+ * about the centre of mass), L = angular momentum at t - 1/2, origin = global
+ * coordinates of window cell (0, 0, 0), step = t, status = latched device
+ * status.                                                                    */
 typedef struct {
     double r[3], d[9], v[3], w[3], F[3], T[3], L[3];
     int64_t origin[3];
@@ -131,7 +134,9 @@ typedef struct {
     double area;     /* surface area, sum of the marker areas dS_k          */
     int32_t kernels_per_step;  /* kernel launches one step() enqueues      */
     int32_t pad0;
-    double Fp[3];    /* pressure part of F: sum_k dS_k (-p(X_k)) n_k, with
+    double Fp[3];    /* pressure part of F: sum_k dA_k (-p(Y_k)) n_k over the
+                      * same surface (Y_k = X_k + 2 n_k, dA_k its areas, by
+                      * default; X_k, dS_k with force_eval 1), with
                       * p = c_s^2 (rho - 1) the isotropic part of Eq. 10;
                       * F - Fp is the viscous (shear) part                 */
 } turret_particle_state;

@@ -219,9 +219,11 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
             int base_rel = (int)fl - 1;         // stencil cells base_rel .. base_rel + 3
             int bv = i_ci[a] + base_rel - i_lo[a];
             float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
-            // a non-finite or out-of-box position must never index memory: park the
-            // stencil at the box origin with zero weights and latch the status
-            if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
+            // a non-finite position, or a stencil reaching the box's outer layer
+            // (never computed by the moments kernel), must never index memory or
+            // read unset moments: park the stencil at the box origin with zero
+            // weights and latch the status
+            if (!isfinite(xr) || bv < 1 || bv > B[a] - 5) {
                 bv = 0;
                 base_rel = i_lo[a] - i_ci[a];
                 w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;
@@ -254,7 +256,7 @@ __device__ __forceinline__ void pm_block(const Geom &g, const BodyConst &bc, con
                 int base_rel = (int)fl - 1;
                 int bv = i_ci[a] + base_rel - i_lo[a];
                 float w4[4] = {peskin_out(1.0f + t), peskin_in(t), peskin_in(1.0f - t), peskin_out(2.0f - t)};
-                if (!isfinite(xr) || bv < 0 || bv > B[a] - 4) {
+                if (!isfinite(xr) || bv < 1 || bv > B[a] - 5) {
                     bv = 0;
                     base_rel = i_lo[a] - i_ci[a];
                     w4[0] = w4[1] = w4[2] = w4[3] = 0.0f;

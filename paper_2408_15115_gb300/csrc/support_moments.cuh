@@ -10,7 +10,8 @@ namespace turret {
 // K2 + binning, one launch.  Blocks [0, nmom): u* and the stress of Eq. 10,
 // sigma = -p I + (1/(2 tau) - 1) P1 with p = c_s^2 (rho - 1), at every
 // support-box cell, from f(t+1) pulled from the post-collision buffer (box
-// cells outside a closed face get zeros; cells no stencil reads are skipped).  Blocks [nmom, nmom + ntiles): for
+// cells outside a closed face get zeros; cells no stencil reads, the outer
+// layer among them, are skipped).  Blocks [nmom, nmom + ntiles): for
 // one TILE^3 tile of the box, two lists in marker order (ordered compaction
 // with warp ballots; no atomics): list 0, the markers whose 4x4x4 stencil
 // overlaps the tile (spreading); list 1, those whose stencil overlaps the
@@ -130,6 +131,13 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
     const int bx = (int)(b % box.Bx);
     const int by = (int)((b / box.Bx) % box.By);
     const int bz = (int)(b / ((long long)box.Bx * box.By));
+    // The outermost layer of the box is never read: along each axis a stencil
+    // of a point P with |P_a - C_a| <= R = rmax + F_OFFSET covers cells
+    // floor(C_a - R) - 1 .. floor(C_a + R) + 2, inside the box's
+    // Ci - rc - 1 .. Ci + rc + 2 (rc = ceil R).  Skipping it keeps every pull
+    // of this kernel inside the box, which is the near region: the moments
+    // then depend on the near launch only, never on the far one.
+    if (bx == 0 || by == 0 || bz == 0 || bx == box.Bx - 1 || by == box.By - 1 || bz == box.Bz - 1) return;
     {
         // The moments are read only inside the 4x4x4 stencils of the markers
         // (u*) and of the offset points X + F_OFFSET n (sigma, p).  Those points

@@ -408,7 +408,9 @@ static bool ibm_layout(const MeshProps &mp, const double *V, int64_t nv, IbmLayo
     }
     L.rmin = rs;
     L.rmax = rb;
-    L.rc = (int)ceil(rb + F_OFFSET + 1e-6);
+    // 1e-3: margin for the FP32 rounding of the marker positions on the GPU
+    // (their stencils must stay off the box's outer layer)
+    L.rc = (int)ceil(rb + F_OFFSET + 1e-3);
     const int B = 2 * L.rc + 6;
     L.box.Bx = L.box.By = L.box.Bz = B;
     L.box.tx = L.box.ty = L.box.tz = (B + TILE - 1) / TILE;
@@ -742,6 +744,11 @@ extern "C" turret_status ibm_load_surface(turret_ctx *c, const double *V, int64_
     CK(cudaMemcpyAsync((void *)c->mk.dSo, c->staging.data() + 7 * nm, nm * 4, cudaMemcpyHostToDevice, c->stream),
        "dSo");
     CK(cudaMemsetAsync(c->ba.h, 0, 3 * (size_t)L.box.nbox * 4, c->stream), "h");
+    // the moments kernel skips the box cells no stencil reads: they keep
+    // finite values (zeros, or an earlier step's moments)
+    CK(cudaMemsetAsync(c->ba.u, 0, 3 * (size_t)L.box.nbox * 4, c->stream), "u");
+    CK(cudaMemsetAsync(c->ba.s, 0, 6 * (size_t)L.box.nbox * 4, c->stream), "sigma");
+    CK(cudaMemsetAsync(c->ba.p, 0, (size_t)L.box.nbox * 4, c->stream), "p");
     // rigid-body state at t: r(t), d = I, v(t-1/2) = v0, w(t-1/2) = w0, L = J w0
     CK(cudaMemcpyAsync(&c->host_state, c->dstate, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream), "state");
     CK(cudaStreamSynchronize(c->stream), "load sync");

@@ -315,7 +315,9 @@ inline size_t storage_bytes(int st) { return st == ST_F32 ? 4 : 2; }
 // the marker stencils (where h_imm can be nonzero) grown by NEAR_MARGIN cells;
 // the support box reaches F_OFFSET cells beyond the marker stencils (the
 // stress is read on the offset surface), so the near region is the support
-// box grown by NEAR_GROW cells.
+// box grown by NEAR_GROW cells.  It holds every cell the support-box moments
+// pull (they skip the box's outer layer), so they wait for the near launch
+// only.
 enum { REGION_ALL = 0, REGION_FAR = 1, REGION_NEAR = 2 };
 constexpr int NEAR_MARGIN = 2;
 constexpr int NEAR_GROW = NEAR_MARGIN - 2;
