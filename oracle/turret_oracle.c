@@ -13,8 +13,10 @@
  *       stream by pull with the boundary conditions of Sec. 2.5;
  *   (2) advance the rigid particle (leap-frog + orientation predictor-corrector,
  *       Sec. 2.3);
- *   (3) evaluate the stress tensor (Eq. 10) at every node, interpolate it at the
- *       markers with the Peskin kernel and sum force / torque (Sec. 2.2 end);
+ *   (3) evaluate the stress tensor (Eq. 10) at every node, interpolate it with
+ *       the Peskin kernel and sum force / torque (Sec. 2.2 end): at the points
+ *       X_k + 2 n_k of the offset surface by default (READING, see
+ *       force_torque), or at the markers as printed;
  *   (4) run the multi-direct-forcing IBM cycles (Sec. 2.2, steps l = 0..4,
  *       n = 4 cycles) and spread h_imm onto the dense Eulerian field.
  * Fields are dense arrays over the whole window; loops are explicit.  The
