@@ -564,8 +564,8 @@ static cudaError_t enqueue_step(turret_ctx *c, int p) {
         if (predict) CE(launch_predict(net, c->dstate, p, c->body.predictor, c->aux));
         CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, p, 1, c->mk, c->aux));
         CE(cudaEventRecord(c->ev_pred, c->aux));
-        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
-                                 c->ba.h, c->box, true, REGION_FAR, c->stream));
+        CE(launch_collide_far(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, c->ba.h,
+                              c->box, c->stream));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_NEAR, c->side));
     } else {
@@ -611,8 +611,8 @@ static cudaError_t enqueue_steps_pipelined(turret_ctx *c, int p0, int K) {
             CE(cudaStreamWaitEvent(c->stream, c->ev_near[q], 0));
             CE(cudaStreamWaitEvent(c->stream, c->ev_pm[q], 0));
         }
-        CE(launch_collide_stream(G, c->storage, c->f[p], c->f[q], c->utop[q], c->utop[p], c->dstate, p, -1, c->ba.h,
-                                 c->box, true, REGION_FAR, c->stream));
+        CE(launch_collide_far(G, c->storage, c->f[p], c->f[q], c->utop[q], c->utop[p], c->dstate, p, c->ba.h, c->box,
+                              c->stream));
         CE(cudaEventRecord(c->ev_far[p], c->stream));
         // aux: prediction and particle/marker update
         if (!first) {

@@ -327,6 +327,12 @@ static_assert(F_OFFSET == 2.0f, "the support box grows by F_OFFSET cells per sid
 cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                   float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
                                   const BoxGeom &box, bool has_box, int region, cudaStream_t s);
+// The far cells of a coupled step (lbm_far.cu): FP32 storage under a register
+// cap that leaves room for the immersed-boundary chain's small blocks; other
+// storages as launch_collide_stream(..., REGION_FAR).
+cudaError_t launch_collide_far(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
+                               float *utop_out, DevState *st, int slot, const float *hbox, const BoxGeom &box,
+                               cudaStream_t s);
 // Re-injection copy of Sec. 2.5 (windows without slide): once the centre's
 // window z in slot `slot` is below trigger, the post-collision planes
 // [zf - below, zf + above) (zf its floor, clipped) move up by target - zf
