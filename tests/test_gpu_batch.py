@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def _runs():
     """Five runs: closed box (FP32), sliding periodic window with pressure top
-    and sponge (FP16), a window too narrow to split far/near cells (BF16), a
+    and sponge (FP16), a periodic window as wide as the support box (BF16), a
     mixed-boundary box with the literal rotation update (FP32), and a sliding
     window in BF16 with stochastically rounded stores."""
     from paper_2408_15115_gb300 import turret as T
