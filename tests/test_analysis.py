@@ -83,3 +83,21 @@ def test_oscillation_frequency_of_a_synthetic_signal():
     f = A.oscillation_frequency(t, x)
     assert abs(f / f0 - 1.0) < 2e-3
     assert abs(A.strouhal(f, 8.0, 0.02) - f * 8.0 / 0.02) < 1e-15
+
+
+def test_fl78_with_a_given_inertia():
+    # `inertia` replaces 2 m r^2 / 5 (a body whose hydrodynamic radius differs
+    # from its mass distribution's): the default value reproduces the default
+    # solution, and the initial angular acceleration is T / I for any I
+    r, nu, kappa, T = 4.0, 0.05, 2.5, 1e-3
+    I0 = 0.4 * kappa * 4.0 / 3.0 * math.pi * r ** 5
+    t = np.array([1e-6, 10.0, 100.0, 1000.0])
+    assert np.allclose(A.fl78_rotation_exact(r, nu, kappa, T, t, inertia=I0),
+                       A.fl78_rotation_exact(r, nu, kappa, T, t), rtol=1e-9, atol=0.0)
+    for I in (0.5 * I0, 3.0 * I0):
+        w = A.fl78_rotation_exact(r, nu, kappa, T, np.array([1e-6]), inertia=I)
+        assert abs(w[0] / (T / I * 1e-6) - 1.0) < 1e-2
+        # the integrator agrees with the exact solution for the same inertia
+        tt, wn = A.fl78_rotation(r, nu, kappa, T, 200.0, 0.25, quad=16, inertia=I)
+        we = A.fl78_rotation_exact(r, nu, kappa, T, tt, inertia=I)
+        assert np.abs(wn - we).max() < 1e-2 * T / (8.0 * math.pi * nu * r ** 3)
