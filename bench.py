@@ -216,7 +216,9 @@ def run_reference(args):
     t0 = time.perf_counter()
     s.step(1)
     t1 = time.perf_counter() - t0
-    warm = min(args.warmup, 1)
+    # the first step counts as warm-up; the rest of the requested warm-up runs
+    # too, bounded to about 30 s of oracle work
+    warm = max(1, min(args.warmup, 1 + int(30.0 / max(t1, 1e-6))))
     if warm > 1:
         s.step(warm - 1)
     k = max(1, min(args.steps, int(budget / max(t1, 1e-6))))
@@ -228,7 +230,7 @@ def run_reference(args):
            "steps": k, "warmup": warm, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
-                      "steps_requested": args.steps},
+                      "steps_requested": args.steps, "warmup_requested": args.warmup},
            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
                             "sample": "%d coupled FP64 oracle steps of the full %s window (of %d requested)" %
                                       (k, cfg["name"], args.steps)},
