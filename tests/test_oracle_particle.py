@@ -373,3 +373,38 @@ def test_shear_spin_up_follows_feuillebois_lasek():
     assert np.abs(w[:, 1] - model).max() < 0.04
     assert abs(w[-1, 1] - 1.0) < 0.02
     assert np.abs(w[:, [0, 2]]).max() < 1e-6
+
+
+def test_window_slide_equals_a_taller_fixed_window():
+    # Reading of Sec. 2.5's re-injection as a sliding window: a ring window
+    # 64 planes high that follows the falling particle must reproduce a fixed
+    # window twice as high, as long as no disturbance has reached the short
+    # window's ends: the plane entering at the bottom is rest fluid there too,
+    # the top plane it drops still holds rest fluid, and the pressure ghost
+    # above rest fluid is rest equilibrium.  Information moves at most one
+    # cell per step and the particle (r = 3) starts 32 cells from either end,
+    # so the two agree for ~24 steps; the particle (v0 = -0.3, kappa 8) falls
+    # 4 cells meanwhile, i.e. 4 slides.  The comparison is independent of the
+    # slide's implementation: the tall window never slides.
+    V, T = I.sphere(4, 6.0)
+    kw = dict(tau=0.8, kappa=8.0, g=(0, 0, -1e-4))
+    a = O.Sim(24, 24, 64, bc_bottom=1, bc_top=2, slide=1, anchor_frac=0.5, **kw)
+    a.init_fields()
+    a.load_particle(V, T, r0=(11.6, 12.3, 32.1), v0=(0, 0, -0.3))
+    b = O.Sim(24, 24, 128, bc_bottom=1, bc_top=2, slide=0, **kw)
+    b.init_fields()
+    b.load_particle(V, T, r0=(11.6, 12.3, 64.1), v0=(0, 0, -0.3))
+    a.step(22)
+    b.step(22)
+    sa, sb = a.state(), b.state()
+    o = int(sa["origin"][2])
+    assert o == -4
+    assert np.abs(sa["r"] - (sb["r"] - np.array([0.0, 0.0, 32.0]))).max() < 1e-12
+    # rounding scales: |v| for v and w (w r ~ v), |F| for F, |F| x 10 cells for T
+    scale = {"v": np.abs(sb["v"]).max(), "w": np.abs(sb["v"]).max(), "F": np.abs(sb["F"]).max(),
+             "T": 10.0 * np.abs(sb["F"]).max()}
+    for key in ("v", "w", "F", "T"):
+        assert np.abs(sa[key] - sb[key]).max() <= 1e-12 * scale[key], key
+    # the short window holds global planes o .. o + 63, i.e. tall planes 32 + o ..
+    ua, ub = a.velocity(), b.velocity()
+    assert np.abs(ua - ub[32 + o: 32 + o + 64]).max() < 1e-12
