@@ -120,3 +120,22 @@ def test_moving_walls_reject_bad_velocities():
         T.Turret(8, 8, 8, 0.1, 1.0, (0, 0, 0), 0, 0, 3, 2, slide=1, anchor_frac=0.3)  # no sliding window
     t.close()
 
+
+
+def test_zero_and_negative_step_counts():
+    # step(0) enqueues nothing; step(-1) is rejected (EINVAL) before any work
+    # and the context stays usable: the next step still matches the oracle
+    from paper_2408_15115_gb300 import turret as T
+    nz, ny, nx = SHAPE
+    t, s = make_pair(nx, ny, nz, 0.05, (0, 0, 0, 0), fields=_fields(SHAPE, 5))
+    before = t.populations().cpu().numpy().copy()
+    t.step(0)
+    assert np.array_equal(t.populations().cpu().numpy(), before)
+    with pytest.raises(T.TurretError) as e:
+        t.step(-1)
+    assert e.value.status == 1
+    assert np.array_equal(t.populations().cpu().numpy(), before)
+    t.step(1)
+    s.fluid_step(1)
+    xi, w = O.lattice()
+    assert np.abs(t.populations().cpu().numpy() - np.moveaxis(s.f() - w, -1, 0)).max() < 2e-9
