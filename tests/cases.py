@@ -63,3 +63,18 @@ def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anc
 
 def sphere_case(n=5, d=8.0):
     return I.sphere(n, d)
+
+
+def k_cyl(lam):
+    """Haberman-Sayre wall factor K(d / D) of the Stokes drag of a sphere on the
+    axis of a long cylinder, from tests/golden/haberman_sayre_1958_wall_factor.txt."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "haberman_sayre_1958_wall_factor.txt")
+    k = 0.0
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            n, c = line.split()
+            k += float(c) * lam ** int(n)
+    return k
+

@@ -6,7 +6,7 @@ import pytest
 from oracle import oracle as O
 from paper_2408_15115_gb300 import inputs as I
 
-from cases import TOL_U_F32, gpu_velocity, make_pair, rel_max
+from cases import TOL_U_F32, gpu_velocity, k_cyl, make_pair, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -217,13 +217,6 @@ def test_reinjection_copy_vs_oracle(storage, tol_f, tol_v):
 
 
 
-def _k_cyl(lam):
-    # Stokes-drag wall correction of a sphere on the axis of a long cylinder,
-    # diameter ratio lam (Haberman & Sayre, 1958)
-    return (1.0 - 2.10444 * lam + 2.08877 * lam ** 3 - 0.94813 * lam ** 5 - 1.372 * lam ** 6
-            + 3.87 * lam ** 8 - 4.19 * lam ** 10)
-
-
 def test_stokes_settling_terminal_velocity_96x96x192():
     # A sphere (d = 8) settling from rest at Re ~ 0.12 in a closed 96 x 96 x 192
     # box, 20000 steps (about 250 settling times (kappa + 1/2) d^2 / (18 nu)):
@@ -242,7 +235,7 @@ def test_stokes_settling_terminal_velocity_96x96x192():
     t.step(1000)
     v2 = t.state()["v"][2]
     t.close()
-    ratio = -v2 / ((kappa - 1.0) * g * d * d / (18.0 * nu) * _k_cyl(d / n))
+    ratio = -v2 / ((kappa - 1.0) * g * d * d / (18.0 * nu) * k_cyl(d / n))
     assert 0.85 < ratio < 1.15, ratio
     assert abs(v2 - v1) < 1e-3 * abs(v2)
 

@@ -3,7 +3,12 @@
 Closed forms: constant-acceleration leap-frog, angular momentum conservation
 of the torque-free update, the exact norm growth and rotation angle of the
 orientation predictor-corrector for a spin about a fixed axis, agreement of
-the printed and the angular-momentum rotation forms for a sphere."""
+the printed and the angular-momentum rotation forms for a sphere.  Surface
+force and torque (Sec. 2.2 end): the divergence theorem for a linear pressure
+field, Stokes settling with the Haberman-Sayre wall factor (tests/golden),
+the exact BBO transient from rest (Eq. B.1), the rotlet of a turned sphere and
+its spin-up in a shear flow (Eq. B.2).  Window slide and re-injection
+(Sec. 2.5): equality with a taller fixed window, and with an unshifted twin."""
 import math
 
 import numpy as np
@@ -11,6 +16,8 @@ import pytest
 
 from oracle import oracle as O
 from paper_2408_15115_gb300 import inputs as I
+
+from cases import k_cyl
 
 
 def _sim_with(verts, tris, kappa=2.0, g=(0, 0, 0), rot_form=0, gravity=0, n=16):
@@ -236,14 +243,6 @@ def test_reinjection_copy_keeps_the_particle_and_its_surroundings():
     assert sa["origin"][2] == sb["origin"][2] - dz
 
 
-def _k_cyl(lam):
-    """Wall correction of the Stokes drag of a sphere on the axis of a long
-    cylinder, diameter ratio lam = d / D (Haberman & Sayre, 1958): the
-    settling speed is v_S K(lam)."""
-    return (1.0 - 2.10444 * lam + 2.08877 * lam ** 3 - 0.94813 * lam ** 5 - 1.372 * lam ** 6
-            + 3.87 * lam ** 8 - 4.19 * lam ** 10)
-
-
 def _stokes_ratio(force_eval, steps):
     n, nz, d, nu, kappa, g = 24, 48, 6.0, 0.3, 2.5, 2e-5
     V, T = I.sphere(4, d)
@@ -253,7 +252,7 @@ def _stokes_ratio(force_eval, steps):
     s.load_particle(V, T, r0=(n / 2 - 0.5, n / 2 - 0.5, 34.0))
     s.step(steps)
     v_s = (kappa - 1.0) * g * d * d / (18.0 * nu)  # Stokes: (kappa - 1) g d^2 / (18 nu)
-    return -s.state()["v"][2] / (v_s * _k_cyl(d / n))
+    return -s.state()["v"][2] / (v_s * k_cyl(d / n))
 
 
 def test_stokes_settling_with_confinement():
