@@ -252,7 +252,8 @@ def _stokes_ratio(force_eval, steps):
     s.load_particle(V, T, r0=(n / 2 - 0.5, n / 2 - 0.5, 34.0))
     s.step(steps)
     v_s = (kappa - 1.0) * g * d * d / (18.0 * nu)  # Stokes: (kappa - 1) g d^2 / (18 nu)
-    return -s.state()["v"][2] / (v_s * k_cyl(d / n))
+    st = s.state()
+    return -st["v"][2] / (v_s * k_cyl(d / n)), st["Fp"][2] / st["F"][2]
 
 
 def test_stokes_settling_with_confinement():
@@ -268,9 +269,14 @@ def test_stokes_settling_with_confinement():
     # taken at the markers themselves (force_eval 1), where the interpolation
     # stencil straddles the interface, under-estimates the drag and settles
     # more than twice too fast.
-    r = _stokes_ratio(0, 200)
+    r, share = _stokes_ratio(0, 200)
     assert 0.85 < r < 1.15, r
-    assert _stokes_ratio(1, 100) > 2.0
+    # Stokes flow past a sphere: the pressure force on any concentric sphere is
+    # 2 pi mu a U, one third of the drag, whatever its radius (so on the offset
+    # surface too); the duct's return flow adds to it (0.415 here, 0.379 in a
+    # 32-wide duct): a dropped or doubled pressure part fails the band
+    assert 1.0 / 3.0 < share < 0.45, share
+    assert _stokes_ratio(1, 100)[0] > 2.0
 
 
 def test_settling_from_rest_follows_bbo():
