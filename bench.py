@@ -1,22 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the Turret hot path on one GB300 (or N replicas, one per GPU).
 
-Workload: the 96 x 96 x 192 sliding turret window with a prolate spheroid
-16:8:8 (812 surface markers) tilted 30 degrees, nu = 0.02, kappa = 2, Re ~ 10,
-FP32 population storage.  One step = collide+stream over every window cell,
+Headline workload: the 256 x 256 x 512 sliding turret window (33.5 M cells)
+with the spherical-harmonic irregular particle of volume-equivalent diameter
+32 (6252 surface markers), Re ~ 1000 (nu = 6.4e-4), kappa = 2, FP32
+population storage, the paper's predictor, the force taken on the offset
+surface (force_eval 0).  One step = collide+stream over every window cell,
 particle update, window slide, stress/velocity on the support box, surface
-force/torque and four IBM cycles (one replay of the step's CUDA graph).
+force/torque and four IBM cycles (replays of the step's CUDA graphs).
 
 Printed JSON line (rank 0):
   value     window cells x steps / s over the timed steps, in GLUPS (all ranks)
-  roofline  the fused collide+stream kernel timed alone: 216 algorithmic
-            bytes per cell / its mean launch time, against the measured HBM
-            copy bandwidth
+  roofline  the step's own collide+stream launches (far cells + near region)
+            timed alone: algorithmic bytes (216 per cell in FP32, 108 with
+            16-bit storage) / mean time, against the measured HBM copy
+            bandwidth; whole_step_frac: the same bytes over the whole step
   e2e       the same metric through the public C ABI from host data:
             context + surface upload + steps with a particle-state read
             after every step
+  windows   the other windows and storage formats (the 96 x 96 x 192 prolate
+            window, the 192 x 192 x 384 irregular window, FP16 / BF16 /
+            BF16 with stochastic rounding), each with its step rate and its
+            collide+stream roofline fraction
   cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the
-            same workload
+            same workload (and one thread on the 96 x 96 x 192 window)
 --impl reference times the oracle alone as the reference arm.
 """
 import argparse
@@ -34,23 +41,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS & %HBM roofline per RR-LBM+IBM step; mixed/batched vs FP32 at ≤1% drag err"
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}
-K1_PROFILE = os.path.join(ROOT, "profiles", "k_collide_stream_prolate_96x96x192.md")
-K1_SOURCES = [os.path.join(ROOT, "paper_2408_15115_gb300", "csrc", f) for f in ("lbm_cell.cuh", "lbm_kernels.cu")]
+K1_PROFILE = os.path.join(ROOT, "profiles", "k_collide_stream_far_f32_irregular_256x256x512.md")
+K1_SOURCES = [os.path.join(ROOT, "paper_2408_15115_gb300", "csrc", f)
+              for f in ("lbm_cell.cuh", "lbm_kernels.cu", "lbm_far.cu", "turret_internal.cuh")]
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="prolate_turret")
-    p.add_argument("--storage", default=None)
+    p.add_argument("--workload", default="irregular_large")
+    p.add_argument("--storage", default="f32")
+    p.add_argument("--no-windows", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
     p.add_argument("--ensemble-steps", type=int, default=100)
     p.add_argument("--no-learned", action="store_true")
-    p.add_argument("--case", default=None, choices=["mlp_train", "ensemble_steps"],
+    p.add_argument("--case", default=None, choices=["mlp_train", "ensemble_steps", "window"],
                    help="run one small workload for a profiler capture instead of the benchmark")
     p.add_argument("--learned-steps", type=int, default=6000)
     return p.parse_args()
@@ -174,11 +183,30 @@ def profile_traffic():
     return float(vals["dram_bytes_per_launch"])
 
 
-def oracle_sample(cfg, budget_s=15.0, max_steps=None):
+def workload(name, storage):
+    from paper_2408_15115_gb300 import configs
+    fn = configs.WORKLOADS[name]
+    return fn(storage=storage) if name != "sphere_box" else fn()
+
+
+ORACLE_BYTES_PER_CELL = 600  # dense FP64 fields of the oracle: 2 x 27 populations, h, u, sigma, scratch
+
+
+def oracle_fits(cells):
+    """Whether the oracle's dense fields for `cells` cells fit in half of the
+    host memory available now."""
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        return True
+    return ORACLE_BYTES_PER_CELL * cells < 0.5 * avail
+
+
+def oracle_sample(cfg, budget_s=15.0, max_steps=None, threads=None):
     """Time the FP64 oracle on the workload: coupled steps of the full window
     from rest; returns (cells*steps/s in GLUPS, threads, steps, seconds)."""
     from oracle import oracle as O
-    O.set_threads(os.cpu_count() or 1)
+    O.set_threads(threads or os.cpu_count() or 1)
     bc = cfg["bc"]
     s = O.Sim(cfg["nx"], cfg["ny"], cfg["nz"], 3 * cfg["nu"] + 0.5, *bc, sponge=cfg["sponge"], slide=cfg["slide"],
               anchor_frac=cfg["anchor"], kappa=cfg["kappa"], g=cfg["g"])
@@ -194,15 +222,21 @@ def oracle_sample(cfg, budget_s=15.0, max_steps=None):
     t0 = time.perf_counter()
     s.step(n)
     dt = time.perf_counter() - t0
-    return cells * n / dt / 1e9, O.get_threads(), n, dt
+    used = O.get_threads()
+    del s
+    return cells * n / dt / 1e9, used, n, dt
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    from paper_2408_15115_gb300 import configs
-    cfg = configs.WORKLOADS[args.workload]()
+    cfg = workload(args.workload, args.storage)
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    if not oracle_fits(cells):
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle's dense fields (%.1f GB) exceed half of "
+                          "this host's available memory" % (ORACLE_BYTES_PER_CELL * cells / 1e9)}))
+        return
     # each reference step is one coupled oracle step of the full window; the
     # count is capped so the whole arm ends within a few minutes
     budget = 150.0
@@ -230,12 +264,88 @@ def run_reference(args):
            "steps": k, "warmup": warm, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
+                      "force_eval": 0, "predictor": "paper",
                       "steps_requested": args.steps, "warmup_requested": args.warmup},
            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
                             "sample": "%d coupled FP64 oracle steps of the full %s window (of %d requested)" %
                                       (k, cfg["name"], args.steps)},
            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+def time_window(cfg, dev, K, W, kernel_launches, peaks, events=None):
+    """Step rate of one window and its collide+stream launches alone.
+
+    The coupled step is replayed K times after W warm-up steps (CUDA events on
+    the context's stream); then the step's own collide+stream launches
+    (lbm_fluid_step: far cells + near region) `kernel_launches` times.
+    Returns the rates, the roofline fractions and the state."""
+    import torch
+
+    from paper_2408_15115_gb300 import configs
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    t = configs.make_turret(cfg, device=dev, flags=cfg.get("flags"))
+    t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
+    st = t.stream
+    t.step(max(W, 8) if K >= 8 else W)  # capture the one-step and the 8-step graphs before timing
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if events is not None:
+        events["before"]()
+    ev0.record(st)
+    t.step(K)
+    ev1.record(st)
+    torch.cuda.synchronize(dev)
+    if events is not None:
+        events["after"]()
+    ms = ev0.elapsed_time(ev1)
+    state = t.state()
+    t.fluid_step(3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    t.fluid_step(kernel_launches)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    k_ms = e0.elapsed_time(e1) / kernel_launches
+    t.close()
+    bpc = BYTES_PER_CELL[cfg["storage"]]
+    hbm = peaks["hbm_gbs"]
+    return {"ms": ms, "state": state, "cells": cells,
+            "glups": cells * K / (ms / 1e3) / 1e9, "us_per_step": 1e3 * ms / K,
+            "kernel_us": 1e3 * k_ms, "kernel_glups": cells / (k_ms / 1e3) / 1e9, "bytes_per_cell": bpc,
+            "kernel_gbs": bpc * cells / (k_ms / 1e3) / 1e9,
+            "kernel_frac": bpc * cells / (k_ms / 1e3) / 1e9 / hbm,
+            "whole_step_frac": bpc * cells / (ms / K / 1e3) / 1e9 / hbm}
+
+
+def windows_leg(dev, peaks, W, f32_us):
+    """Every window size and storage format: the step rate and the
+    collide+stream roofline fraction (bytes per cell of the storage format)."""
+    legs = [("prolate_turret", "f32", None, 4000, 1000),
+            ("irregular_turret", "f32", None, 1000, 300), ("irregular_turret", "f16", None, 1000, 300),
+            ("irregular_turret", "bf16", None, 1000, 300),
+            ("irregular_turret", "bf16", {"stochastic_rounding": 1}, 1000, 300),
+            ("irregular_large", "f16", None, 400, 100), ("irregular_large", "bf16", None, 400, 100),
+            ("irregular_large", "bf16", {"stochastic_rounding": 1}, 400, 100)]
+    out = {}
+    for name, storage, flags, K, KL in legs:
+        cfg = workload(name, storage)
+        if flags:
+            cfg["flags"] = flags
+        r = time_window(cfg, dev, K, W, KL, peaks)
+        key = "%s/%s%s" % (cfg["name"], storage, "_sr" if flags else "")
+        e = {k: r[k] for k in ("glups", "us_per_step", "kernel_us", "kernel_glups", "bytes_per_cell", "kernel_gbs",
+                               "kernel_frac", "whole_step_frac")}
+        e["steps"] = K
+        e["particle_steps_per_s"] = K / (r["ms"] / 1e3)
+        if storage == "f32":
+            f32_us[cfg["name"]] = (r["us_per_step"], r["kernel_us"])
+        elif cfg["name"] in f32_us:
+            e["step_speedup_vs_f32"] = f32_us[cfg["name"]][0] / r["us_per_step"]
+            e["kernel_speedup_vs_f32"] = f32_us[cfg["name"]][1] / r["kernel_us"]
+        out[key] = e
+    return out
 
 
 def ensemble_leg(dev, K, W, tile_cache):
@@ -440,58 +550,34 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    cfg = configs.WORKLOADS[args.workload]() if args.storage is None else \
-        configs.WORKLOADS[args.workload](storage=args.storage)
+    cfg = workload(args.workload, args.storage)
     cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
     K, W = args.steps, args.warmup
+    peaks, peak_kind = measured_peaks()
 
     ranks = Ranks(world, dev)
     barrier = ranks.barrier
     max_over_ranks = ranks.max
 
-    # ---- device-resident timed steps ------------------------------------
-    t = configs.make_turret(cfg, device=dev)
-    t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
-    st = t.stream
-    t.step(W)  # first calls capture the two per-parity step graphs
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize(dev)
-    with Clocks(local) as clk:
-        ev0.record(st)
-        t.step(K)
-        ev1.record(st)
-        torch.cuda.synchronize(dev)
-    barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    # ---- device-resident timed steps, then the step's collide+stream alone --
+    clk = Clocks(local)
+    r = time_window(cfg, dev, K, W, max(100, min(K, 1000)), peaks,
+                    events={"before": lambda: (barrier(), torch.cuda.synchronize(dev), clk.__enter__()),
+                            "after": lambda: (clk.__exit__(), barrier())})
+    ms = max_over_ranks(r["ms"])
     clocks = clk.summary()
-    state = t.state()
-    kps = state["kernels_per_step"]
+    kps = r["state"]["kernels_per_step"]
     value = whole_job_glups(world, cells, K, ms)
-
-    # ---- the fused collide+stream kernel alone (roofline) -------------------
-    t.fluid_step(W)
-    torch.cuda.synchronize(dev)
-    k1_launches = max(200, min(K, 5000))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    t.fluid_step(k1_launches)
-    e1.record(st)
-    torch.cuda.synchronize(dev)
-    k1_ms = e0.elapsed_time(e1) / k1_launches
     bpc = BYTES_PER_CELL[cfg["storage"]]
-    peaks, peak_kind = measured_peaks()
-    achieved = bpc * cells / (k1_ms / 1e3) / 1e9
-    traffic = profile_traffic()
-    t.close()
-    del t
+    k_us = r["kernel_us"]
+    achieved = bpc * cells / (k_us / 1e6) / 1e9
+    traffic = profile_traffic() if cfg["storage"] == "f32" else None
 
     # ---- end to end through the C ABI from host data ----------------------
     from paper_2408_15115_gb300 import turret as T
     V = np.ascontiguousarray(cfg["verts"])
     Tr = np.ascontiguousarray(cfg["tris"], dtype=np.int32)
-    K2 = K
+    K2 = max(K, 100)
     torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
@@ -503,7 +589,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     t2.close()
-    e2e = {"value": world * cells * K2 / e2e_s / 1e9, "unit": "GLUPS",
+    del t2
+    e2e = {"value": world * cells * K2 / e2e_s / 1e9, "unit": "GLUPS", "steps": K2,
            "h2d_bytes_per_step": (V.nbytes + Tr.nbytes) / K2,
            "d2h_bytes_per_step": __import__("ctypes").sizeof(T.ParticleState),
            "includes": "context creation, surface upload, and a particle-state read after every step"}
@@ -515,25 +602,36 @@ def run_ours(args):
            "dtype": cfg["storage"], "data": "synthetic",
            "config": {"workload": cfg["name"], "cells": cells, "markers": int(cfg["verts"].shape[0]),
                       "storage": cfg["storage"], "nu": cfg["nu"], "kappa": cfg["kappa"], "g": cfg["g"][2],
+                      "predictor": "paper", "force_eval": 0, "ibm_cycles": 4,
                       "l2": "inputs larger than L2 (two population buffers of %d MiB)" % (cells * bpc // 2 // 2**20),
                       "replicas": world},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                        "kernel": "k_collide_stream", "algorithmic_bytes_per_launch": bpc * cells,
-                        "us_per_launch": 1e3 * k1_ms, "glups_kernel": cells / (k1_ms / 1e3) / 1e9,
-                        "peak_kind": peak_kind,
+                        "kernel": "k_collide_stream_far_f32 + near-region k_collide_stream" if cfg["storage"] == "f32"
+                        else "k_collide_stream (far cells + near region)",
+                        "algorithmic_bytes_per_launch": bpc * cells,
+                        "us_per_launch": k_us, "glups_kernel": cells / (k_us / 1e6) / 1e9,
+                        "peak_kind": peak_kind, "particle_steps_per_s": K / (ms / 1e3),
                         "whole_step_frac": (bpc * cells / (ms / K / 1e3) / 1e9) / peaks["hbm_gbs"]},
            "e2e": e2e, "gpu_launches": kps * K, "clocks": clocks}
+    if world == 1 and not args.no_windows:
+        out["windows"] = windows_leg(dev, peaks, W, {cfg["name"]: (r["us_per_step"], k_us)}
+                                     if cfg["storage"] == "f32" else {})
     if world == 1 and not args.no_ensemble:
         out["ensemble"] = ensemble_leg(dev, args.ensemble_steps, max(W, 3),
                                        os.path.join(ROOT, "paper_2408_15115_gb300", "_build", "tiles.json"))
     if world == 1 and not args.no_learned:
         out["learned_predictor"] = learned_leg(dev, args.learned_steps)
-    if world == 1 and not args.no_cpu_baseline:
-        v, cores, n, dt = oracle_sample(cfg)
+    if world == 1 and not args.no_cpu_baseline and oracle_fits(cells):
+        v, cores, n, dt = oracle_sample(cfg, budget_s=12.0)
+        v1, c1, n1, dt1 = oracle_sample(workload("prolate_turret", "f32"), budget_s=10.0, threads=1)
         out["cpu_baseline"] = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                                "sample": "%d coupled FP64 oracle steps of the full %s window from rest (%.1f s)" %
-                                         (n, cfg["name"], dt)}
+                                         (n, cfg["name"], dt),
+                               "single_thread": {"value": v1, "unit": "GLUPS", "cores": c1,
+                                                 "sample": "%d coupled FP64 oracle steps of the full "
+                                                           "prolate_96x96x192_turret window, one thread (%.1f s)"
+                                                           % (n1, dt1)}}
     print(json.dumps(out))
 
 
@@ -541,7 +639,9 @@ def run_case(args):
     """Small fixed workloads for profiler captures: `mlp_train`, three BF16
     training steps of the surrogate network at batch 4096; `ensemble_steps`,
     the 64-run ensemble as one batch with tiles (128, 2, 32), 5 + 20 steps in
-    FP32 then 5 + 20 with storage alternating FP32/FP16."""
+    FP32 then 5 + 20 with storage alternating FP32/FP16; `window`, the
+    --workload window in --storage, --steps coupled steps without graphs
+    (one launch per kernel) then three launches of its collide+stream alone."""
     import numpy as np
     import torch
 
@@ -562,6 +662,15 @@ def run_case(args):
             net.train_step(x, y, want_loss=False)
         torch.cuda.synchronize(dev)
         net.close()
+    elif args.case == "window":
+        cfg = workload(args.workload, args.storage)
+        t = configs.make_turret(cfg, device=dev, flags={"no_graph": 1})
+        t.load_surface(cfg["verts"], cfg["tris"], cfg["r0"])
+        t.step(args.steps)
+        t.fluid_step(3)
+        torch.cuda.synchronize(dev)
+        out.update(workload=cfg["name"], storage=args.storage, steps=args.steps, status=t.state()["status"])
+        t.close()
     else:
         for storage in ("f32", "alternate"):
             runs = configs.load_ensemble(configs.ensemble(64, seed=4, storage=storage), device=dev)

@@ -202,7 +202,10 @@ TURRET_API turret_status step(turret_ctx *c, int64_t n);
 
 /* Advances the fluid alone by n collide+stream steps (Eq. 7 / Eq. 15 with
  * h_imm held at its current value; the particle does not move).  Launches
- * only the fused collide+stream kernel; asynchronous.                      */
+ * only the fused collide+stream kernels a coupled step uses for the window:
+ * with a particle whose support box is small against the window, the
+ * far-cell launch and then the near-region launch, in order on the context's
+ * stream; otherwise one launch over the whole window.  Asynchronous.      */
 TURRET_API turret_status lbm_fluid_step(turret_ctx *c, int64_t n);
 
 /* Copies the particle state to the host (waits for the stream); returns the
@@ -251,7 +254,10 @@ TURRET_API turret_status ibm_spread(const float *X, const float *h, const float 
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make it before any stream capture.  All calls on a device
  * share the one array: calls whose GPU work overlaps (other streams, other
- * threads) race and must be serialised by the caller.  Waits for `stream`.  */
+ * threads) race and must be serialised by the caller.  The looked-up address
+ * is kept for the life of the process: after cudaDeviceReset on a device
+ * (which unloads the library's device image there) this entry point must not
+ * be called on that device again.  Waits for `stream`.                      */
 TURRET_API turret_status ibm_spread_noalloc(const float *X, const float *h, const float *dS, int64_t n_markers,
                                             int32_t nx, int32_t ny, int32_t nz, float *field, void *stream);
 

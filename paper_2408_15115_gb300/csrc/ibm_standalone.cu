@@ -198,6 +198,9 @@ extern "C" turret_status ibm_spread(const float *X, const float *h, const float 
 // exits.  The address of the array is a device address only on the device:
 // host code obtains it once per device with cudaGetSymbolAddress (on the
 // first call made with that device current) and passes it to the kernels.
+// The cached address is valid for as long as the device's primary context
+// lives: cudaDeviceReset unloads the image, and the entry point must not be
+// called on that device afterwards.
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 constexpr int NOALLOC_MAX_DEVICES = 64;

@@ -937,12 +937,25 @@ extern "C" turret_status turret_query_predictor(turret_ctx *c, turret_predictor_
 extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
     if (!c) return fail(c, TURRET_EINVAL, "NULL context");
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
+    // the kernels of the coupled step's collide+stream (far cells, then the
+    // near region, which also carries the body slot), so that timing this
+    // call times the step's own bulk launch
+    const bool split = c->has_particle && c->split && c->reinject.trigger == 0;
     for (int64_t k = 0; k < n; ++k) {
         const int p = (int)(c->step & 1);
-        CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
-                                 1 - p, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle, REGION_ALL,
-                                 c->stream),
-           "fluid step");
+        if (split) {
+            CK(launch_collide_far(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
+                                  c->ba.h, c->box, c->stream),
+               "fluid step (far cells)");
+            CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
+                                     p, 1 - p, c->ba.h, c->box, true, REGION_NEAR, c->stream),
+               "fluid step (near region)");
+        } else {
+            CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
+                                     p, 1 - p, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle,
+                                     REGION_ALL, c->stream),
+               "fluid step");
+        }
         c->step++;
     }
     return TURRET_OK;
@@ -1016,15 +1029,20 @@ struct CkptHeader {
 };
 const char CKPT_MAGIC[8] = {'T', 'U', 'R', 'R', 'E', 'T', 'C', 'K'};
 
+// Every flag but no_graph (which changes how a step is launched, not what it
+// computes) must match for a bitwise resume.
+bool same_flags(const turret_flags &a, const turret_flags &b) {
+    turret_flags x = a, y = b;
+    x.no_graph = y.no_graph = 0;
+    x.pad0 = y.pad0 = 0;
+    return memcmp(&x, &y, sizeof(turret_flags)) == 0;
+}
+
 bool same_config(const CkptHeader &h, const turret_ctx *c) {
     return h.storage == c->storage && h.has_particle == (c->has_particle ? 1 : 0) &&
            h.nm == (c->has_particle ? c->nm : 0) && memcmp(&h.win, &c->win, sizeof(turret_window)) == 0 &&
-           h.flags.force_scheme == c->flags.force_scheme && h.flags.rot_form == c->flags.rot_form &&
-           h.flags.gravity == c->flags.gravity && h.flags.ibm_cycles == c->flags.ibm_cycles &&
-           h.flags.stochastic_rounding == c->flags.stochastic_rounding &&
-           h.flags.force_eval == c->flags.force_eval && h.nu == c->nu &&
-           h.kappa == c->kappa && h.g[0] == c->g[0] && h.g[1] == c->g[1] && h.g[2] == c->g[2] &&
-           h.nbox == (c->has_particle ? c->box.nbox : 0);
+           same_flags(h.flags, c->flags) && h.nu == c->nu && h.kappa == c->kappa && h.g[0] == c->g[0] &&
+           h.g[1] == c->g[1] && h.g[2] == c->g[2] && h.nbox == (c->has_particle ? c->box.nbox : 0);
 }
 
 void fill_header(CkptHeader &h, const turret_ctx *c) {
@@ -1091,7 +1109,11 @@ extern "C" turret_status turret_load(turret_ctx *c, const char *path) {
         fclose(fp);
         return fail(c, TURRET_EINVAL, "not a checkpoint of this format");
     }
-    if (!same_config(h, c) || h.bytes_pop != want.bytes_pop || h.bytes_state != want.bytes_state) {
+    // every part is copied into the caller's workspace: all five sizes must be
+    // the ones this context carves, or a foreign file would overwrite its
+    // neighbours
+    if (!same_config(h, c) || h.bytes_pop != want.bytes_pop || h.bytes_utop != want.bytes_utop ||
+        h.bytes_state != want.bytes_state || h.bytes_h != want.bytes_h || h.bytes_hl != want.bytes_hl) {
         fclose(fp);
         return fail(c, TURRET_ESTATE, "checkpoint of a differently configured context");
     }

@@ -51,3 +51,47 @@ def test_mismatched_checkpoints_are_refused(tmp_path):
     with pytest.raises(T.TurretError) as e:
         a.load(str(junk))
     assert e.value.status == 1
+
+
+def test_tampered_sizes_and_flags_are_refused(tmp_path):
+    # a checkpoint whose part sizes do not match the context, or whose
+    # rigid-body flags differ, is refused before anything is copied into the
+    # workspace; the context stays usable
+    import ctypes as C
+
+    from paper_2408_15115_gb300 import turret as T
+
+    class Header(C.Structure):
+        _fields_ = [("magic", C.c_char * 8), ("version", C.c_int32), ("storage", C.c_int32),
+                    ("has_particle", C.c_int32), ("nm", C.c_int32), ("win", T.Window), ("flags", T.Flags),
+                    ("nu", C.c_double), ("kappa", C.c_double), ("g", C.c_double * 3), ("step", C.c_int64),
+                    ("nbox", C.c_int64), ("bytes_pop", C.c_int64), ("bytes_utop", C.c_int64),
+                    ("bytes_state", C.c_int64), ("bytes_h", C.c_int64), ("bytes_hl", C.c_int64)]
+
+    path = tmp_path / "ck.bin"
+    a = _make("f32")
+    a.step(3)
+    a.save(str(path))
+    raw = path.read_bytes()
+    h0 = Header.from_buffer_copy(raw[:C.sizeof(Header)])
+    assert h0.magic == b"TURRETCK" and h0.nm == a.state()["n_markers"]
+    for field in ("bytes_utop", "bytes_h", "bytes_hl"):
+        h = Header.from_buffer_copy(raw[:C.sizeof(Header)])
+        setattr(h, field, getattr(h, field) + 4096)
+        bad = tmp_path / ("bad_%s.bin" % field)
+        bad.write_bytes(bytes(h) + raw[C.sizeof(Header):] + b"\0" * 4096)
+        with pytest.raises(T.TurretError) as e:
+            a.load(str(bad))
+        assert e.value.status == 4, field
+    c = configs.ensemble_member("prolate", 10.0, 30.0, (64, 64, 64), "f32", seed=3)
+    for flag in ("renorm_orientation", "fixed_position"):
+        b = configs.make_turret(c, flags={flag: 1})
+        b.load_surface(c["verts"], c["tris"], c["r0"], v0=(0, 0, -0.05))
+        with pytest.raises(T.TurretError) as e:
+            b.load(str(path))
+        assert e.value.status == 4, flag
+        b.close()
+    # the refused loads left the context as it was
+    before = a.state()
+    a.step(2)
+    assert a.state()["step"] == before["step"] + 2

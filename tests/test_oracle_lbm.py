@@ -301,6 +301,50 @@ def test_sponge_raises_viscosity_towards_the_top():
     assert np.array_equal(s1.velocity(), s2.velocity())
 
 
+def test_sponge_profile_from_steady_shear_with_variable_viscosity():
+    # The sponge of Sec. 2.5 raises the viscosity linearly to tau = 1 on the
+    # top plane.  Steady plane Couette flow transmits one shear stress S through
+    # every plane, so the velocity gradient is S / nu(z): the viscosity of each
+    # plane is read off the steady profile, with S taken in the uniform part
+    # below the sponge where nu = nu0 is known.  Every sponge plane must carry
+    # nu(z) = (tau(z) - 1/2) / 3 with tau rising by (1 - tau0) / L per plane
+    # from tau0 just below the sponge to 1 on the top plane (one plane of
+    # shift is a 3-4 % change here; the centred differences of a smooth
+    # profile are good to ~1e-3).
+    nz, L, tau0, U = 40, 16, 0.8, 0.02
+    z = np.arange(nz)
+    # start near the steady state: u rising as the running integral of a rough
+    # 1/nu guess (the linear profile below, doubled viscosity at the top);
+    # what is left decays as exp(-nu0 (pi / H)^2 t), e^-7 over the run
+    guess = 1.0 / np.where(z < nz - L, 1.0, 1.0 + (z - (nz - L) + 1) / L)
+    prof = np.cumsum(guess) - 0.5 * guess
+    u = np.zeros((nz, 2, 2, 3))
+    u[..., 0] = (-U + 2 * U * prof / (prof[-1] + 0.5 * guess[-1]))[:, None, None]
+    threads = O.get_threads()
+    O.set_threads(2)
+    try:
+        s = O.Sim(2, 2, nz, tau0, bc_bottom=3, bc_top=3, sponge=L, uw_bottom=(-U, 0, 0), uw_top=(U, 0, 0))
+        s.init_fields(None, u)
+        s.fluid_step(12000)
+        ux = s.velocity()[:, 0, 0, 0]
+    finally:
+        O.set_threads(threads)
+    du = np.gradient(ux)  # centred differences inside
+    nu0 = (tau0 - 0.5) / 3.0
+    S = nu0 * np.mean(du[4:nz - L - 4])
+    assert np.abs(du[4:nz - L - 4] * nu0 / S - 1.0).max() < 1e-4  # uniform stress below the sponge
+    zs = np.arange(nz - L + 1, nz - 1)  # sponge planes with both neighbours inside it
+    tau = tau0 + (1.0 - tau0) * (zs - (nz - L) + 1) / L
+    nu_expected = (tau - 0.5) / 3.0
+    nu_measured = S / du[zs]
+    print("nu measured / expected per sponge plane:", np.round(nu_measured / nu_expected, 5))
+    assert np.abs(nu_measured / nu_expected - 1.0).max() < 1e-2, nu_measured / nu_expected
+    # and the profile is not a plane off either way
+    for shift in (-1, 1):
+        tau_s = tau0 + (1.0 - tau0) * (zs + shift - (nz - L) + 1) / L
+        assert np.abs(nu_measured / ((tau_s - 0.5) / 3.0) - 1.0).max() > 2e-2
+
+
 @pytest.mark.parametrize("u_bottom,u_top", [((0.0, 0.0, 0.0), (0.02, 0.0, 0.0)), ((0.0, -0.015, 0.0), (0.0, 0.015, 0.0))])
 def test_moving_walls_couette_profile_and_shear_stress(u_bottom, u_top):
     # steady plane Couette flow between halfway-bounce-back walls at z = -1/2

@@ -144,3 +144,46 @@ def test_features_are_frame_invariant():
     b = M.features(M0 @ Rl.T, Rl @ v, Rl @ w, Fh @ Rl.T, Th @ Rl.T)
     assert np.allclose(a[4:], b[4:], atol=1e-12)
     assert a.shape == (34,)
+
+
+def test_features_and_target_of_a_hand_worked_history():
+    # Five consecutive trajectory records (t-3 .. t+1) of a body turned by
+    # -90 degrees about z: its axes in the lab frame are d0 = (0, 1, 0),
+    # d1 = (-1, 0, 0), d2 = (0, 0, 1), so M (rows d_i) takes lab (a, b, c) to
+    # body (b, -a, c), and its quaternion is (cos 45, 0, 0, -sin 45).
+    # Forces newest first F(t) = (0,0,4), F(t-1) = (0,0,2), F(t-2) = (3,0,0),
+    # F(t-3) = (0,1,0): s_F = 4; torques T(t) = (1,0,0), T(t-1) = (0,2,0),
+    # T(t-2) = 0, T(t-3) = (0,0,-1): s_T = 2.  v = (1,2,3), w = (0,0,0.5).
+    # Next level F(t+1) = (1,0,7), T(t+1) = (2,-2,0): departures from linear
+    # extrapolation (0,0,6) and (2,-2,0) are (1,0,1) and 0.  Every number
+    # below is worked out by hand from these.
+    d = np.array([0.0, 1.0, 0.0, -1.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    F = [(0, 1, 0), (3, 0, 0), (0, 0, 2), (0, 0, 4), (1, 0, 7)]   # t-3 .. t+1
+    T = [(0, 0, -1), (0, 0, 0), (0, 2, 0), (1, 0, 0), (2, -2, 0)]
+    log = np.zeros((5, M.LOG_REC))
+    for j in range(5):
+        log[j, 0:9] = d
+        log[j, 9:12] = (1, 2, 3)
+        log[j, 12:15] = (0, 0, 0.5)
+        log[j, 15:18] = F[j]
+        log[j, 18:21] = T[j]
+        log[j, 21] = 100 + j
+    x, y = M.samples(log)
+    assert x.shape == (1, 34) and y.shape == (1, 6)
+    r = math.sqrt(0.5)
+    want_x = np.array([r, 0, 0, -r,                  # quaternion, w >= 0
+                       2, -1, 3,                      # M v
+                       0, 0, 0.5,                     # M w
+                       0, 0, 1, 0, -0.5, 0,           # h = 0: M F(t) / 4, M T(t) / 2
+                       0, 0, 0.5, 1, 0, 0,            # h = 1
+                       0, -0.75, 0, 0, 0, 0,          # h = 2
+                       0.25, 0, 0, 0, 0, -0.5])       # h = 3
+    want_y = np.array([0, -0.25, 0.25, 0, 0, 0])
+    assert np.abs(x[0] - want_x).max() < 1e-15, x[0] - want_x
+    assert np.abs(y[0] - want_y).max() < 1e-15, y[0] - want_y
+    # the network's output y turned back into a lab-frame prediction
+    Fh = [np.array(F[3 - h], float) for h in range(4)]
+    Th = [np.array(T[3 - h], float) for h in range(4)]
+    Fp, Tp = M.prediction(d.reshape(3, 3), Fh, Th, want_y)
+    assert np.abs(Fp - np.array([1, 0, 7])).max() < 1e-15
+    assert np.abs(Tp - np.array([2, -2, 0])).max() < 1e-15
