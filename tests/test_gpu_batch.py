@@ -156,13 +156,16 @@ def test_batch_rejects_invalid_run_lists():
     b.close()
 
 
-def test_batched_run_matches_oracle():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_batched_run_matches_oracle(force_eval):
     # the closed-box sphere of the FP32 parity suite, advanced inside a batch
-    # with a second (FP16) run, against the FP64 oracle after 100 steps
+    # with a second (FP16) run, against the FP64 oracle after 100 steps; the
+    # force on the offset surface (0) or at the markers as printed (1)
     from paper_2408_15115_gb300 import turret as T
     V, Tr = I.sphere(5, 8.0)
     fields = I.random_state((64, 32, 32), u_amp=0.01, rho_amp=0.001, kmax=4, seed=1)
     t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), fields=fields,
+                     flags={"force_eval": force_eval},
                      particle=(V, Tr, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
     other = _runs()[1]
     b = T.Batch([other, t])

@@ -45,12 +45,15 @@ def test_sphere_in_closed_box_100_steps(force_eval):
     _compare_state(t, s)
 
 
-def test_tilted_ellipsoid_rotation_and_torque():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_tilted_ellipsoid_rotation_and_torque(force_eval):
+    # force_eval 0: stress on the offset surface; 1: at the markers, as printed
     shape = (48, 40, 40)
     V, T = I.ellipsoid(6, (6.0, 3.0, 3.0))
     V = I.rotate(I.rotate(V, "x", 30.0), "z", 20.0)
     fields = I.random_state(shape, u_amp=0.02, rho_amp=0.001, kmax=3, seed=2)
     t, s = make_pair(40, 40, 48, 0.04, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=6, fields=fields,
+                     flags={"force_eval": force_eval},
                      particle=(V, T, (19.7, 20.2, 22.3), (0, 0, -0.01), (0.002, -0.001, 0.003)))
     t.step(100)
     s.step(100)
@@ -62,11 +65,13 @@ def test_tilted_ellipsoid_rotation_and_torque():
     assert rel_max(u, s.velocity()) < TOL_U_F32
 
 
-def test_sliding_window_follows_particle():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_sliding_window_follows_particle(force_eval):
     # falling sphere in a periodic column with the ring window; several slides
     shape = (48, 24, 24)
     V, T = I.sphere(4, 6.0)
     t, s = make_pair(24, 24, 48, 0.05, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -2e-4), sponge=6, slide=1, anchor=0.5,
+                     flags={"force_eval": force_eval},
                      particle=(V, T, (11.6, 12.3, 24.1), (0, 0, -0.15), (0, 0, 0)))
     t.step(80)
     s.step(80)
@@ -119,7 +124,8 @@ def test_stokes_settling_cfg1_drag_and_velocity_vs_oracle():
     assert abs(a["v"][2] - b["v"][2]) / abs(b["v"][2]) < 5e-3
 
 
-def test_held_sphere_in_shear_flow_vs_oracle():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_held_sphere_in_shear_flow_vs_oracle(force_eval):
     # a sphere with its centre held in the shear between two moving walls:
     # force, torque and the spin-up of its rotation against the oracle
     n = 24
@@ -127,7 +133,8 @@ def test_held_sphere_in_shear_flow_vs_oracle():
     z = np.arange(n) + 0.5
     u = np.zeros((n, n, n, 3))
     u[..., 0] = (-0.01 + 0.02 * z / n)[:, None, None]
-    t, s = make_pair(n, n, n, 0.1, (0, 0, 3, 3), kappa=2.0, g=(0, 0, -1e-5), flags={"fixed_position": 1},
+    t, s = make_pair(n, n, n, 0.1, (0, 0, 3, 3), kappa=2.0, g=(0, 0, -1e-5),
+                     flags={"fixed_position": 1, "force_eval": force_eval},
                      fields=(None, u), walls=((-0.01, 0, 0), (0.01, 0, 0)),
                      particle=(V, T, (11.6, 11.3, 11.8), (0, 0, 0), (0, 0, 0)))
     t.step(60)
@@ -200,13 +207,15 @@ def test_sphere_spin_up_in_shear_flow_follows_feuillebois_lasek():
     assert np.abs(w[:, [0, 2]]).max() < 1e-3     # about y only
 
 
+@pytest.mark.parametrize("force_eval", [0, 1])
 @pytest.mark.parametrize("storage,tol_f,tol_v", [("f32", 1e-4, 1e-5), ("f16", 2e-2, 2e-3)])
-def test_reinjection_copy_vs_oracle(storage, tol_f, tol_v):
+def test_reinjection_copy_vs_oracle(storage, tol_f, tol_v, force_eval):
     # the re-injection copy of Sec. 2.5: a falling sphere crosses the trigger
     # plane and the block of fluid around it is copied up with it; the window
     # origin, the trajectory and the force against the oracle through the event
     V, T = I.icosphere(3, 3.0)
     t, s = make_pair(20, 20, 64, 0.1, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=4, storage=storage,
+                     flags={"force_eval": force_eval},
                      reinject=(22, 40, 12, 14), particle=(V, T, (9.8, 10.1, 22.5), (0, 0, -0.05), (0, 0, 0)))
     t.step(60)
     s.step(60)

@@ -31,16 +31,19 @@ def _rel(a, b):
 
 
 @pytest.mark.slow
-def test_sphere_box_storage_vs_oracle():
+@pytest.mark.parametrize("force_eval", [0, 1])
+def test_sphere_box_storage_vs_oracle(force_eval):
     # the 32x32x64 closed-box sphere (d = 8, 252 markers) from rest, 400 steps:
     # time-averaged drag and settling velocity over the second half, and the
-    # fall distance, for every storage type against the FP64 oracle
+    # fall distance, for every storage type against the FP64 oracle; the force
+    # on the offset surface (0) or at the markers as printed (1)
     V, T = I.sphere(5, 8.0)
     O.set_threads(0)
     hist = {}
     sim = None
     for st in ("f32", "f16", "bf16"):
         t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), storage=st,
+                         flags={"force_eval": force_eval},
                          particle=(V, T, (15.5, 15.5, 44.0), (0, 0, 0), (0, 0, 0)))
         hist[st] = _history(t.step, t.state, 400, 10)
         if sim is None:
