@@ -102,7 +102,12 @@ typedef struct {
  *               round each stored value up or down with probability equal to
  *               its distance from the other neighbour (unbiased rounding),
  *               the random bits a hash of (element, time step): results stay
- *               deterministic.  0: round to nearest even.                   */
+ *               deterministic.  0: round to nearest even.
+ *   staged_loads 1 (FP16 / BF16 storage): the bulk collide+stream moves its
+ *               tiles' sources and results through shared memory with bulk
+ *               tensor copies (a producer warp and four computing warps per
+ *               block) instead of plain 2-byte global loads and stores (0, the
+ *               default, measured faster).  Results are identical.          */
 typedef struct {
     int32_t force_scheme;
     int32_t rot_form;
@@ -113,7 +118,7 @@ typedef struct {
     int32_t stochastic_rounding;
     int32_t fixed_position;
     int32_t force_eval;
-    int32_t pad0;
+    int32_t staged_loads;
 } turret_flags;
 
 /* Particle state (Sec. 2.3): r = centre of mass in global lattice coordinates

@@ -318,6 +318,35 @@ __device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, con
         }
 }
 
+// The same for the unforced equilibrium, whose factor c = K is a power of two:
+// K W_i (rho E + drho) = fma(E, K W_i rho, K W_i drho) bit for bit (scaling by
+// a power of two is exact), one operation less per population.
+template <bool SC>
+__device__ __forceinline__ void set_eq_dev_pow2(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
+                                                float drho, float K, float s[27]) {
+    float r[4], d[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const float c = K * (float)(1 << (2 * w));  // K W for W = 1, 4, 16, 64
+        r[w] = c * rho;
+        d[w] = c * drho;
+    }
+    float sxy[9];
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = fmaf(fx.a[ex], fy.a[ey], fx.a[ex] + fy.a[ey]);
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = k + 9 * ez;
+            const int lw = SC ? 0 : (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
+            const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
+            s[i] = fmaf(E, r[lw], d[lw]);
+        }
+}
+
 // Post-collision populations of one cell in the storage domain of ST
 // (FP32: s_i = 216 (f*_i - w_i)).  forced: equilibrium part
 // (1-w) f0(u) + w f0(u + tau h) (scheme 0) or f0(u + tau h) (scheme 1), both
@@ -329,7 +358,7 @@ __device__ __forceinline__ void collide_factored(const Macro &M, float omega, fl
     constexpr float K = Codec<ST>::K;
     const AxisF fx = axis_of<SC>(M.ux), fy = axis_of<SC>(M.uy), fz = axis_of<SC>(M.uz);
     if (!forced) {
-        add_eq_dev<SC>(fx, fy, fz, M.rho, M.drho, K, s, true);
+        set_eq_dev_pow2<SC>(fx, fy, fz, M.rho, M.drho, K, s);
     } else {
         const AxisF vx = axis_of<SC>(M.ux + tau * hx), vy = axis_of<SC>(M.uy + tau * hy),
                     vz = axis_of<SC>(M.uz + tau * hz);
@@ -606,6 +635,35 @@ __device__ __forceinline__ void add_eq_dev2(const AxisF2 &fx, const AxisF2 &fy, 
         }
 }
 
+// set_eq_dev_pow2 for a cell pair: the unforced equilibrium deviation
+// K W_i (rho E + drho) as fma(E, K W_i rho, K W_i drho), bit for bit equal.
+template <bool SC>
+__device__ __forceinline__ void set_eq_dev2_pow2(const AxisF2 &fx, const AxisF2 &fy, const AxisF2 &fz, f2 rho,
+                                                 f2 drho, float K, f2 s[27]) {
+    f2 r[4], d[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if (SC && w > 0) continue;
+        const f2 c = F2(K * (float)(1 << (2 * w)));  // K W for W = 1, 4, 16, 64
+        r[w] = pmul(c, rho);
+        d[w] = pmul(c, drho);
+    }
+    f2 sxy[9];
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = pfma(fx.a[ex], fy.a[ey], padd(fx.a[ex], fy.a[ey]));
+#pragma unroll
+    for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int i = k + 9 * ez;
+            const int lw = SC ? 0 : (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
+            const f2 E = pfma(sxy[k], fz.a[ez], padd(sxy[k], fz.a[ez]));
+            s[i] = pfma(E, r[lw], d[lw]);
+        }
+}
+
 // Post-collision populations of two cells in the storage domain of ST.
 // forced lanes take (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
 // f0(u + tau h) (scheme 1); other lanes f0(u) (their h is zero, and their
@@ -617,7 +675,7 @@ __device__ __forceinline__ void collide_pair(const Macro2 &M, f2 omega, f2 tau, 
     constexpr float K = Codec<ST>::K;
     const AxisF2 fx = axis_of2<SC>(M.ux), fy = axis_of2<SC>(M.uy), fz = axis_of2<SC>(M.uz);
     if (!anyforced) {
-        add_eq_dev2<SC>(fx, fy, fz, M.rho, M.drho, F2(K), s, true);
+        set_eq_dev2_pow2<SC>(fx, fy, fz, M.rho, M.drho, K, s);
     } else {
         const AxisF2 vx = axis_of2<SC>(pfma(tau, h[0], M.ux)), vy = axis_of2<SC>(pfma(tau, h[1], M.uy)),
                      vz = axis_of2<SC>(pfma(tau, h[2], M.uz));
@@ -724,6 +782,12 @@ __device__ __forceinline__ void pull27x2(const Geom &g, const typename Codec<ST>
     for (int i = 0; i < 27; ++i) q[i].y = qa[i];
 }
 
+template <int ST, int MODE, bool STORE = true>
+__device__ __forceinline__ void k1_pair_collide_store(const Geom &g, typename Codec<ST>::T *__restrict__ dst,
+                                                      float *__restrict__ utop_out, const BodySlot &S,
+                                                      const float *__restrict__ hbox, const BoxGeom &box, int x,
+                                                      int y, const int z[2], const bool on[2], f2 q[27]);
+
 // K1 for the cell pair (cx, cy, cz), (cx, cy, cz + 1): window coordinates for
 // ALL / ALLF / FAR, near-region coordinates for NEAR; cells outside the
 // window (or the mode's region) are not written, and a pair with none
@@ -782,9 +846,22 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
     // a missing cell shares its partner's plane (loads in bounds, no store)
     if (!on[0]) z[0] = z[1];
     if (!on[1]) z[1] = z[0];
-    const int ring = S.ring;
     f2 q[27];
-    pull27x2<ST>(g, src, x, y, z[0], z[1], ring, S.reseed, utop_in, q);
+    pull27x2<ST>(g, src, x, y, z[0], z[1], S.ring, S.reseed, utop_in, q);
+    k1_pair_collide_store<ST, MODE>(g, dst, utop_out, S, hbox, box, x, y, z, on, q);
+}
+
+// The part of K1 after the pull, for a pair of cells (x, y, z[0]), (x, y,
+// z[1]) whose pre-collision values are q (shared by the plain pull above and
+// the staged kernels, so both run identical arithmetic).  STORE false: leave
+// the post-collision values in q (storage domain) for the caller to store.
+template <int ST, int MODE, bool STORE>
+__device__ __forceinline__ void k1_pair_collide_store(const Geom &g, typename Codec<ST>::T *__restrict__ dst,
+                                                      float *__restrict__ utop_out, const BodySlot &S,
+                                                      const float *__restrict__ hbox, const BoxGeom &box, int x,
+                                                      int y, const int z[2], const bool on[2], f2 q[27]) {
+    const bool perx = g.bc_x == BC_PERIODIC, pery = g.bc_y == BC_PERIODIC, perz = g.bc_bottom == BC_PERIODIC;
+    const int ring = S.ring;
     const f2 omega = make_float2(omega_of(g, z[0]), omega_of(g, z[1]));
     bool forced[2] = {false, false};
     f2 h[3] = {F2(0.0f), F2(0.0f), F2(0.0f)};
@@ -818,6 +895,7 @@ __device__ __forceinline__ void k1_pair(const Geom &g, const typename Codec<ST>:
         }
     collide_pair<ST>(M, omega, tau, forced[0] || forced[1], forced[0], forced[1], h,
                      (MODE == K1_ALLF || MODE == K1_NEAR) ? g.force_scheme : 0, q);
+    if (!STORE) return;  // the caller stores q itself
     const int ncell = (int)g.ncell;
     const int oa = zphys(z[0], ring, g.nz) * (int)g.plane, ob = zphys(z[1], ring, g.nz) * (int)g.plane;
     typename Codec<ST>::T *d = dst + (y * g.nx + x);

@@ -23,7 +23,10 @@ __global__ void __maxnreg__(120) k_collide_stream_far_f32(Geom g, const float *_
 
 cudaError_t launch_collide_far(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                float *utop_out, DevState *st, int slot, const float *hbox, const BoxGeom &box,
-                               cudaStream_t s) {
+                               cudaStream_t s, const CUtensorMap *lmap, const CUtensorMap *smap) {
+    if (storage != ST_F32 && lmap && smap)
+        return launch_collide_staged(g, storage, *lmap, *smap, src, dst, utop_in, utop_out, st, slot, -1, hbox, box,
+                                     REGION_FAR, s);
     if (storage != ST_F32)
         return launch_collide_stream(g, storage, src, dst, utop_in, utop_out, st, slot, -1, hbox, box, true,
                                      REGION_FAR, s);

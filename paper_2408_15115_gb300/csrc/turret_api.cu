@@ -194,6 +194,12 @@ extern "C" turret_status lbm_init(turret_ctx **out, const turret_window *win, tu
     }
     G.tau_z = tau_z;
     G.omega_z = tau_z + win->nz;
+    // 16-bit storage on a window the staged collide+stream tiles: tensor maps
+    // of both population buffers (plain loads if the driver refuses them)
+    c->staged = staged_eligible(G, c->storage) && prepare_staged();
+    for (int k = 0; k < 2 && c->staged; ++k)
+        c->staged = encode_population_map(&c->lmap[k], c->f[k], G, true) &&
+                    encode_population_map(&c->smap[k], c->f[k], G, false);
     c->has_particle = false;
     c->split = false;
     c->step = 0;
@@ -532,12 +538,31 @@ static cudaError_t enqueue_coupling(turret_ctx *c, const void *fsrc, const float
     return cudaSuccess;
 }
 
+// Tensor maps of the staged 16-bit collide+stream from f[p] into f[1 - p]
+// (source boxes of f[p], destination boxes of f[1 - p]) when the window can be
+// staged and flags.staged_loads asks for it, else null (plain loads and stores).
+static const CUtensorMap *src_map(const turret_ctx *c, int p) {
+    return (c->staged && c->flags.staged_loads) ? &c->lmap[p] : nullptr;
+}
+static const CUtensorMap *dst_map(const turret_ctx *c, int p) {
+    return (c->staged && c->flags.staged_loads) ? &c->smap[1 - p] : nullptr;
+}
+
+// Collide+stream over the whole window without forcing (no particle), the
+// window slot carried to slot_out.
+static cudaError_t collide_window(const turret_ctx *c, int p, cudaStream_t s) {
+    if (src_map(c, p))
+        return launch_collide_staged(c->geom, c->storage, *src_map(c, p), *dst_map(c, p), c->f[p], c->f[1 - p],
+                                     c->utop[1 - p], c->utop[p], c->dstate, p, 1 - p, nullptr, c->box, REGION_ALL,
+                                     s);
+    return launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
+                                 1 - p, nullptr, c->box, false, REGION_ALL, s);
+}
+
 // One step from parity p: f[p] holds f*(t-1), f[1-p] receives f*(t).
 static cudaError_t enqueue_step(turret_ctx *c, int p) {
     const Geom &G = c->geom;
-    if (!c->has_particle)
-        return launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
-                                     1 - p, nullptr, c->box, false, REGION_ALL, c->stream);
+    if (!c->has_particle) return collide_window(c, p, c->stream);
     if (c->reinject.trigger > 0) {
         // re-injection copy: collide+stream over the whole window, the particle
         // and marker update, the copy of f*(t) (the buffer of f*(t-1) stages
@@ -565,7 +590,7 @@ static cudaError_t enqueue_step(turret_ctx *c, int p) {
         CE(launch_particle_markers(c->geom, c->body, c->box, c->dstate, p, 1, c->mk, c->aux));
         CE(cudaEventRecord(c->ev_pred, c->aux));
         CE(launch_collide_far(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, c->ba.h,
-                              c->box, c->stream));
+                              c->box, c->stream, src_map(c, p), dst_map(c, p)));
         CE(launch_collide_stream(G, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p, -1,
                                  c->ba.h, c->box, true, REGION_NEAR, c->side));
     } else {
@@ -612,7 +637,7 @@ static cudaError_t enqueue_steps_pipelined(turret_ctx *c, int p0, int K) {
             CE(cudaStreamWaitEvent(c->stream, c->ev_pm[q], 0));
         }
         CE(launch_collide_far(G, c->storage, c->f[p], c->f[q], c->utop[q], c->utop[p], c->dstate, p, c->ba.h, c->box,
-                              c->stream));
+                              c->stream, src_map(c, p), dst_map(c, p)));
         CE(cudaEventRecord(c->ev_far[p], c->stream));
         // aux: prediction and particle/marker update
         if (!first) {
@@ -801,8 +826,9 @@ static void set_node_priorities(const turret_ctx *c, cudaGraph_t gr) {
         if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp;
         if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
-        const bool is_bulk = kp.gridDim.x == bulk.x && kp.gridDim.y == bulk.y && kp.gridDim.z == bulk.z &&
-                             kp.blockDim.x == 32 && kp.blockDim.y == 4;
+        const bool is_bulk = (kp.gridDim.x == bulk.x && kp.gridDim.y == bulk.y && kp.gridDim.z == bulk.z &&
+                              kp.blockDim.x == 32 && kp.blockDim.y == 4) ||
+                             is_staged_kernel(kp.func);
         cudaLaunchAttributeValue v;
         memset(&v, 0, sizeof v);
         v.priority = is_bulk ? lo : hi;
@@ -945,15 +971,16 @@ extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
         const int p = (int)(c->step & 1);
         if (split) {
             CK(launch_collide_far(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
-                                  c->ba.h, c->box, c->stream),
+                                  c->ba.h, c->box, c->stream, src_map(c, p), dst_map(c, p)),
                "fluid step (far cells)");
             CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
                                      p, 1 - p, c->ba.h, c->box, true, REGION_NEAR, c->stream),
                "fluid step (near region)");
+        } else if (!c->has_particle) {
+            CK(collide_window(c, p, c->stream), "fluid step");
         } else {
             CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
-                                     p, 1 - p, c->has_particle ? c->ba.h : nullptr, c->box, c->has_particle,
-                                     REGION_ALL, c->stream),
+                                     p, 1 - p, c->ba.h, c->box, true, REGION_ALL, c->stream),
                "fluid step");
         }
         c->step++;
@@ -996,6 +1023,7 @@ extern "C" turret_status query_particle_state(turret_ctx *c, turret_particle_sta
     if (D.status == STAT_DOMAIN) return fail(c, TURRET_EDOMAIN, "a marker stencil left the window");
     if (D.status == STAT_DIVERGED) return fail(c, TURRET_EDIVERGED, "non-finite force or torque");
     if (D.status == STAT_OVERFLOW) return fail(c, TURRET_EOVERFLOW, "a support tile overflowed its marker list");
+    if (D.status == STAT_TIMEOUT) return fail(c, TURRET_ETIMEOUT, "a staged copy did not complete in time");
     return TURRET_OK;
 }
 
@@ -1029,12 +1057,12 @@ struct CkptHeader {
 };
 const char CKPT_MAGIC[8] = {'T', 'U', 'R', 'R', 'E', 'T', 'C', 'K'};
 
-// Every flag but no_graph (which changes how a step is launched, not what it
-// computes) must match for a bitwise resume.
+// Every flag but no_graph and staged_loads (which change how a step is
+// launched, not what it computes) must match for a bitwise resume.
 bool same_flags(const turret_flags &a, const turret_flags &b) {
     turret_flags x = a, y = b;
     x.no_graph = y.no_graph = 0;
-    x.pad0 = y.pad0 = 0;
+    x.staged_loads = y.staged_loads = 0;
     return memcmp(&x, &y, sizeof(turret_flags)) == 0;
 }
 

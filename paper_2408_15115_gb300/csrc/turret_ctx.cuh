@@ -1,6 +1,7 @@
 // turret_ctx.cuh -- the context behind the opaque turret_ctx handle of the
 // C ABI (include/turret.h), shared by the single-run and the batch entry points.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -23,6 +24,11 @@ struct turret_ctx {
     turret::Geom geom;
     // fluid workspace
     void *f[2];
+    // tensor maps of the two population buffers for the staged 16-bit
+    // collide+stream: source boxes (lmap) and destination boxes (smap);
+    // staged: they were encoded
+    CUtensorMap lmap[2], smap[2];
+    bool staged;
     float *utop[2];
     turret::DevState *dstate;
     // particle

@@ -14,6 +14,7 @@
 //                 u*, sigma and the spread force h as SoA float planes.
 //   markers     : SoA arrays, one entry per surface vertex.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -23,7 +24,7 @@ namespace turret {
 
 enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_PRESSURE = 2, BC_MOVING = 3 };
 enum { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
-enum { STAT_OK = 0, STAT_DIVERGED = 5, STAT_DOMAIN = 7, STAT_OVERFLOW = 8 };
+enum { STAT_OK = 0, STAT_DIVERGED = 5, STAT_TIMEOUT = 6, STAT_DOMAIN = 7, STAT_OVERFLOW = 8 };
 
 // Rigid body + window state, FP64 (Sec. 2.3), resident in device memory.
 // Everything that changes from one time level to the next lives in two slots
@@ -328,11 +329,26 @@ cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, v
                                   float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
                                   const BoxGeom &box, bool has_box, int region, cudaStream_t s);
 // The far cells of a coupled step (lbm_far.cu): FP32 storage under a register
-// cap that leaves room for the immersed-boundary chain's small blocks; other
-// storages as launch_collide_stream(..., REGION_FAR).
+// cap that leaves room for the immersed-boundary chain's small blocks; 16-bit
+// storages with their sources staged in shared memory when `map` (the tensor
+// map of src, see encode_population_map) is given, else as
+// launch_collide_stream(..., REGION_FAR).
 cudaError_t launch_collide_far(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                float *utop_out, DevState *st, int slot, const float *hbox, const BoxGeom &box,
-                               cudaStream_t s);
+                               cudaStream_t s, const CUtensorMap *lmap = nullptr, const CUtensorMap *smap = nullptr);
+// 16-bit collide+stream with sources and results staged in shared memory by
+// bulk tensor copies (lbm_staged.cu): REGION_FAR or REGION_ALL without
+// forcing.  staged_eligible: the window's tiling allows it; lmap / smap: the
+// source (box 48 x 4 x 2 x 3) and destination (box 32 x 4 x 2 x 27) tensor
+// maps of the buffers (encode_population_map); prepare_staged once per device.
+bool staged_eligible(const Geom &g, int storage);
+bool encode_population_map(CUtensorMap *map, const void *buf, const Geom &g, bool source);
+bool prepare_staged();
+bool is_staged_kernel(const void *fn);
+cudaError_t launch_collide_staged(const Geom &g, int storage, const CUtensorMap &lmap, const CUtensorMap &smap,
+                                  const void *src, void *dst, const float *utop_in, float *utop_out, DevState *st,
+                                  int slot, int slot_out, const float *hbox, const BoxGeom &box, int region,
+                                  cudaStream_t s);
 // Re-injection copy of Sec. 2.5 (windows without slide): once the centre's
 // window z in slot `slot` is below trigger, the post-collision planes
 // [zf - below, zf + above) (zf its floor, clipped) move up by target - zf

@@ -30,7 +30,7 @@ class Flags(C.Structure):
     _fields_ = [("force_scheme", C.c_int32), ("rot_form", C.c_int32), ("gravity", C.c_int32),
                 ("renorm_orientation", C.c_int32), ("ibm_cycles", C.c_int32), ("no_graph", C.c_int32),
                 ("stochastic_rounding", C.c_int32), ("fixed_position", C.c_int32), ("force_eval", C.c_int32),
-                ("pad0", C.c_int32)]
+                ("staged_loads", C.c_int32)]
 
 
 class ParticleState(C.Structure):
