@@ -605,6 +605,13 @@ struct turret_mlp {
     float *part;  // split-K partial sums [MAX_SLICES][128][128]
     double *loss;
     long long adam_step;
+    // the training step (standardise, forward, backward, AdamW, BF16 copy) as
+    // one CUDA graph per batch size; between replays only the input pointers
+    // and the optimiser's scalars change, in the three nodes that take them
+    cudaGraph_t train_graph;  // kept: its nodes address the instantiated graph's nodes
+    cudaGraphExec_t train_exec;
+    int train_n;
+    cudaGraphNode_t node_x, node_y, node_adam;
     std::string err;
 };
 
@@ -647,6 +654,7 @@ void carve_mlp(MCarver &cv, int cap, turret_mlp *m) {
 
 turret_status mfail(turret_mlp *m, turret_status s, const std::string &msg) {
     if (m) m->err = msg; else g_mlp_err = msg;
+    if (s == TURRET_ECUDA) cudaGetLastError();  // a non-sticky error must not surface in later launches
     return s;
 }
 
@@ -772,6 +780,9 @@ extern "C" turret_status mlp_init(turret_mlp **out, int32_t batch_cap, int32_t p
     m->precision = precision;
     m->stream = (cudaStream_t)stream;
     m->adam_step = 0;
+    m->train_exec = nullptr;
+    m->train_graph = nullptr;
+    m->train_n = 0;
     MCarver cv{(char *)ws, 0};
     carve_mlp(cv, batch_cap, m);
     std::vector<float> norm(2 * (MLP_IN + MLP_OUT));
@@ -864,6 +875,102 @@ extern "C" turret_status mlp_loss_grad(turret_mlp *m, const float *x, const floa
     return TURRET_OK;
 }
 
+namespace {
+// One training step's kernels on the network's stream.
+cudaError_t enqueue_train(turret_mlp *m, const float *x, const float *y, int n, const turret_adamw *opt, float bc1,
+                          float bc2) {
+    cudaError_t e = prepare(m, x, y, n);
+    if (e == cudaSuccess) e = forward(m, n);
+    if (e == cudaSuccess) e = backward(m, n);
+    if (e != cudaSuccess) return e;
+    k_adamw<<<(MLP_NPARAM + 255) / 256, 256, 0, m->stream>>>(m->P, m->G, m->Mm, m->Vv, opt->lr, opt->beta1,
+                                                             opt->beta2, opt->eps, opt->weight_decay, bc1, bc2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return refresh(m);
+}
+
+void drop_train_graph(turret_mlp *m) {
+    if (m->train_exec) cudaGraphExecDestroy(m->train_exec);
+    if (m->train_graph) cudaGraphDestroy(m->train_graph);
+    m->train_exec = nullptr;
+    m->train_graph = nullptr;
+    m->train_n = 0;
+}
+
+// Capture the training step for batch size n and find the nodes whose
+// arguments change between steps (the two standardisations, AdamW).
+cudaError_t capture_train(turret_mlp *m, const float *x, const float *y, int n, const turret_adamw *opt) {
+    drop_train_graph(m);
+    cudaGraph_t gr;
+    cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = enqueue_train(m, x, y, n, opt, 1.0f, 1.0f);
+    cudaError_t e2 = cudaStreamEndCapture(m->stream, &gr);
+    if (e != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(gr);
+        return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    size_t nn = 0;
+    m->node_x = m->node_y = m->node_adam = nullptr;
+    e = cudaGraphGetNodes(gr, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(gr, nodes.data(), &nn);
+    for (size_t k = 0; k < nn && e == cudaSuccess; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if ((e = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
+        if (kp.func == (void *)k_adamw) m->node_adam = nodes[k];
+        if (kp.func == (void *)k_standardise) {
+            const int d = *static_cast<const int *>(kp.kernelParams[2]);
+            (d == MLP_IN ? m->node_x : m->node_y) = nodes[k];
+        }
+    }
+    if (e == cudaSuccess && (!m->node_x || !m->node_y || !m->node_adam)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->train_exec, gr, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        m->train_exec = nullptr;
+        return e;
+    }
+    m->train_graph = gr;
+    m->train_n = n;
+    return cudaSuccess;
+}
+
+// Replay the captured step with this step's inputs and optimiser scalars.
+cudaError_t replay_train(turret_mlp *m, const float *x, const float *y, int n, const turret_adamw *opt, float bc1,
+                         float bc2) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    int d = MLP_IN;
+    const float *mean = m->norm, *stdv = m->norm + MLP_IN;
+    float *outp = m->X0;
+    void *args_x[6] = {&x, &n, &d, &mean, &stdv, &outp};
+    kp.func = (void *)k_standardise;
+    kp.gridDim = dim3((n * MLP_IN + 255) / 256);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args_x;
+    cudaError_t e = cudaGraphExecKernelNodeSetParams(m->train_exec, m->node_x, &kp);
+    if (e != cudaSuccess) return e;
+    int dy = MLP_OUT;
+    const float *meany = m->norm + 2 * MLP_IN, *stdy = m->norm + 2 * MLP_IN + MLP_OUT;
+    float *outy = m->T;
+    void *args_y[6] = {&y, &n, &dy, &meany, &stdy, &outy};
+    kp.gridDim = dim3((n * MLP_OUT + 255) / 256);
+    kp.kernelParams = args_y;
+    if ((e = cudaGraphExecKernelNodeSetParams(m->train_exec, m->node_y, &kp)) != cudaSuccess) return e;
+    float lr = opt->lr, b1 = opt->beta1, b2 = opt->beta2, eps = opt->eps, wd = opt->weight_decay;
+    void *args_a[11] = {&m->P, &m->G, &m->Mm, &m->Vv, &lr, &b1, &b2, &eps, &wd, &bc1, &bc2};
+    kp.func = (void *)k_adamw;
+    kp.gridDim = dim3((MLP_NPARAM + 255) / 256);
+    kp.kernelParams = args_a;
+    if ((e = cudaGraphExecKernelNodeSetParams(m->train_exec, m->node_adam, &kp)) != cudaSuccess) return e;
+    return cudaGraphLaunch(m->train_exec, m->stream);
+}
+}  // namespace
+
 extern "C" turret_status mlp_train_step(turret_mlp *m, const float *x, const float *y, int32_t n,
                                         const turret_adamw *opt, float *loss) {
     if (!m || !x || !y || !opt) return mfail(m, TURRET_EINVAL, "NULL argument");
@@ -871,16 +978,16 @@ extern "C" turret_status mlp_train_step(turret_mlp *m, const float *x, const flo
     if (!(opt->lr >= 0.0f) || !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
         !(opt->eps > 0.0f) || !(opt->weight_decay >= 0.0f))
         return mfail(m, TURRET_EINVAL, "invalid optimiser settings");
-    MK(prepare(m, x, y, n), "standardise");
-    MK(forward(m, n), "forward");
-    MK(backward(m, n), "backward");
     m->adam_step += 1;
     const float bc1 = (float)(1.0 - pow((double)opt->beta1, (double)m->adam_step));
     const float bc2 = (float)(1.0 - pow((double)opt->beta2, (double)m->adam_step));
-    k_adamw<<<(MLP_NPARAM + 255) / 256, 256, 0, m->stream>>>(m->P, m->G, m->Mm, m->Vv, opt->lr, opt->beta1,
-                                                             opt->beta2, opt->eps, opt->weight_decay, bc1, bc2);
-    MK(cudaGetLastError(), "adamw");
-    MK(refresh(m), "refresh bf16");
+    if (m->stream) {
+        // a graph replay per step (the captured step has ~25 kernels)
+        if (m->train_n != n) MK(capture_train(m, x, y, n, opt), "training graph capture");
+        MK(replay_train(m, x, y, n, opt, bc1, bc2), "training graph launch");
+    } else {
+        MK(enqueue_train(m, x, y, n, opt, bc1, bc2), "training step");
+    }
     if (loss) {
         double L = 0.0;
         MK(cudaMemcpyAsync(&L, m->loss, 8, cudaMemcpyDeviceToHost, m->stream), "loss");
@@ -893,6 +1000,7 @@ extern "C" turret_status mlp_train_step(turret_mlp *m, const float *x, const flo
 extern "C" turret_status mlp_destroy(turret_mlp *m) {
     if (!m) return TURRET_EINVAL;
     if (m->stream) cudaStreamSynchronize(m->stream);
+    drop_train_graph(m);
     delete m;
     return TURRET_OK;
 }

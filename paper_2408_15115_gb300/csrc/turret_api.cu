@@ -42,6 +42,7 @@ static turret_status fail(turret_ctx *c, turret_status s, const std::string &msg
 }
 
 static turret_status cuda_fail(turret_ctx *c, cudaError_t e, const char *where) {
+    cudaGetLastError();  // a non-sticky error must not surface in later launches
     return fail(c, TURRET_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
