@@ -39,6 +39,7 @@ class OrcParams(C.Structure):
         ("fixed_position", C.c_int), ("uw_bottom", C.c_double * 3), ("uw_top", C.c_double * 3),
         ("reinject_trigger", C.c_int), ("reinject_target", C.c_int), ("reinject_below", C.c_int),
         ("reinject_above", C.c_int), ("force_eval", C.c_int),
+        ("predictor", C.c_int), ("pred_warm", C.c_int), ("pred_eps", C.c_double),
     ]
 
 
@@ -75,6 +76,10 @@ def lib():
                      "orc_advance_particle_only", "orc_fluid_step", "orc_step", "orc_load_particle"):
             getattr(L, name).restype = C.c_int if name in ("orc_step", "orc_load_particle") else None
         L.orc_get_threads.restype = C.c_int
+        L.orc_ibm_warm.restype = C.c_int
+        L.orc_ibm_cycles.restype = C.c_int64
+        L.orc_ibm_cycles.argtypes = [C.c_void_p]
+        L.orc_predictor_step.restype = None
         _lib = L
     return _lib
 
@@ -202,6 +207,20 @@ def ibm(ustar, X, U, dS, ncycles=4, periodic=(True, True, True)):
     return himm, hl
 
 
+def ibm_warm(ustar, X, U, dS, h0, ncycles=4, eps=0.0, periodic=(True, True, True)):
+    """IBM cycles warm-started from the Lagrangian force h0 (predictor option):
+    returns (h_imm dense, h, cycles run)."""
+    ustar = _c(ustar)
+    shape = ustar.shape[:3]
+    X = _c(X)
+    himm = np.zeros(tuple(shape) + (3,))
+    hl = _c(h0).copy()
+    g = _grid(shape, periodic)
+    run = lib().orc_ibm_warm(C.byref(g), _p(ustar), _p(X), _p(_c(U)), _p(_c(dS)), C.c_int64(X.shape[0]),
+                             C.c_int(ncycles), C.c_double(eps), _p(himm), _p(hl))
+    return himm, hl, run
+
+
 class Sim:
     """Dense FP64 window simulation (fluid + optional particle), Table 1 order.
 
@@ -212,20 +231,24 @@ class Sim:
     below, above): the re-injection copy of Sec. 2.5 (slide 0 only; trigger 0
     off).  force_eval 0: force and torque from the stress on the surface
     offset by 2 cells along the normals (outside the diffuse interface); 1: the
-    stress interpolated at the markers, as printed in Sec. 2.2.  Arrays are
-    (nz, ny, nx, ...)."""
+    stress interpolated at the markers, as printed in Sec. 2.2.  predictor 1:
+    markers move with the body's motion at t + 1 estimated from a linear
+    extrapolation of F, T (not in the paper); pred_warm 1 with it: IBM cycles
+    warm-started from the previous step's h, skipped once the slip is below
+    pred_eps.  Arrays are (nz, ny, nx, ...)."""
 
     STATE_FIELDS = 45
 
     def __init__(self, nx, ny, nz, tau, bc_x=0, bc_y=0, bc_bottom=0, bc_top=0, sponge=0, slide=0,
                  anchor_frac=0.25, force_scheme=0, rot_form=0, gravity=0, renorm=0, ibm_cycles=4,
                  kappa=1.0, g=(0.0, 0.0, 0.0), fixed_position=0, uw_bottom=(0.0, 0.0, 0.0), uw_top=(0.0, 0.0, 0.0),
-                 reinject=(0, 0, 0, 0), force_eval=0):
+                 reinject=(0, 0, 0, 0), force_eval=0, predictor=0, pred_warm=0, pred_eps=0.0):
         self.shape = (nz, ny, nx)
         p = OrcParams(nx, ny, nz, bc_x, bc_y, bc_bottom, bc_top, sponge, slide, float(anchor_frac), float(tau),
                       force_scheme, rot_form, gravity, renorm, ibm_cycles, float(kappa), (C.c_double * 3)(*g),
                       int(fixed_position), (C.c_double * 3)(*uw_bottom), (C.c_double * 3)(*uw_top),
-                      *[int(v) for v in reinject], int(force_eval))
+                      *[int(v) for v in reinject], int(force_eval), int(predictor), int(pred_warm),
+                      float(pred_eps))
         self._params = p
         self._s = lib().orc_new(C.byref(p))
 
@@ -306,3 +329,14 @@ class Sim:
 
     def advance_particle_only(self, n=1):
         lib().orc_advance_particle_only(C.c_void_p(self._s), C.c_int(n))
+
+    def ibm_cycles(self):
+        """IBM cycles run so far."""
+        return int(lib().orc_ibm_cycles(C.c_void_p(self._s)))
+
+    def predictor_step(self, F, T):
+        """Predictor and 6DOF update alone: enter F, T as the current force
+        evaluation, predict, advance; returns the (v, omega) the markers move with."""
+        vel, om = np.zeros(3), np.zeros(3)
+        lib().orc_predictor_step(C.c_void_p(self._s), _p(_c(F)), _p(_c(T)), _p(vel), _p(om))
+        return vel, om

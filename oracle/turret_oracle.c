@@ -377,6 +377,12 @@ typedef struct {
      * above) around it (zf = floor of that z) move up by target - zf */
     int reinject_trigger, reinject_target, reinject_below, reinject_above;
     int force_eval;           /* 0: stress on the offset surface X + 2n (READING, default); 1: at the markers */
+    /* force/torque predictor (not in the paper; see predict()): 0 the paper's
+     * step; 1 linear extrapolation of F, T driving the marker velocities at
+     * t + 1; pred_warm 1: the IBM cycles start from the previous step's h and
+     * a cycle is skipped once the slip of the previous one is below pred_eps */
+    int predictor, pred_warm;
+    double pred_eps;
 } orc_params;
 
 typedef struct {
@@ -401,6 +407,11 @@ typedef struct {
     double Fp[3];              /* pressure part of F: sum_k dS_k (-p(X_k)) n_k */
     int64_t origin[3], step;
     int status;
+    /* predictor state: F, T of the last two force evaluations (newest first),
+     * the prediction for the next time level, IBM cycles run */
+    double Fh[2][3], Th[2][3], Fhat[3], That[3];
+    int hist_n, use_pred, warm_ready;
+    int64_t cycles;
 } orc_sim;
 
 static inline int64_t cidx(const orc_sim *s, int x, int y, int z) {
@@ -638,6 +649,37 @@ void orc_spread(const orc_grid *g, const double *hk, const double *X, const doub
  * h_imm is h1 of the last cycle, so steps l=2..4 of the last cycle are not
  * run.  Outputs: himm (dense, 3 per cell) and hl (the Lagrangian force that
  * was spread, 3 per marker).                                                 */
+/* The IBM cycles warm-started from a given Lagrangian force h (predictor
+ * option, not in the paper): for cycle 1 .. ncycles, unless the previous
+ * cycle's slip max_k |U_k - I[u* + S h](X_k)| (over markers and components)
+ * is below eps, h <- h + U - I[u* + S h]; then h_imm = S[h].  hl: h on entry
+ * and on return.  Returns the cycles run.                                    */
+int orc_ibm_warm(const orc_grid *g, const double *ustar, const double *X, const double *U, const double *dS, int64_t nm,
+                 int ncycles, double eps, double *himm, double *hl) {
+    int64_t ncell = (int64_t)g->nx * g->ny * g->nz;
+    double *ui = (double *)malloc(sizeof(double) * 3 * (size_t)nm);
+    double *u2 = (double *)malloc(sizeof(double) * 3 * (size_t)ncell);
+    double slip = INFINITY;
+    int run = 0;
+    for (int cyc = 1; cyc <= ncycles; ++cyc) {
+        if (cyc > 1 && slip < eps) break;
+        orc_spread(g, hl, X, dS, nm, himm);
+        for (int64_t c = 0; c < 3 * ncell; ++c) u2[c] = ustar[c] + himm[c];
+        orc_interp(g, u2, 3, X, nm, ui);
+        slip = 0.0;
+        for (int64_t k = 0; k < 3 * nm; ++k) {
+            const double r = U[k] - ui[k];
+            if (fabs(r) > slip) slip = fabs(r);
+            hl[k] += r;
+        }
+        run += 1;
+    }
+    orc_spread(g, hl, X, dS, nm, himm);
+    free(ui);
+    free(u2);
+    return run;
+}
+
 void orc_ibm(const orc_grid *g, const double *ustar, const double *X, const double *U, const double *dS, int64_t nm,
              int ncycles, double *himm, double *hl) {
     int64_t ncell = (int64_t)g->nx * g->ny * g->nz;
@@ -668,8 +710,12 @@ static orc_grid sim_grid(const orc_sim *s) {
  * body to lab components), n_k = M^T nb_k, U_k = v + omega x (X_k - C), with C
  * the centre of mass in window coordinates (READING: U_k from v, omega at
  * t + dt/2, the only level available at event (4), and X_k at t + dt).      */
+static void marker_motion(const orc_sim *s, double vel[3], double om[3]);
+
 static void update_markers(orc_sim *s) {
     double C[3] = {s->r[0] - (double)s->origin[0], s->r[1] - (double)s->origin[1], s->r[2] - (double)s->origin[2]};
+    double vel[3], om[3];
+    marker_motion(s, vel, om);
     for (int64_t k = 0; k < s->nm; ++k) {
         double arm[3], nn[3];
         for (int a = 0; a < 3; ++a) {
@@ -681,11 +727,11 @@ static void update_markers(orc_sim *s) {
             }
         }
         double wx[3];
-        cross(s->w, arm, wx);
+        cross(om, arm, wx);
         for (int a = 0; a < 3; ++a) {
             s->X[3 * k + a] = C[a] + arm[a];
             s->n[3 * k + a] = nn[a];
-            s->U[3 * k + a] = s->v[a] + wx[a];
+            s->U[3 * k + a] = vel[a] + wx[a];
         }
     }
 }
@@ -772,7 +818,13 @@ static void force_torque(orc_sim *s) {
 
 static void run_ibm(orc_sim *s) {
     orc_grid g = sim_grid(s);
-    orc_ibm(&g, s->u, s->X, s->U, s->dS, s->nm, s->p.ibm_cycles, s->h, s->hl);
+    if (s->p.predictor && s->p.pred_warm && s->warm_ready) {
+        s->cycles += orc_ibm_warm(&g, s->u, s->X, s->U, s->dS, s->nm, s->p.ibm_cycles, s->p.pred_eps, s->h, s->hl);
+    } else {
+        orc_ibm(&g, s->u, s->X, s->U, s->dS, s->nm, s->p.ibm_cycles, s->h, s->hl);
+        s->cycles += s->p.ibm_cycles - 1;
+    }
+    s->warm_ready = 1;  /* every later step may start from this h */
 }
 
 
@@ -830,6 +882,60 @@ static void advance_particle(orc_sim *s) {
             double l = sqrt(s->d[3 * i] * s->d[3 * i] + s->d[3 * i + 1] * s->d[3 * i + 1] + s->d[3 * i + 2] * s->d[3 * i + 2]);
             for (int a = 0; a < 3; ++a) s->d[3 * i + a] /= l;
         }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Force/torque predictor.  Not part of the paper, whose only predictor is the
+ * orientation predictor-corrector above; the marker velocities of the IBM
+ * step (event 4) are otherwise taken at t + 1/2.  With predictor 1 the force
+ * and torque of the next time level are extrapolated linearly from the last
+ * two evaluations, F^(t+1) = 2 F(t) - F(t-1) (F(t) alone after the first
+ * evaluation), and the markers move with the estimate of the body's motion at
+ * t + 1 that this gives, half a leap-frog step on from t + 1/2:
+ *   v^ = v(t+1/2) + (g_eff + F^ / m) / 2          (0 for a held centre),
+ *   angular momentum form: L^ = L(t+1/2) + T^ / 2,  omega^ = M^T (J/m)^-1 M L^ / m,
+ *   printed form:  omega^ = omega(t+1/2) + M^T (J/m)^-1 M T^ / (2 m),
+ * with M the orientation at t + 1.                                           */
+static void push_history(orc_sim *s) {
+    for (int a = 0; a < 3; ++a) {
+        s->Fh[1][a] = s->Fh[0][a];
+        s->Th[1][a] = s->Th[0][a];
+        s->Fh[0][a] = s->F[a];
+        s->Th[0][a] = s->T[a];
+    }
+    if (s->hist_n < 2) s->hist_n += 1;
+}
+
+static void predict(orc_sim *s) {
+    for (int a = 0; a < 3; ++a) {
+        s->Fhat[a] = s->hist_n >= 2 ? 2.0 * s->Fh[0][a] - s->Fh[1][a] : s->Fh[0][a];
+        s->That[a] = s->hist_n >= 2 ? 2.0 * s->Th[0][a] - s->Th[1][a] : s->Th[0][a];
+    }
+}
+
+/* Translational and angular velocity the markers move with: v, omega at
+ * t + 1/2 (the paper), or the predicted estimates at t + 1. */
+static void marker_motion(const orc_sim *s, double vel[3], double om[3]) {
+    if (!s->use_pred) {
+        for (int a = 0; a < 3; ++a) {
+            vel[a] = s->v[a];
+            om[a] = s->w[a];
+        }
+        return;
+    }
+    const double m = s->p.kappa * s->vol;
+    for (int a = 0; a < 3; ++a) {
+        const double ge = (s->p.gravity == 1 ? 1.0 : 1.0 - 1.0 / s->p.kappa) * s->p.g[a];
+        vel[a] = s->p.fixed_position ? 0.0 : s->v[a] + 0.5 * (ge + s->Fhat[a] / m);
+    }
+    double src[3], sb[3], wb[3];
+    for (int a = 0; a < 3; ++a) src[a] = s->p.rot_form == 1 ? s->That[a] : s->L[a] + 0.5 * s->That[a];
+    for (int i = 0; i < 3; ++i) sb[i] = s->d[3 * i] * src[0] + s->d[3 * i + 1] * src[1] + s->d[3 * i + 2] * src[2];
+    for (int i = 0; i < 3; ++i) wb[i] = (s->Jminv[3 * i] * sb[0] + s->Jminv[3 * i + 1] * sb[1] + s->Jminv[3 * i + 2] * sb[2]) / m;
+    for (int a = 0; a < 3; ++a) {
+        const double wl = s->d[a] * wb[0] + s->d[3 + a] * wb[1] + s->d[6 + a] * wb[2];
+        om[a] = s->p.rot_form == 1 ? s->w[a] + 0.5 * wl : wl;
     }
 }
 
@@ -933,6 +1039,7 @@ int orc_load_particle(orc_sim *s, const double *verts, int64_t nv, const int32_t
     update_markers(s);
     if (check_support(s) != 0) return -2;
     force_torque(s);
+    push_history(s);
     run_ibm(s);
     return 0;
 }
@@ -942,6 +1049,10 @@ int orc_load_particle(orc_sim *s, const double *verts, int64_t nv, const int32_t
 int orc_step(orc_sim *s, int n) {
     for (int k = 0; k < n; ++k) {
         collide_all(s);                                /* (1) collide with h_imm(t) */
+        if (s->has_particle && s->p.predictor) {       /* F^, T^ for t+1 (predictor option) */
+            predict(s);
+            s->use_pred = 1;
+        }
         if (s->has_particle) advance_particle(s);      /* (2) particle(t+1) from F(t), T(t) */
         if (s->has_particle) slide_window(s);
         if (s->has_particle) reinject(s);
@@ -950,11 +1061,33 @@ int orc_step(orc_sim *s, int n) {
         s->step++;
         if (!s->has_particle) continue;
         update_markers(s);
+        s->use_pred = 0;
         if (check_support(s) != 0) return -2;
         force_torque(s);                               /* (3) F(t+1), T(t+1) */
+        push_history(s);
         run_ibm(s);                                    /* (4) h_imm(t+1) */
     }
     return 0;
+}
+
+/* IBM cycles run so far (the paper's step: ibm_cycles - 1 per step). */
+int64_t orc_ibm_cycles(const orc_sim *s) { return s->cycles; }
+
+/* The predictor and the 6DOF update alone (tests): F, T are taken as the
+ * force evaluation of the current time level (entered in the history), the
+ * prediction for the next level is made, the particle advances with F, T,
+ * and the motion the markers then move with is returned in vel, om. */
+void orc_predictor_step(orc_sim *s, const double *F, const double *T, double *vel, double *om) {
+    for (int a = 0; a < 3; ++a) {
+        s->F[a] = F[a];
+        s->T[a] = T[a];
+    }
+    push_history(s);
+    predict(s);
+    s->use_pred = 1;
+    advance_particle(s);
+    marker_motion(s, vel, om);
+    s->use_pred = 0;
 }
 
 /* Particle state: r[3] (global), d[9] (rows d_i), v[3], w[3], F[3], T[3],

@@ -25,13 +25,15 @@ def gpu_velocity(t):
 
 
 def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anchor=0.25, storage="f32",
-              flags=None, fields=None, particle=None, walls=None, reinject=None):
+              flags=None, fields=None, particle=None, walls=None, reinject=None, predictor=None):
     """Build a (Turret, oracle Sim) pair with identical configuration.
 
     bc = (bc_x, bc_y, bc_bottom, bc_top); fields = (rho, u) or None;
     particle = (verts, tris, r0, v0, w0) or None; walls = (u_bottom, u_top)
     for moving walls (bc 3) or None; reinject = (trigger, target, below,
-    above) for the re-injection copy or None."""
+    above) for the re-injection copy or None; predictor = (warm, eps) for the
+    linear-extrapolation predictor with predicted marker velocities (and
+    warm-started cycles when warm) or None."""
     from paper_2408_15115_gb300 import turret as T
     flags = dict(flags or {})
     tau = 3 * nu + 0.5
@@ -43,7 +45,11 @@ def make_pair(nx, ny, nz, nu, bc, kappa=1.0, g=(0, 0, 0), sponge=0, slide=0, anc
               ibm_cycles=flags.get("ibm_cycles", 4), kappa=kappa, g=g,
               fixed_position=flags.get("fixed_position", 0),
               uw_bottom=walls[0] if walls else (0, 0, 0), uw_top=walls[1] if walls else (0, 0, 0),
-              reinject=reinject or (0, 0, 0, 0), force_eval=flags.get("force_eval", 0))
+              reinject=reinject or (0, 0, 0, 0), force_eval=flags.get("force_eval", 0),
+              predictor=1 if predictor else 0, pred_warm=int(predictor[0]) if predictor else 0,
+              pred_eps=float(predictor[1]) if predictor else 0.0)
+    if predictor is not None:
+        t.set_predictor("linear", warm=bool(predictor[0]), velocity=True, slip_eps=float(predictor[1]))
     if reinject is not None:
         t.set_reinjection(*reinject)
     if walls is not None:

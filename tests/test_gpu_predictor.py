@@ -216,3 +216,32 @@ def test_trained_network_gains_over_linear_extrapolation():
     assert e["network"].mean() < e["linear"].mean()
     assert e["network"].mean() < 0.5 * e["persistence"].mean()
     net.close()
+
+
+@pytest.mark.parametrize("warm,eps", [(False, 1e-4), (True, 0.0), (True, 1.0)])
+def test_linear_predictor_step_vs_oracle(warm, eps):
+    # the predictor option against the oracle's restatement of it: marker
+    # velocities from linear extrapolation of F, T, with the paper's cold
+    # cycles or warm-started ones (eps 0: all four cycles every step; eps 1:
+    # one cycle per step, the slip always below it) -- the 32 x 32 x 64 closed
+    # box with the seeded flow and the d = 8 sphere, 100 steps
+    from oracle import oracle as O
+
+    from cases import TOL_U_F32, gpu_velocity, make_pair, rel_max
+    shape = (64, 32, 32)
+    V, Tr = I.sphere(5, 8.0)
+    fields = I.random_state(shape, u_amp=0.01, rho_amp=0.001, kmax=4, seed=1)
+    O.set_threads(0)
+    t, s = make_pair(32, 32, 64, 0.05, (1, 1, 1, 1), kappa=2.5, g=(0, 0, -1e-5), fields=fields,
+                     particle=(V, Tr, (15.5, 15.5, 44.0), (0, 0, -0.01), (0.001, 0, 0)),
+                     predictor=(warm, eps))
+    t.step(100)
+    s.step(100)
+    a, b = t.state(), s.state()
+    assert np.abs(a["F"] - b["F"]).max() / np.abs(b["F"]).max() < 1e-4, (a["F"], b["F"])
+    assert np.abs(a["v"] - b["v"]).max() / np.abs(b["v"]).max() < 1e-5, (a["v"], b["v"])
+    assert np.abs(a["w"] - b["w"]).max() / np.abs(b["w"]).max() < 1e-4, (a["w"], b["w"])
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < TOL_U_F32
+    assert t.predictor_stats()["cycles"] == s.ibm_cycles()
+    t.close()

@@ -169,3 +169,34 @@ def test_open_mesh_rejected():
         O.mesh_props(V, T[1:])
     with pytest.raises(ValueError):
         O.mesh_props(V, T[:, ::-1])  # inward orientation gives negative volume
+
+
+@pytest.mark.parametrize("ncycles", [1, 3, 4])
+def test_warm_started_ibm_cycles_equal_their_closed_form(ncycles):
+    # predictor option: the cycles start from a given h0 instead of U - I[u*];
+    # with no early stop (eps 0), C cycles give
+    # h_C = (I - A)^C h0 + sum_{j<C} (I - A)^j r0, r0 = U - I[u*], A = I o S
+    # (built densely here), and h_imm = S[h_C]
+    shape = (14, 14, 14)
+    V, T = I.icosphere(2, 3.0)
+    X = V + 7.0 + RNG.uniform(-0.3, 0.3, 3)
+    dS = O.mesh_props(V, T)["dS"]
+    ustar = 0.01 * RNG.standard_normal(shape + (3,))
+    U = 0.01 * RNG.standard_normal((X.shape[0], 3))
+    h0 = 0.01 * RNG.standard_normal((X.shape[0], 3))
+    himm, h, run = O.ibm_warm(ustar, X, U, dS, h0, ncycles, 0.0, (False, False, False))
+    assert run == ncycles
+    Phi = _phi_matrix(X, shape)
+    A = Phi.T @ (Phi * dS[None, :])
+    r0 = U - Phi.T @ ustar.reshape(-1, 3)
+    M = np.eye(A.shape[0]) - A
+    want = h0.copy()
+    for _ in range(ncycles):
+        want = M @ want + r0
+    assert np.abs(h - want).max() < 1e-12
+    assert np.abs(himm.reshape(-1, 3) - Phi @ (h * dS[:, None])).max() < 1e-12
+    # a slip tolerance above the first cycle's residual stops after one cycle
+    res1 = np.abs(r0 - A @ h0).max()
+    _, h1, run1 = O.ibm_warm(ustar, X, U, dS, h0, 4, 2.0 * res1, (False, False, False))
+    assert run1 == 1
+    assert np.abs(h1 - (M @ h0 + r0)).max() < 1e-12
