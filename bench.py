@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--case", default=None, choices=["mlp_train", "ensemble_steps", "window"],
                    help="run one small workload for a profiler capture instead of the benchmark")
     p.add_argument("--learned-steps", type=int, default=6000)
+    p.add_argument("--runs", type=int, default=64, help="runs of the ensemble_steps profiling case")
     return p.parse_args()
 
 
@@ -672,8 +673,9 @@ def run_ours(args):
 def run_case(args):
     """Small fixed workloads for profiler captures: `mlp_train`, three BF16
     training steps of the surrogate network at batch 4096; `ensemble_steps`,
-    the 64-run ensemble as one batch with tiles (128, 2, 32), 5 + 20 steps in
-    FP32 then 5 + 20 with storage alternating FP32/FP16; `window`, the
+    the 64-run ensemble (or its first --runs runs) as one batch with tiles
+    (128, 2, 32), 5 + 20 steps in FP32 then 5 + 20 with storage alternating
+    FP32/FP16; `window`, the
     --workload window in --storage, --steps coupled steps without graphs
     (one launch per kernel) then three launches of its collide+stream alone."""
     import numpy as np
@@ -707,7 +709,7 @@ def run_case(args):
         t.close()
     else:
         for storage in ("f32", "alternate"):
-            runs = configs.load_ensemble(configs.ensemble(64, seed=4, storage=storage), device=dev)
+            runs = configs.load_ensemble(configs.ensemble(64, seed=4, storage=storage)[:args.runs], device=dev)
             b = T.Batch(runs, device=dev)
             b.set_tiles(128, 2, [32] * len(runs))
             b.step(5)
