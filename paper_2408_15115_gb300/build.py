@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libturret.so")
-SOURCES = ["lbm_kernels.cu", "lbm_far.cu", "lbm_staged.cu", "lbm_batch.cu", "support_kernels.cu", "window_kernels.cu", "ibm_kernels.cu", "ibm_standalone.cu",
+SOURCES = ["lbm_kernels.cu", "lbm_far.cu", "lbm_staged.cu", "lbm_xpair.cu", "lbm_batch.cu", "support_kernels.cu", "window_kernels.cu", "ibm_kernels.cu", "ibm_standalone.cu",
            "turret_api.cu", "batch_api.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

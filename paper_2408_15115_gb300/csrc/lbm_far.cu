@@ -27,6 +27,8 @@ cudaError_t launch_collide_far(const Geom &g, int storage, const void *src, void
     if (storage != ST_F32 && lmap && smap)
         return launch_collide_staged(g, storage, *lmap, *smap, src, dst, utop_in, utop_out, st, slot, -1, hbox, box,
                                      REGION_FAR, s);
+    if (storage != ST_F32 && xpair_eligible(g, storage))
+        return launch_collide_xpair(g, storage, src, dst, utop_in, utop_out, st, slot, -1, hbox, box, REGION_FAR, s);
     if (storage != ST_F32)
         return launch_collide_stream(g, storage, src, dst, utop_in, utop_out, st, slot, -1, hbox, box, true,
                                      REGION_FAR, s);

@@ -556,6 +556,9 @@ static cudaError_t collide_window(const turret_ctx *c, int p, cudaStream_t s) {
         return launch_collide_staged(c->geom, c->storage, *src_map(c, p), *dst_map(c, p), c->f[p], c->f[1 - p],
                                      c->utop[1 - p], c->utop[p], c->dstate, p, 1 - p, nullptr, c->box, REGION_ALL,
                                      s);
+    if (xpair_eligible(c->geom, c->storage))
+        return launch_collide_xpair(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
+                                    p, 1 - p, nullptr, c->box, REGION_ALL, s);
     return launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
                                  1 - p, nullptr, c->box, false, REGION_ALL, s);
 }
@@ -829,7 +832,7 @@ static void set_node_priorities(const turret_ctx *c, cudaGraph_t gr) {
         if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
         const bool is_bulk = (kp.gridDim.x == bulk.x && kp.gridDim.y == bulk.y && kp.gridDim.z == bulk.z &&
                               kp.blockDim.x == 32 && kp.blockDim.y == 4) ||
-                             is_staged_kernel(kp.func);
+                             is_staged_kernel(kp.func) || is_xpair_kernel(kp.func);
         cudaLaunchAttributeValue v;
         memset(&v, 0, sizeof v);
         v.priority = is_bulk ? lo : hi;

@@ -330,9 +330,9 @@ cudaError_t launch_collide_stream(const Geom &g, int storage, const void *src, v
                                   const BoxGeom &box, bool has_box, int region, cudaStream_t s);
 // The far cells of a coupled step (lbm_far.cu): FP32 storage under a register
 // cap that leaves room for the immersed-boundary chain's small blocks; 16-bit
-// storages with their sources staged in shared memory when `map` (the tensor
-// map of src, see encode_population_map) is given, else as
-// launch_collide_stream(..., REGION_FAR).
+// storages staged in shared memory when the tensor maps lmap / smap of src and
+// dst are given (see encode_population_map), else on x-adjacent pairs where
+// xpair_eligible, else as launch_collide_stream(..., REGION_FAR).
 cudaError_t launch_collide_far(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                float *utop_out, DevState *st, int slot, const float *hbox, const BoxGeom &box,
                                cudaStream_t s, const CUtensorMap *lmap = nullptr, const CUtensorMap *smap = nullptr);
@@ -345,6 +345,14 @@ bool staged_eligible(const Geom &g, int storage);
 bool encode_population_map(CUtensorMap *map, const void *buf, const Geom &g, bool source);
 bool prepare_staged();
 bool is_staged_kernel(const void *fn);
+// 16-bit collide+stream on x-adjacent cell pairs with 4-byte accesses
+// (lbm_xpair.cu): REGION_FAR or REGION_ALL without forcing; xpair_eligible:
+// FP16 or round-to-nearest BF16 on a window the 64 x 2 x 2 tiles cover.
+bool xpair_eligible(const Geom &g, int storage);
+bool is_xpair_kernel(const void *fn);
+cudaError_t launch_collide_xpair(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
+                                 float *utop_out, DevState *st, int slot, int slot_out, const float *hbox,
+                                 const BoxGeom &box, int region, cudaStream_t s);
 cudaError_t launch_collide_staged(const Geom &g, int storage, const CUtensorMap &lmap, const CUtensorMap &smap,
                                   const void *src, void *dst, const float *utop_in, float *utop_out, DevState *st,
                                   int slot, int slot_out, const float *hbox, const BoxGeom &box, int region,
