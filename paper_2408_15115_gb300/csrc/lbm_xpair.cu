@@ -40,7 +40,8 @@ __device__ __forceinline__ f2 unpack2<ST_F16>(unsigned w) {
 }
 template <>
 __device__ __forceinline__ f2 unpack2<ST_BF16>(unsigned w) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+    // a BF16 value is the high half of the FP32 value with the same bits
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
 template <int ST>
