@@ -1,6 +1,7 @@
-"""The 16-bit collide+stream with its sources and results staged in shared
-memory by bulk tensor copies (flags.staged_loads) against the same kernel with
-plain global loads and stores: bitwise equal
+"""The 16-bit collide+stream paths: the default one on x-adjacent cell pairs
+with 4-byte accesses against the FP64 oracle, and the opt-in one with its
+sources and results staged in shared memory by bulk tensor copies
+(flags.staged_loads) against the default: bitwise equal
 populations and particle state, on fluid-only periodic windows (every tile at
 a periodic edge patched from the far side) and on coupled sliding windows
 (far-cell tiles staged, tiles at the near region, the ring's wrap and the
@@ -81,4 +82,43 @@ def test_staged_fp16_window_vs_oracle():
     s.fluid_step(100)
     u, _ = gpu_velocity(t)
     assert rel_max(u, s.velocity()) < 2e-3
+    t.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+def test_xpair_window_vs_oracle(storage, tol):
+    # the default 16-bit path on a window its 64 x 2 x 2 tiles cover (x-adjacent
+    # cell pairs, 4-byte accesses; boundary planes on the cell-pair path):
+    # 64 x 32 x 32 with a no-slip bottom, a pressure top and a sponge, 100
+    # steps of a seeded flow against the FP64 oracle
+    shape = (32, 32, 64)
+    O.set_threads(0)
+    fields = I.random_state(shape, u_amp=0.01, rho_amp=0.001, kmax=3, seed=17)
+    t, s = make_pair(64, 32, 32, 0.03, (0, 0, 1, 2), sponge=4, storage=storage, fields=fields)
+    t.step(100)
+    s.fluid_step(100)
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < tol
+    t.close()
+
+
+@pytest.mark.parametrize("storage,tol_f,tol_v", [("f16", 2e-2, 2e-3), ("bf16", 5e-2, 2e-2)])
+def test_xpair_coupled_sliding_window_vs_oracle(storage, tol_f, tol_v):
+    # a coupled 64 x 64 x 96 sliding window in 16-bit storage: the far cells on
+    # x-pairs, the near region and the boundary planes on the cell-pair path;
+    # 40 steps against the FP64 oracle (force, body velocity, fluid velocity)
+    V, Tr = I.sphere(6, 10.0)
+    O.set_threads(0)
+    r0 = (31.3, 32.6, 36.2)
+    t, s = make_pair(64, 64, 96, 0.02, (0, 0, 1, 2), kappa=2.0, g=(0, 0, -1e-4), sponge=8, slide=1, anchor=0.45,
+                     storage=storage, particle=(V, Tr, r0, (0.0, 0.0, -0.05), (0.0, 0.002, 0.0)))
+    t.step(40)
+    s.step(40)
+    a, b = t.state(), s.state()
+    assert abs(b["origin"][2]) >= 3
+    assert np.array_equal(a["origin"], b["origin"].astype(np.int64))
+    assert np.abs(a["F"] - b["F"]).max() / np.abs(b["F"]).max() < tol_f, (a["F"], b["F"])
+    assert np.abs(a["v"] - b["v"]).max() / np.abs(b["v"]).max() < tol_v, (a["v"], b["v"])
+    u, _ = gpu_velocity(t)
+    assert rel_max(u, s.velocity()) < tol_v
     t.close()
