@@ -18,9 +18,10 @@
 // the recursion: a sum over index pairs), so every term is an outer product
 // of one 3-vector per axis and a collision is
 //   moments : 3 separable passes of 3-point sums over x, y, z (10 moments)
-//   rebuild : per-axis factors X, X', X'' and 9 (y,z) pair terms, then
-//             3 FMAs per population (collide_factored below)
-// about 300 FP32 flops per cell.  Populations are stored as deviations
+//   rebuild : per-axis factors X, X', X'' and five terms per (y, z) pair that
+//             carry the equilibrium and the off-equilibrium parts together,
+//             then 3 FMAs per population (collide_rr below)
+// about 335 FP32 operations per cell.  Populations are stored as deviations
 // s_i = 216 (f_i - w_i) (FP32) or s_i / W_i scaled (FP16/BF16) and every
 // pass works in that storage domain (Codec); the moments use drho = sum s, so
 // no O(1) term cancels in single precision.
@@ -180,86 +181,118 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
             }
 }
 
-// Raw moments of the scaled deviations up to second order (all times 216):
-// drho = sum s, j = sum xi s, Pi'_ab = sum xi_a xi_b s, by three separable
-// 3-point passes.  From a storage domain r_i = K s_i / W_i the passes carry
-// the axis weights W1 = (1, 4, 1) of the sums that need them (the 4 sits on
-// xi = 0, where the xi-weighted sums vanish anyway) and the result is
-// divided by K (exact).
-struct Mom {
-    float drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
+// ---------------------------------------------------------------------------
+// Lane-generic arithmetic of the moments and the collision: V = float (one
+// cell) or f2 (two cells, one packed f32x2 instruction per operation).  Every
+// operation is an explicitly rounded intrinsic (nothing is contracted), and a
+// packed operation rounds each lane as the scalar one does, so a cell gets the
+// same bits whichever form computes it and whatever cell it is paired with.
+typedef float2 f2;
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }  // exact product
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 vrcp(f2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+template <class V>
+__device__ __forceinline__ V vs(float a);
+template <>
+__device__ __forceinline__ float vs<float>(float a) { return a; }
+template <>
+__device__ __forceinline__ f2 vs<f2>(float a) { return F2(a); }
+// a times a power of two c (exact; no operation for c = 1)
+template <class V>
+__device__ __forceinline__ V vpow2(V a, float c) { return c == 1.0f ? a : vmul(a, vs<V>(c)); }
+
+// Raw moments of the stored values up to second order, by three separable
+// 3-point passes: drho = sum r, j = sum xi r, the diagonal Pi'_aa = sum xi_a^2 r
+// and the off-diagonal ones negated, n_ab = -sum xi_a xi_b r (free here, and it
+// saves a negation later).  FP32 storage holds r_i = s_i = 216 (f_i - w_i); the
+// 16-bit domains r_i = K s_i / W_i carry the axis weights W1 = (1, 4, 1) in the
+// sums that need them (the 4 sits on xi = 0, where the xi-weighted sums vanish
+// anyway).  Every moment here is thus K times the scaled moment, which is 216
+// times the physical one (K = 1 for FP32 and BF16).
+template <class V>
+struct MomR {
+    V drho, jx, jy, jz, pxx, pyy, pzz, nxy, nxz, nyz;
 };
 
-// a + W1(1) b + c: the centre weight applied in the storage domains
-template <bool SC>
-__device__ __forceinline__ float wsum3(float a, float b, float c) {
-    return SC ? fmaf(4.0f, b, a + c) : a + b + c;
+// a + W1(1) b + c in the storage domain
+template <bool SC, class V>
+__device__ __forceinline__ V wsum3(V a, V b, V c) {
+    return SC ? vfma(vs<V>(4.0f), b, vadd(a, c)) : vadd(vadd(a, b), c);
 }
 
-template <int ST>
-__device__ __forceinline__ Mom moments27(const float q[27]) {
+template <int ST, class V>
+__device__ __forceinline__ MomR<V> moments_raw(const V q[27]) {
     constexpr bool SC = Codec<ST>::scaled;
-    float A0[9], A1[9], A2[9];
+    V A0[9], A1[9], A2[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {  // k = ey + 3 ez; x pass
-        const float a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
+    for (int k = 0; k < 9; ++k) {  // x pass, k = ey + 3 ez
+        const V a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
         A0[k] = wsum3<SC>(a, b, c);
-        A1[k] = c - a;
-        A2[k] = c + a;
+        A1[k] = vsub(c, a);
+        A2[k] = vadd(c, a);
     }
-    float B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
+    V B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
 #pragma unroll
     for (int ez = 0; ez < 3; ++ez) {  // y pass
         const int k = 3 * ez;
         B00[ez] = wsum3<SC>(A0[k], A0[k + 1], A0[k + 2]);
-        B01[ez] = A0[k + 2] - A0[k];
-        B02[ez] = A0[k + 2] + A0[k];
+        B01[ez] = vsub(A0[k + 2], A0[k]);
+        B02[ez] = vadd(A0[k + 2], A0[k]);
         B10[ez] = wsum3<SC>(A1[k], A1[k + 1], A1[k + 2]);
-        B11[ez] = A1[k + 2] - A1[k];
+        B11[ez] = vsub(A1[k], A1[k + 2]);  // -sum xi_y (sum xi_x r)
         B20[ez] = wsum3<SC>(A2[k], A2[k + 1], A2[k + 2]);
     }
-    Mom m;  // z pass
+    MomR<V> m;  // z pass
     m.drho = wsum3<SC>(B00[0], B00[1], B00[2]);
-    m.jz = B00[2] - B00[0];
-    m.pzz = B00[2] + B00[0];
+    m.jz = vsub(B00[2], B00[0]);
+    m.pzz = vadd(B00[2], B00[0]);
     m.jy = wsum3<SC>(B01[0], B01[1], B01[2]);
-    m.pyz = B01[2] - B01[0];
+    m.nyz = vsub(B01[0], B01[2]);
     m.pyy = wsum3<SC>(B02[0], B02[1], B02[2]);
     m.jx = wsum3<SC>(B10[0], B10[1], B10[2]);
-    m.pxz = B10[2] - B10[0];
-    m.pxy = wsum3<SC>(B11[0], B11[1], B11[2]);
+    m.nxz = vsub(B10[0], B10[2]);
+    m.nxy = wsum3<SC>(B11[0], B11[1], B11[2]);
     m.pxx = wsum3<SC>(B20[0], B20[1], B20[2]);
-    if (SC && Codec<ST>::K != 1.0f) {
-        constexpr float ik = 1.0f / Codec<ST>::K;
-        m.drho *= ik; m.jx *= ik; m.jy *= ik; m.jz *= ik; m.pxx *= ik;
-        m.pyy *= ik; m.pzz *= ik; m.pxy *= ik; m.pxz *= ik; m.pyz *= ik;
-    }
     return m;
 }
 
-// Macroscopic quantities from the scaled moments (the tilde quantities are
-// 216 times the physical ones):
+// Macroscopic quantities from the raw moments (tilde: 216 times physical):
 //   drho = drho~ / 216, rho = 1 + drho, u = j~ / (216 + drho~),
-//   P1~ = Pi'~ - drho~ I / 3 - j~ u^T   (= 216 [Pi - rho (I/3 + u u)]).
-struct Macro {
-    float drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;  // P: scaled by 216
+//   q_ab = -K P1~_ab,  P1~ = Pi'~ - drho~ I / 3 - j~ u^T  (= 216 [Pi - rho (I/3 + u u)]).
+// K is a power of two, so taking the raw sums without dividing them by K
+// changes no bit of drho or u (216 K + K drho~ and K j~ round as the unscaled
+// sums, scaled).
+template <class V>
+struct MacroR {
+    V drho, rho, ux, uy, uz, qxx, qyy, qzz, qxy, qxz, qyz;
 };
 
-__device__ __forceinline__ Macro macro_of(const Mom &m) {
-    Macro M;
-    M.drho = m.drho * INV_SCALE;
-    M.rho = 1.0f + M.drho;
-    const float ir = __frcp_rn(SCALE + m.drho);
-    M.ux = m.jx * ir;
-    M.uy = m.jy * ir;
-    M.uz = m.jz * ir;
-    const float d3 = m.drho * (1.0f / 3.0f);
-    M.Pxx = m.pxx - d3 - m.jx * M.ux;
-    M.Pyy = m.pyy - d3 - m.jy * M.uy;
-    M.Pzz = m.pzz - d3 - m.jz * M.uz;
-    M.Pxy = m.pxy - m.jx * M.uy;
-    M.Pxz = m.pxz - m.jx * M.uz;
-    M.Pyz = m.pyz - m.jy * M.uz;
+template <int ST, class V>
+__device__ __forceinline__ MacroR<V> macro_raw(const MomR<V> &m) {
+    constexpr float K = Codec<ST>::K;
+    MacroR<V> M;
+    M.drho = vmul(m.drho, vs<V>(INV_SCALE / K));
+    M.rho = vadd(vs<V>(1.0f), M.drho);
+    const V ir = vrcp(vadd(vs<V>(SCALE * K), m.drho));
+    M.ux = vmul(m.jx, ir);
+    M.uy = vmul(m.jy, ir);
+    M.uz = vmul(m.jz, ir);
+    const V d3 = vmul(m.drho, vs<V>(1.0f / 3.0f));
+    M.qxx = vfma(m.jx, M.ux, vsub(d3, m.pxx));
+    M.qyy = vfma(m.jy, M.uy, vsub(d3, m.pyy));
+    M.qzz = vfma(m.jz, M.uz, vsub(d3, m.pzz));
+    M.qxy = vfma(m.jx, M.uy, m.nxy);
+    M.qxz = vfma(m.jx, M.uz, m.nxz);
+    M.qyz = vfma(m.jy, M.uz, m.nyz);
     return M;
 }
 
@@ -267,135 +300,138 @@ __device__ __forceinline__ Macro macro_of(const Mom &m) {
 // weighted basis g_p(xi) = w1(xi) H_p(xi), every term of the post-collision
 // Hermite expansion is an outer product of one 3-vector per axis, so each
 // population is rebuilt directly from per-axis vectors (here scaled by 6 so
-// that the weights 6 w1 = (1, 4, 1) are exact):
+// that the weights 6 w1 = W1 = (1, 4, 1) are exact):
 //   X(e)   = 6 sum_p u^p g_p(e)      = W1(e) (1 + a(e)),  a = (-3u+3u^2, -3u^2/2, 3u+3u^2)
 //   X'(e)  = 6 sum_p p u^(p-1) g_p(e) = (6u - 3, -12u, 6u + 3)
-//   X''(e) = 6 sum_p p(p-1) u^(p-2) g_p(e) = (6, -12, 6)
-// and, for P' = (1 - 1/tau) P1 (P1 the physical tensor),
-//   s_i = 216 (f*_i - w_i) = [rho X Y Z - W_i] + X'' [P'xx/2 Y Z]
-//         + X [P'yy/2 Y'' Z + P'zz/2 Y Z'' + P'yz Y' Z'] + X' [P'xy Y' Z + P'xz Y Z'],
-// the bracketed equilibrium deviation evaluated as W_i (rho E + drho) with
-// E = (1+a_x)(1+a_y)(1+a_z) - 1 expanded so no O(1) term cancels.  In the
-// scaled storage domains every per-axis factor is divided by W1(e), which
+//   X''(e) = 6 sum_p p(p-1) u^(p-2) g_p(e) = (6, -12, 6).
+// In the scaled storage domains every factor is divided by W1(e), which
 // divides each product by W_i: X / W1 = 1 + a, X' / W1, X'' / W1 = (6, -3, 6).
-struct AxisF {
-    float a[3], X[3], Xp[3];
+template <class V>
+struct AxisR {
+    V a[3], X[3], Xp[3];
 };
 
-template <bool SC>
-__device__ __forceinline__ AxisF axis_of(float u) {
-    AxisF f;
-    const float u2 = u * u;
-    f.a[0] = 3.0f * (u2 - u);
-    f.a[1] = -1.5f * u2;
-    f.a[2] = 3.0f * (u2 + u);
-    f.X[0] = 1.0f + f.a[0];
-    f.X[1] = SC ? 1.0f + f.a[1] : 4.0f * (1.0f + f.a[1]);
-    f.X[2] = 1.0f + f.a[2];
-    f.Xp[0] = 6.0f * u - 3.0f;
-    f.Xp[1] = SC ? -3.0f * u : -12.0f * u;
-    f.Xp[2] = 6.0f * u + 3.0f;
+template <bool SC, class V>
+__device__ __forceinline__ AxisR<V> axis_r(V u) {
+    AxisR<V> f;
+    const V u2 = vmul(u, u);
+    f.a[0] = vmul(vs<V>(3.0f), vsub(u2, u));
+    f.a[1] = vmul(vs<V>(-1.5f), u2);
+    f.a[2] = vmul(vs<V>(3.0f), vadd(u2, u));
+    f.X[0] = vadd(vs<V>(1.0f), f.a[0]);
+    f.X[1] = SC ? vadd(vs<V>(1.0f), f.a[1]) : vmul(vs<V>(4.0f), vadd(vs<V>(1.0f), f.a[1]));
+    f.X[2] = vadd(vs<V>(1.0f), f.a[2]);
+    f.Xp[0] = vfma(vs<V>(6.0f), u, vs<V>(-3.0f));
+    f.Xp[1] = vmul(vs<V>(SC ? -3.0f : -12.0f), u);
+    f.Xp[2] = vfma(vs<V>(6.0f), u, vs<V>(3.0f));
     return f;
 }
 
-// Equilibrium deviation W_i (rho E + drho) (SC: rho E + drho), times c, into s.
-template <bool SC>
-__device__ __forceinline__ void add_eq_dev(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
-                                           float drho, float c, float s[27], bool first) {
-    float sxy[9];
-#pragma unroll
-    for (int ey = 0; ey < 3; ++ey)
-#pragma unroll
-        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = fmaf(fx.a[ex], fy.a[ey], fx.a[ex] + fy.a[ey]);
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int i = k + 9 * ez;
-            const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
-            const float v = (SC ? c : c * Wq(i)) * fmaf(E, rho, drho);
-            s[i] = first ? v : s[i] + v;
-        }
-}
-
-// The same for the unforced equilibrium, whose factor c = K is a power of two:
-// K W_i (rho E + drho) = fma(E, K W_i rho, K W_i drho) bit for bit (scaling by
-// a power of two is exact), one operation less per population.
-template <bool SC>
-__device__ __forceinline__ void set_eq_dev_pow2(const AxisF &fx, const AxisF &fy, const AxisF &fz, float rho,
-                                                float drho, float K, float s[27]) {
-    float r[4], d[4];
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const float c = K * (float)(1 << (2 * w));  // K W for W = 1, 4, 16, 64
-        r[w] = c * rho;
-        d[w] = c * drho;
-    }
-    float sxy[9];
-#pragma unroll
-    for (int ey = 0; ey < 3; ++ey)
-#pragma unroll
-        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = fmaf(fx.a[ex], fy.a[ey], fx.a[ex] + fy.a[ey]);
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int i = k + 9 * ez;
-            const int lw = SC ? 0 : (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
-            const float E = fmaf(sxy[k], fz.a[ez], sxy[k] + fz.a[ez]);
-            s[i] = fmaf(E, r[lw], d[lw]);
-        }
-}
-
-// Post-collision populations of one cell in the storage domain of ST
-// (FP32: s_i = 216 (f*_i - w_i)).  forced: equilibrium part
-// (1-w) f0(u) + w f0(u + tau h) (scheme 0) or f0(u + tau h) (scheme 1), both
-// reducing to f0(u) at h = 0.
-template <int ST>
-__device__ __forceinline__ void collide_factored(const Macro &M, float omega, float tau, bool forced, float hx,
-                                                 float hy, float hz, int scheme, float s[27]) {
+// Post-collision values in the storage domain of ST (FP32: s_i = 216 (f*_i -
+// w_i); 16-bit: K s_i / W_i) from the macroscopic state, as f* = f0 + (1 -
+// 1/tau) f1 (Eq. 7) with f1 rebuilt from P1 (Eq. A.3).  With Y, Z the factors
+// X of the y and z axes, W = W1 in the storage domain (1 in the 16-bit ones),
+// Aw = W a, r = K rho, d = K drho and P' = (1 - 1/tau) P1:
+//   G0 = P'xx/2 Y Z,  G1 = P'yy/2 Y'' Z + P'zz/2 Y Z'' + P'yz Y' Z',
+//   G2 = P'xy Y' Z + P'xz Y Z'                  (off-equilibrium, per (y, z));
+// the equilibrium deviation W_i (r E + d), E = (1+a_x)(1+a_y)(1+a_z) - 1,
+// splits as Aw_x G3 + W_x G4 with G3 = r Y Z and G4 = r Aw_y Z + W_y W_z
+// (r a_z + d); and X_x = W_x + Aw_x.  So every value is three FMAs from five
+// per-(y, z) terms,
+//   s_i = X''_x G0 + Aw_x (G1 + G3) + X'_x G2 + W_x (G1 + G4),
+// with no O(1) term cancelling (G3 enters only multiplied by a_x).
+// Forced lanes take the equilibrium c1 f0(u) + c2 f0(v), v = u + tau h
+// (Eq. 15 reading: scheme 0 c = (1 - omega, omega), scheme 1 (0, 1)); the
+// unforced lanes of a forced pair pass c = (1, 0) and h = 0 and get the values
+// of the unforced form (an exact zero may come out with the other sign).
+template <int ST, class V>
+__device__ __forceinline__ void collide_rr(const MacroR<V> &M, V omega, bool anyforced, V c1, V c2, V tau,
+                                           const V h[3], V s[27]) {
     constexpr bool SC = Codec<ST>::scaled;
     constexpr float K = Codec<ST>::K;
-    const AxisF fx = axis_of<SC>(M.ux), fy = axis_of<SC>(M.uy), fz = axis_of<SC>(M.uz);
-    if (!forced) {
-        set_eq_dev_pow2<SC>(fx, fy, fz, M.rho, M.drho, K, s);
-    } else {
-        const AxisF vx = axis_of<SC>(M.ux + tau * hx), vy = axis_of<SC>(M.uy + tau * hy),
-                    vz = axis_of<SC>(M.uz + tau * hz);
-        if (scheme == 1) {
-            add_eq_dev<SC>(vx, vy, vz, M.rho, M.drho, K, s, true);
-        } else {
-            add_eq_dev<SC>(fx, fy, fz, M.rho, M.drho, K * (1.0f - omega), s, true);
-            add_eq_dev<SC>(vx, vy, vz, M.rho, M.drho, K * omega, s, false);
-        }
-    }
-    // P' = (1 - 1/tau) P1 with P1 = P1~ / 216 (times K in the storage domain)
-    const float om1 = (1.0f - omega) * (INV_SCALE * K);
-    const float hxx = 0.5f * om1 * M.Pxx, hyy = 0.5f * om1 * M.Pyy, hzz = 0.5f * om1 * M.Pzz;
-    const float pxy = om1 * M.Pxy, pxz = om1 * M.Pxz, pyz = om1 * M.Pyz;
-    const float Xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};
-    float cY[3], cZ[3], bY[3], aY[3], bZ[3];
+    const float xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};  // X''
+    const float w[3] = {1.0f, SC ? 1.0f : 4.0f, 1.0f};        // W1 in the storage domain
+    const AxisR<V> fx = axis_r<SC>(M.ux), fy = axis_r<SC>(M.uy), fz = axis_r<SC>(M.uz);
+    // P' (storage domain) = -(1 - omega) q / 216: hxx = P'xx / 2, pxy = P'xy, ...
+    const V n1 = vmul(vsub(vs<V>(1.0f), omega), vs<V>(-INV_SCALE));
+    const V nh = vmul(n1, vs<V>(0.5f));
+    const V hxx = vmul(nh, M.qxx), hyy = vmul(nh, M.qyy), hzz = vmul(nh, M.qzz);
+    const V pxy = vmul(n1, M.qxy), pxz = vmul(n1, M.qxz), pyz = vmul(n1, M.qyz);
+    V cY[3], cZ[3], bY[3], aY[3], bZ[3], HZ[3], Ax[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        cY[e] = hyy * Xpp[e];     // P'yy/2 Y''
-        cZ[e] = hzz * Xpp[e];     // P'zz/2 Z''
-        bY[e] = pyz * fy.Xp[e];   // P'yz Y'
-        aY[e] = pxy * fy.Xp[e];   // P'xy Y'
-        bZ[e] = pxz * fz.Xp[e];   // P'xz Z'
+        cY[e] = vmul(hyy, vs<V>(xpp[e]));  // P'yy/2 Y''
+        cZ[e] = vmul(hzz, vs<V>(xpp[e]));  // P'zz/2 Z''
+        bY[e] = vmul(pyz, fy.Xp[e]);       // P'yz Y'
+        aY[e] = vmul(pxy, fy.Xp[e]);       // P'xy Y'
+        bZ[e] = vmul(pxz, fz.Xp[e]);       // P'xz Z'
+        HZ[e] = vmul(hxx, fz.X[e]);        // P'xx/2 Z
+        Ax[e] = vpow2(fx.a[e], w[e]);      // Aw_x
+    }
+    const V r = vpow2(M.rho, K), d = vpow2(M.drho, K);
+    if (!anyforced) {
+        V rY[3], rA[3], Qz[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            rY[e] = vmul(r, fy.X[e]);
+            rA[e] = vpow2(vmul(r, fy.a[e]), w[e]);
+            Qz[e] = vpow2(vfma(r, fz.a[e], d), w[e]);
+        }
+#pragma unroll
+        for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+            for (int ey = 0; ey < 3; ++ey) {
+                const V Y = fy.X[ey], Z = fz.X[ez];
+                const V G0 = vmul(Y, HZ[ez]);
+                const V G1 = vfma(cY[ey], Z, vfma(Y, cZ[ez], vmul(bY[ey], fz.Xp[ez])));
+                const V G2 = vfma(aY[ey], Z, vmul(Y, bZ[ez]));
+                const V G3 = vmul(rY[ey], Z);
+                const V G4 = vfma(rA[ey], Z, vpow2(Qz[ez], w[ey]));
+                const V G13 = vadd(G1, G3), G14 = vadd(G1, G4);
+#pragma unroll
+                for (int ex = 0; ex < 3; ++ex)
+                    s[ex + 3 * ey + 9 * ez] =
+                        vfma(vs<V>(xpp[ex]), G0, vfma(Ax[ex], G13, vfma(fx.Xp[ex], G2, vpow2(G14, w[ex]))));
+            }
+        return;
+    }
+    const AxisR<V> gx = axis_r<SC>(vfma(tau, h[0], M.ux)), gy = axis_r<SC>(vfma(tau, h[1], M.uy)),
+                   gz = axis_r<SC>(vfma(tau, h[2], M.uz));
+    const V r1 = vmul(c1, r), d1 = vmul(c1, d), r2 = vmul(c2, r), d2 = vmul(c2, d);
+    V rY1[3], rA1[3], Qz1[3], rY2[3], rA2[3], Qz2[3], Bx[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        rY1[e] = vmul(r1, fy.X[e]);
+        rA1[e] = vpow2(vmul(r1, fy.a[e]), w[e]);
+        Qz1[e] = vpow2(vfma(r1, fz.a[e], d1), w[e]);
+        rY2[e] = vmul(r2, gy.X[e]);
+        rA2[e] = vpow2(vmul(r2, gy.a[e]), w[e]);
+        Qz2[e] = vpow2(vfma(r2, gz.a[e], d2), w[e]);
+        Bx[e] = vpow2(gx.a[e], w[e]);
     }
 #pragma unroll
     for (int ez = 0; ez < 3; ++ez)
 #pragma unroll
         for (int ey = 0; ey < 3; ++ey) {
-            const float G0 = hxx * (fy.X[ey] * fz.X[ez]);
-            const float G1 = fmaf(cY[ey], fz.X[ez], fmaf(fy.X[ey], cZ[ez], bY[ey] * fz.Xp[ez]));
-            const float G2 = fmaf(aY[ey], fz.X[ez], fy.X[ey] * bZ[ez]);
+            const V Y = fy.X[ey], Z = fz.X[ez];
+            const V G0 = vmul(Y, HZ[ez]);
+            const V G1 = vfma(cY[ey], Z, vfma(Y, cZ[ez], vmul(bY[ey], fz.Xp[ez])));
+            const V G2 = vfma(aY[ey], Z, vmul(Y, bZ[ez]));
+            const V G3u = vmul(rY1[ey], Z), G3v = vmul(rY2[ey], gz.X[ez]);
+            const V G4 = vadd(vfma(rA1[ey], Z, vpow2(Qz1[ez], w[ey])), vfma(rA2[ey], gz.X[ez], vpow2(Qz2[ez], w[ey])));
+            const V G13 = vadd(G1, G3u), G14 = vadd(G1, G4);
 #pragma unroll
-            for (int ex = 0; ex < 3; ++ex) {
-                const int i = ex + 3 * ey + 9 * ez;
-                s[i] = fmaf(Xpp[ex], G0, fmaf(fx.X[ex], G1, fmaf(fx.Xp[ex], G2, s[i])));
-            }
+            for (int ex = 0; ex < 3; ++ex)
+                s[ex + 3 * ey + 9 * ez] = vfma(vs<V>(xpp[ex]), G0,
+                                               vfma(Ax[ex], G13, vfma(Bx[ex], G3v, vfma(fx.Xp[ex], G2, vpow2(G14, w[ex])))));
         }
+}
+
+// Equilibrium weights of a lane (see collide_rr): unforced (1, 0); forced
+// scheme 0 (1 - omega, omega), scheme 1 (0, 1).
+__device__ __forceinline__ void forcing_weights(float omega, bool forced, int scheme, float &c1, float &c2) {
+    c1 = !forced ? 1.0f : (scheme == 1 ? 0.0f : 1.0f - omega);
+    c2 = !forced ? 0.0f : (scheme == 1 ? 1.0f : omega);
 }
 
 // Offset of window coordinate c from (box origin - margin) along one axis,
@@ -474,17 +510,18 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
             forced = true;
         }
     }
-    const Macro M = macro_of(moments27<ST>(q));
+    const MacroR<float> M = macro_raw<ST>(moments_raw<ST>(q));
     if (zl == g.nz - 1) {
         const size_t c = (size_t)y * g.nx + x;
         utop_out[c] = M.ux;
         utop_out[g.plane + c] = M.uy;
         utop_out[2 * g.plane + c] = M.uz;
     }
-    if (MODE == K1_ALLF || MODE == K1_NEAR)
-        collide_factored<ST>(M, omega, tau_of(g, zl), forced, hx, hy, hz, g.force_scheme, q);
-    else
-        collide_factored<ST>(M, omega, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
+    float c1, c2;
+    forcing_weights(omega, forced, g.force_scheme, c1, c2);
+    const float h[3] = {hx, hy, hz};
+    const float tau = (MODE == K1_ALLF || MODE == K1_NEAR) ? tau_of(g, zl) : 1.0f;
+    collide_rr<ST>(M, omega, forced, c1, c2, tau, h, q);
     const int oz = zphys(zl, ring, g.nz) * (int)g.plane;
     const int ncell = (int)g.ncell;
     typename Codec<ST>::T *d = dst + (y * g.nx + x);
@@ -506,217 +543,6 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
 // as a packed f32x2 instruction (per lane the same correctly rounded
 // operation); the x/y source indices, boundary flags and region tests are
 // shared.  A cell's result never depends on the other cell of its pair.
-typedef float2 f2;
-__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ f2 padd(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 psub(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }  // exact product
-__device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-
-template <bool SC>
-__device__ __forceinline__ f2 pwsum3(f2 a, f2 b, f2 c) {
-    return SC ? pfma(F2(4.0f), b, padd(a, c)) : padd(padd(a, b), c);
-}
-
-struct Mom2 {
-    f2 drho, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
-};
-
-template <int ST>
-__device__ __forceinline__ Mom2 moments27x2(const f2 q[27]) {
-    constexpr bool SC = Codec<ST>::scaled;
-    f2 A0[9], A1[9], A2[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const f2 a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
-        A0[k] = pwsum3<SC>(a, b, c);
-        A1[k] = psub(c, a);
-        A2[k] = padd(c, a);
-    }
-    f2 B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez) {
-        const int k = 3 * ez;
-        B00[ez] = pwsum3<SC>(A0[k], A0[k + 1], A0[k + 2]);
-        B01[ez] = psub(A0[k + 2], A0[k]);
-        B02[ez] = padd(A0[k + 2], A0[k]);
-        B10[ez] = pwsum3<SC>(A1[k], A1[k + 1], A1[k + 2]);
-        B11[ez] = psub(A1[k + 2], A1[k]);
-        B20[ez] = pwsum3<SC>(A2[k], A2[k + 1], A2[k + 2]);
-    }
-    Mom2 m;
-    m.drho = pwsum3<SC>(B00[0], B00[1], B00[2]);
-    m.jz = psub(B00[2], B00[0]);
-    m.pzz = padd(B00[2], B00[0]);
-    m.jy = pwsum3<SC>(B01[0], B01[1], B01[2]);
-    m.pyz = psub(B01[2], B01[0]);
-    m.pyy = pwsum3<SC>(B02[0], B02[1], B02[2]);
-    m.jx = pwsum3<SC>(B10[0], B10[1], B10[2]);
-    m.pxz = psub(B10[2], B10[0]);
-    m.pxy = pwsum3<SC>(B11[0], B11[1], B11[2]);
-    m.pxx = pwsum3<SC>(B20[0], B20[1], B20[2]);
-    if (SC && Codec<ST>::K != 1.0f) {
-        const f2 ik = F2(1.0f / Codec<ST>::K);
-        m.drho = pmul(m.drho, ik); m.jx = pmul(m.jx, ik); m.jy = pmul(m.jy, ik); m.jz = pmul(m.jz, ik);
-        m.pxx = pmul(m.pxx, ik); m.pyy = pmul(m.pyy, ik); m.pzz = pmul(m.pzz, ik);
-        m.pxy = pmul(m.pxy, ik); m.pxz = pmul(m.pxz, ik); m.pyz = pmul(m.pyz, ik);
-    }
-    return m;
-}
-
-struct Macro2 {
-    f2 drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;  // P: scaled by 216
-};
-
-__device__ __forceinline__ Macro2 macro_of2(const Mom2 &m) {
-    Macro2 M;
-    M.drho = pmul(m.drho, F2(INV_SCALE));
-    M.rho = padd(F2(1.0f), M.drho);
-    const f2 den = padd(F2(SCALE), m.drho);
-    const f2 ir = make_float2(__frcp_rn(den.x), __frcp_rn(den.y));
-    M.ux = pmul(m.jx, ir);
-    M.uy = pmul(m.jy, ir);
-    M.uz = pmul(m.jz, ir);
-    const f2 d3 = pmul(m.drho, F2(1.0f / 3.0f));
-    M.Pxx = psub(psub(m.pxx, d3), pmul(m.jx, M.ux));
-    M.Pyy = psub(psub(m.pyy, d3), pmul(m.jy, M.uy));
-    M.Pzz = psub(psub(m.pzz, d3), pmul(m.jz, M.uz));
-    M.Pxy = psub(m.pxy, pmul(m.jx, M.uy));
-    M.Pxz = psub(m.pxz, pmul(m.jx, M.uz));
-    M.Pyz = psub(m.pyz, pmul(m.jy, M.uz));
-    return M;
-}
-
-struct AxisF2 {
-    f2 a[3], X[3], Xp[3];
-};
-
-template <bool SC>
-__device__ __forceinline__ AxisF2 axis_of2(f2 u) {
-    AxisF2 f;
-    const f2 u2 = pmul(u, u);
-    f.a[0] = pmul(F2(3.0f), psub(u2, u));
-    f.a[1] = pmul(F2(-1.5f), u2);
-    f.a[2] = pmul(F2(3.0f), padd(u2, u));
-    f.X[0] = padd(F2(1.0f), f.a[0]);
-    f.X[1] = SC ? padd(F2(1.0f), f.a[1]) : pmul(F2(4.0f), padd(F2(1.0f), f.a[1]));
-    f.X[2] = padd(F2(1.0f), f.a[2]);
-    f.Xp[0] = pfma(F2(6.0f), u, F2(-3.0f));
-    f.Xp[1] = pmul(F2(SC ? -3.0f : -12.0f), u);
-    f.Xp[2] = pfma(F2(6.0f), u, F2(3.0f));
-    return f;
-}
-
-// c * W_i (rho E + drho) (SC: c (rho E + drho)) into s, or added to s; c per lane.
-template <bool SC>
-__device__ __forceinline__ void add_eq_dev2(const AxisF2 &fx, const AxisF2 &fy, const AxisF2 &fz, f2 rho, f2 drho,
-                                            f2 c, f2 s[27], bool first) {
-    f2 cw[4];  // c W for W = 1, 4, 16, 64
-    cw[0] = c;
-    if (!SC) {
-        cw[1] = pmul(c, F2(4.0f));
-        cw[2] = pmul(c, F2(16.0f));
-        cw[3] = pmul(c, F2(64.0f));
-    }
-    f2 sxy[9];
-#pragma unroll
-    for (int ey = 0; ey < 3; ++ey)
-#pragma unroll
-        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = pfma(fx.a[ex], fy.a[ey], padd(fx.a[ex], fy.a[ey]));
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int i = k + 9 * ez;
-            const int lw = (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
-            const f2 E = pfma(sxy[k], fz.a[ez], padd(sxy[k], fz.a[ez]));
-            const f2 v = pmul(SC ? c : cw[lw], pfma(E, rho, drho));
-            s[i] = first ? v : padd(s[i], v);
-        }
-}
-
-// set_eq_dev_pow2 for a cell pair: the unforced equilibrium deviation
-// K W_i (rho E + drho) as fma(E, K W_i rho, K W_i drho), bit for bit equal.
-template <bool SC>
-__device__ __forceinline__ void set_eq_dev2_pow2(const AxisF2 &fx, const AxisF2 &fy, const AxisF2 &fz, f2 rho,
-                                                 f2 drho, float K, f2 s[27]) {
-    f2 r[4], d[4];
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        if (SC && w > 0) continue;
-        const f2 c = F2(K * (float)(1 << (2 * w)));  // K W for W = 1, 4, 16, 64
-        r[w] = pmul(c, rho);
-        d[w] = pmul(c, drho);
-    }
-    f2 sxy[9];
-#pragma unroll
-    for (int ey = 0; ey < 3; ++ey)
-#pragma unroll
-        for (int ex = 0; ex < 3; ++ex) sxy[ex + 3 * ey] = pfma(fx.a[ex], fy.a[ey], padd(fx.a[ex], fy.a[ey]));
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int i = k + 9 * ez;
-            const int lw = SC ? 0 : (i % 3 == 1) + ((i / 3) % 3 == 1) + (i / 9 == 1);  // log4 W_i
-            const f2 E = pfma(sxy[k], fz.a[ez], padd(sxy[k], fz.a[ez]));
-            s[i] = pfma(E, r[lw], d[lw]);
-        }
-}
-
-// Post-collision populations of two cells in the storage domain of ST.
-// forced lanes take (1-w) f0(u) + w f0(u + tau h) (scheme 0) or
-// f0(u + tau h) (scheme 1); other lanes f0(u) (their h is zero, and their
-// scheme-0 weights are 1 and 0, so the shifted term adds an exact zero).
-template <int ST>
-__device__ __forceinline__ void collide_pair(const Macro2 &M, f2 omega, f2 tau, bool anyforced, bool fa, bool fb,
-                                             f2 h[3], int scheme, f2 s[27]) {
-    constexpr bool SC = Codec<ST>::scaled;
-    constexpr float K = Codec<ST>::K;
-    const AxisF2 fx = axis_of2<SC>(M.ux), fy = axis_of2<SC>(M.uy), fz = axis_of2<SC>(M.uz);
-    if (!anyforced) {
-        set_eq_dev2_pow2<SC>(fx, fy, fz, M.rho, M.drho, K, s);
-    } else {
-        const AxisF2 vx = axis_of2<SC>(pfma(tau, h[0], M.ux)), vy = axis_of2<SC>(pfma(tau, h[1], M.uy)),
-                     vz = axis_of2<SC>(pfma(tau, h[2], M.uz));
-        if (scheme == 1) {
-            add_eq_dev2<SC>(vx, vy, vz, M.rho, M.drho, F2(K), s, true);
-        } else {
-            const f2 w1 = pmul(F2(K), psub(F2(1.0f), omega)), w2 = pmul(F2(K), omega);
-            const f2 c1 = make_float2(fa ? w1.x : K, fb ? w1.y : K);
-            const f2 c2 = make_float2(fa ? w2.x : 0.0f, fb ? w2.y : 0.0f);
-            add_eq_dev2<SC>(fx, fy, fz, M.rho, M.drho, c1, s, true);
-            add_eq_dev2<SC>(vx, vy, vz, M.rho, M.drho, c2, s, false);
-        }
-    }
-    const f2 om1 = pmul(psub(F2(1.0f), omega), F2(INV_SCALE * K));
-    const f2 hom = pmul(F2(0.5f), om1);
-    const f2 hxx = pmul(hom, M.Pxx), hyy = pmul(hom, M.Pyy), hzz = pmul(hom, M.Pzz);
-    const f2 pxy = pmul(om1, M.Pxy), pxz = pmul(om1, M.Pxz), pyz = pmul(om1, M.Pyz);
-    const float xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};
-    f2 cY[3], cZ[3], bY[3], aY[3], bZ[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        cY[e] = pmul(hyy, F2(xpp[e]));
-        cZ[e] = pmul(hzz, F2(xpp[e]));
-        bY[e] = pmul(pyz, fy.Xp[e]);
-        aY[e] = pmul(pxy, fy.Xp[e]);
-        bZ[e] = pmul(pxz, fz.Xp[e]);
-    }
-#pragma unroll
-    for (int ez = 0; ez < 3; ++ez)
-#pragma unroll
-        for (int ey = 0; ey < 3; ++ey) {
-            const f2 G0 = pmul(hxx, pmul(fy.X[ey], fz.X[ez]));
-            const f2 G1 = pfma(cY[ey], fz.X[ez], pfma(fy.X[ey], cZ[ez], pmul(bY[ey], fz.Xp[ez])));
-            const f2 G2 = pfma(aY[ey], fz.X[ez], pmul(fy.X[ey], bZ[ez]));
-#pragma unroll
-            for (int ex = 0; ex < 3; ++ex) {
-                const int i = ex + 3 * ey + 9 * ez;
-                s[i] = pfma(F2(xpp[ex]), G0, pfma(fx.X[ex], G1, pfma(fx.Xp[ex], G2, s[i])));
-            }
-        }
-}
 
 // Source plane of logical plane zl for velocity index ez (= xi_z + 1): 0 and
 // the physical plane, 1 bounce-back, 2 pressure ghost, 3 the entering plane.
@@ -884,7 +710,7 @@ __device__ __forceinline__ void k1_pair_collide_store(const Geom &g, typename Co
         }
         tau = make_float2(tau_of(g, z[0]), tau_of(g, z[1]));
     }
-    const Macro2 M = macro_of2(moments27x2<ST>(q));
+    const MacroR<f2> M = macro_raw<ST>(moments_raw<ST>(q));
 #pragma unroll
     for (int l = 0; l < 2; ++l)
         if (on[l] && z[l] == g.nz - 1) {
@@ -893,8 +719,10 @@ __device__ __forceinline__ void k1_pair_collide_store(const Geom &g, typename Co
             utop_out[g.plane + c] = l ? M.uy.y : M.uy.x;
             utop_out[2 * g.plane + c] = l ? M.uz.y : M.uz.x;
         }
-    collide_pair<ST>(M, omega, tau, forced[0] || forced[1], forced[0], forced[1], h,
-                     (MODE == K1_ALLF || MODE == K1_NEAR) ? g.force_scheme : 0, q);
+    f2 c1, c2;
+    forcing_weights(omega.x, forced[0], g.force_scheme, c1.x, c2.x);
+    forcing_weights(omega.y, forced[1], g.force_scheme, c1.y, c2.y);
+    collide_rr<ST>(M, omega, forced[0] || forced[1], c1, c2, tau, h, q);
     if (!STORE) return;  // the caller stores q itself
     const int ncell = (int)g.ncell;
     const int oa = zphys(z[0], ring, g.nz) * (int)g.plane, ob = zphys(z[1], ring, g.nz) * (int)g.plane;

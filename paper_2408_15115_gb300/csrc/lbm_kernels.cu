@@ -36,15 +36,16 @@ __global__ void k_init_equilibrium(Geom g, typename Codec<ST>::T *__restrict__ d
                                    const double *__restrict__ u, float *__restrict__ utop) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
-    Macro M;
+    MacroR<float> M;
     M.drho = drho ? (float)drho[c] : 0.0f;
     M.rho = (float)(1.0 + (drho ? drho[c] : 0.0));
     M.ux = u ? (float)u[3 * c] : 0.0f;
     M.uy = u ? (float)u[3 * c + 1] : 0.0f;
     M.uz = u ? (float)u[3 * c + 2] : 0.0f;
-    M.Pxx = M.Pyy = M.Pzz = M.Pxy = M.Pxz = M.Pyz = 0.0f;
+    M.qxx = M.qyy = M.qzz = M.qxy = M.qxz = M.qyz = 0.0f;
     float q[27];
-    collide_factored<ST>(M, 1.0f, 1.0f, false, 0.0f, 0.0f, 0.0f, 0, q);
+    const float h[3] = {0.0f, 0.0f, 0.0f};
+    collide_rr<ST>(M, 1.0f, false, 1.0f, 0.0f, 1.0f, h, q);
 #pragma unroll
     for (int i = 0; i < 27; ++i) Codec<ST>::store(dst + (size_t)i * g.ncell + c, q[i]);
     const long long z = c / g.plane;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(128) k_macro(Geom g, const typename Codec<ST>:
             out[(size_t)i * g.ncell + c] = q[i] * ((Codec<ST>::scaled ? Wq(i) / Codec<ST>::K : 1.0f) * INV_SCALE);
         return;
     }
-    const Macro M = macro_of(moments27<ST>(q));
+    const MacroR<float> M = macro_raw<ST>(moments_raw<ST>(q));
     out[c] = M.rho;
     out[g.ncell + c] = M.ux;
     out[2 * g.ncell + c] = M.uy;
