@@ -184,21 +184,63 @@ __device__ __forceinline__ void pull27(const Geom &g, const typename Codec<ST>::
 // ---------------------------------------------------------------------------
 // Lane-generic arithmetic of the moments and the collision: V = float (one
 // cell) or f2 (two cells, one packed f32x2 instruction per operation).  Every
-// operation is an explicitly rounded intrinsic (nothing is contracted), and a
-// packed operation rounds each lane as the scalar one does, so a cell gets the
-// same bits whichever form computes it and whatever cell it is paired with.
+// operation is a hand-written add/sub/mul/fma.rn instruction (.f32 or
+// .f32x2), which the compiler keeps as written: with explicit rounding it
+// fuses nothing.  (The packed intrinsics of CUDA 13.0 were measured to fuse a
+// multiply whose only use is an add into one FMA, even under -fmad=false, so
+// the scalar and packed forms of the same source rounded differently.)  A
+// packed instruction rounds each lane as the scalar one does, so a cell gets
+// the same bits whichever form computes it and whatever cell it is paired with.
 typedef float2 f2;
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
 
-__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) {
+    float r;
+    asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float vsub(float a, float b) {
+    float r;
+    asm("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float vmul(float a, float b) {
+    float r;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float vfma(float a, float b, float c) {
+    float r;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 __device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
-__device__ __forceinline__ f2 vadd(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 vsub(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.0f), a); }  // exact product
-__device__ __forceinline__ f2 vmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ unsigned long long f2_u64(f2 a) {
+    return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ f2 u64_f2(unsigned long long a) {
+    return make_float2(__uint_as_float((unsigned)a), __uint_as_float((unsigned)(a >> 32)));
+}
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_u64(a)), "l"(f2_u64(b)));
+    return u64_f2(r);
+}
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_u64(a)), "l"(f2_u64(b)));
+    return u64_f2(r);
+}
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_u64(a)), "l"(f2_u64(b)));
+    return u64_f2(r);
+}
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_u64(a)), "l"(f2_u64(b)), "l"(f2_u64(c)));
+    return u64_f2(r);
+}
 __device__ __forceinline__ f2 vrcp(f2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
 template <class V>
 __device__ __forceinline__ V vs(float a);
@@ -211,16 +253,16 @@ template <class V>
 __device__ __forceinline__ V vpow2(V a, float c) { return c == 1.0f ? a : vmul(a, vs<V>(c)); }
 
 // Raw moments of the stored values up to second order, by three separable
-// 3-point passes: drho = sum r, j = sum xi r, the diagonal Pi'_aa = sum xi_a^2 r
-// and the off-diagonal ones negated, n_ab = -sum xi_a xi_b r (free here, and it
-// saves a negation later).  FP32 storage holds r_i = s_i = 216 (f_i - w_i); the
-// 16-bit domains r_i = K s_i / W_i carry the axis weights W1 = (1, 4, 1) in the
-// sums that need them (the 4 sits on xi = 0, where the xi-weighted sums vanish
-// anyway).  Every moment here is thus K times the scaled moment, which is 216
-// times the physical one (K = 1 for FP32 and BF16).
+// 3-point passes: drho = sum r, the momentum negated (nj = -sum xi r, which
+// costs nothing here and keeps the stress below free of a multiply feeding an
+// add) and Pi'_ab = sum xi_a xi_b r.  FP32 storage holds r_i = s_i = 216 (f_i
+// - w_i); the 16-bit domains r_i = K s_i / W_i carry the axis weights W1 = (1,
+// 4, 1) in the sums that need them (the 4 sits on xi = 0, where the
+// xi-weighted sums vanish anyway).  Every moment here is thus K times the
+// scaled moment, which is 216 times the physical one (K = 1 for FP32 and BF16).
 template <class V>
 struct MomR {
-    V drho, jx, jy, jz, pxx, pyy, pzz, nxy, nxz, nyz;
+    V drho, njx, njy, njz, pxx, pyy, pzz, pxy, pxz, pyz;
 };
 
 // a + W1(1) b + c in the storage domain
@@ -237,7 +279,7 @@ __device__ __forceinline__ MomR<V> moments_raw(const V q[27]) {
     for (int k = 0; k < 9; ++k) {  // x pass, k = ey + 3 ez
         const V a = q[3 * k], b = q[3 * k + 1], c = q[3 * k + 2];
         A0[k] = wsum3<SC>(a, b, c);
-        A1[k] = vsub(c, a);
+        A1[k] = vsub(a, c);  // -sum xi_x r
         A2[k] = vadd(c, a);
     }
     V B00[3], B01[3], B02[3], B10[3], B11[3], B20[3];
@@ -245,35 +287,36 @@ __device__ __forceinline__ MomR<V> moments_raw(const V q[27]) {
     for (int ez = 0; ez < 3; ++ez) {  // y pass
         const int k = 3 * ez;
         B00[ez] = wsum3<SC>(A0[k], A0[k + 1], A0[k + 2]);
-        B01[ez] = vsub(A0[k + 2], A0[k]);
+        B01[ez] = vsub(A0[k], A0[k + 2]);  // -sum xi_y
         B02[ez] = vadd(A0[k + 2], A0[k]);
         B10[ez] = wsum3<SC>(A1[k], A1[k + 1], A1[k + 2]);
-        B11[ez] = vsub(A1[k], A1[k + 2]);  // -sum xi_y (sum xi_x r)
+        B11[ez] = vsub(A1[k], A1[k + 2]);  // +sum xi_x xi_y
         B20[ez] = wsum3<SC>(A2[k], A2[k + 1], A2[k + 2]);
     }
     MomR<V> m;  // z pass
     m.drho = wsum3<SC>(B00[0], B00[1], B00[2]);
-    m.jz = vsub(B00[2], B00[0]);
+    m.njz = vsub(B00[0], B00[2]);
     m.pzz = vadd(B00[2], B00[0]);
-    m.jy = wsum3<SC>(B01[0], B01[1], B01[2]);
-    m.nyz = vsub(B01[0], B01[2]);
+    m.njy = wsum3<SC>(B01[0], B01[1], B01[2]);
+    m.pyz = vsub(B01[0], B01[2]);
     m.pyy = wsum3<SC>(B02[0], B02[1], B02[2]);
-    m.jx = wsum3<SC>(B10[0], B10[1], B10[2]);
-    m.nxz = vsub(B10[0], B10[2]);
-    m.nxy = wsum3<SC>(B11[0], B11[1], B11[2]);
+    m.njx = wsum3<SC>(B10[0], B10[1], B10[2]);
+    m.pxz = vsub(B10[0], B10[2]);
+    m.pxy = wsum3<SC>(B11[0], B11[1], B11[2]);
     m.pxx = wsum3<SC>(B20[0], B20[1], B20[2]);
     return m;
 }
 
 // Macroscopic quantities from the raw moments (tilde: 216 times physical):
 //   drho = drho~ / 216, rho = 1 + drho, u = j~ / (216 + drho~),
-//   q_ab = -K P1~_ab,  P1~ = Pi'~ - drho~ I / 3 - j~ u^T  (= 216 [Pi - rho (I/3 + u u)]).
+//   P_ab = K P1~_ab,  P1~ = Pi'~ - drho~ I / 3 - j~ u^T  (= 216 [Pi - rho (I/3 + u u)]).
 // K is a power of two, so taking the raw sums without dividing them by K
 // changes no bit of drho or u (216 K + K drho~ and K j~ round as the unscaled
-// sums, scaled).
+// sums, scaled); u = (-j)(-1 / (216 K + drho)) has the bits of j / (...).
+// Each stress component is one or two FMAs, so it is rounded once or twice.
 template <class V>
 struct MacroR {
-    V drho, rho, ux, uy, uz, qxx, qyy, qzz, qxy, qxz, qyz;
+    V drho, rho, ux, uy, uz, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 };
 
 template <int ST, class V>
@@ -281,18 +324,17 @@ __device__ __forceinline__ MacroR<V> macro_raw(const MomR<V> &m) {
     constexpr float K = Codec<ST>::K;
     MacroR<V> M;
     M.drho = vmul(m.drho, vs<V>(INV_SCALE / K));
-    M.rho = vadd(vs<V>(1.0f), M.drho);
-    const V ir = vrcp(vadd(vs<V>(SCALE * K), m.drho));
-    M.ux = vmul(m.jx, ir);
-    M.uy = vmul(m.jy, ir);
-    M.uz = vmul(m.jz, ir);
-    const V d3 = vmul(m.drho, vs<V>(1.0f / 3.0f));
-    M.qxx = vfma(m.jx, M.ux, vsub(d3, m.pxx));
-    M.qyy = vfma(m.jy, M.uy, vsub(d3, m.pyy));
-    M.qzz = vfma(m.jz, M.uz, vsub(d3, m.pzz));
-    M.qxy = vfma(m.jx, M.uy, m.nxy);
-    M.qxz = vfma(m.jx, M.uz, m.nxz);
-    M.qyz = vfma(m.jy, M.uz, m.nyz);
+    M.rho = vfma(m.drho, vs<V>(INV_SCALE / K), vs<V>(1.0f));
+    const V nir = vrcp(vsub(vs<V>(-SCALE * K), m.drho));
+    M.ux = vmul(m.njx, nir);
+    M.uy = vmul(m.njy, nir);
+    M.uz = vmul(m.njz, nir);
+    M.Pxx = vfma(m.njx, M.ux, vfma(m.drho, vs<V>(-1.0f / 3.0f), m.pxx));
+    M.Pyy = vfma(m.njy, M.uy, vfma(m.drho, vs<V>(-1.0f / 3.0f), m.pyy));
+    M.Pzz = vfma(m.njz, M.uz, vfma(m.drho, vs<V>(-1.0f / 3.0f), m.pzz));
+    M.Pxy = vfma(m.njx, M.uy, m.pxy);
+    M.Pxz = vfma(m.njx, M.uz, m.pxz);
+    M.Pyz = vfma(m.njy, M.uz, m.pyz);
     return M;
 }
 
@@ -314,13 +356,13 @@ struct AxisR {
 template <bool SC, class V>
 __device__ __forceinline__ AxisR<V> axis_r(V u) {
     AxisR<V> f;
-    const V u2 = vmul(u, u);
-    f.a[0] = vmul(vs<V>(3.0f), vsub(u2, u));
+    const V u2 = vmul(u, u), tm = vfma(u, u, vmul(u, vs<V>(-1.0f))), tp = vfma(u, u, u);  // u^2 -+ u
+    f.a[0] = vmul(vs<V>(3.0f), tm);
     f.a[1] = vmul(vs<V>(-1.5f), u2);
-    f.a[2] = vmul(vs<V>(3.0f), vadd(u2, u));
-    f.X[0] = vadd(vs<V>(1.0f), f.a[0]);
-    f.X[1] = SC ? vadd(vs<V>(1.0f), f.a[1]) : vmul(vs<V>(4.0f), vadd(vs<V>(1.0f), f.a[1]));
-    f.X[2] = vadd(vs<V>(1.0f), f.a[2]);
+    f.a[2] = vmul(vs<V>(3.0f), tp);
+    f.X[0] = vfma(vs<V>(3.0f), tm, vs<V>(1.0f));
+    f.X[1] = SC ? vfma(vs<V>(-1.5f), u2, vs<V>(1.0f)) : vmul(vs<V>(4.0f), vfma(vs<V>(-1.5f), u2, vs<V>(1.0f)));
+    f.X[2] = vfma(vs<V>(3.0f), tp, vs<V>(1.0f));
     f.Xp[0] = vfma(vs<V>(6.0f), u, vs<V>(-3.0f));
     f.Xp[1] = vmul(vs<V>(SC ? -3.0f : -12.0f), u);
     f.Xp[2] = vfma(vs<V>(6.0f), u, vs<V>(3.0f));
@@ -352,11 +394,11 @@ __device__ __forceinline__ void collide_rr(const MacroR<V> &M, V omega, bool any
     const float xpp[3] = {6.0f, SC ? -3.0f : -12.0f, 6.0f};  // X''
     const float w[3] = {1.0f, SC ? 1.0f : 4.0f, 1.0f};        // W1 in the storage domain
     const AxisR<V> fx = axis_r<SC>(M.ux), fy = axis_r<SC>(M.uy), fz = axis_r<SC>(M.uz);
-    // P' (storage domain) = -(1 - omega) q / 216: hxx = P'xx / 2, pxy = P'xy, ...
-    const V n1 = vmul(vsub(vs<V>(1.0f), omega), vs<V>(-INV_SCALE));
-    const V nh = vmul(n1, vs<V>(0.5f));
-    const V hxx = vmul(nh, M.qxx), hyy = vmul(nh, M.qyy), hzz = vmul(nh, M.qzz);
-    const V pxy = vmul(n1, M.qxy), pxz = vmul(n1, M.qxz), pyz = vmul(n1, M.qyz);
+    // P' (storage domain) = (1 - omega) P / 216: hxx = P'xx / 2, pxy = P'xy, ...
+    const V o1 = vmul(vsub(vs<V>(1.0f), omega), vs<V>(INV_SCALE));
+    const V oh = vmul(o1, vs<V>(0.5f));
+    const V hxx = vmul(oh, M.Pxx), hyy = vmul(oh, M.Pyy), hzz = vmul(oh, M.Pzz);
+    const V pxy = vmul(o1, M.Pxy), pxz = vmul(o1, M.Pxz), pyz = vmul(o1, M.Pyz);
     V cY[3], cZ[3], bY[3], aY[3], bZ[3], HZ[3], Ax[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -385,9 +427,8 @@ __device__ __forceinline__ void collide_rr(const MacroR<V> &M, V omega, bool any
                 const V G0 = vmul(Y, HZ[ez]);
                 const V G1 = vfma(cY[ey], Z, vfma(Y, cZ[ez], vmul(bY[ey], fz.Xp[ez])));
                 const V G2 = vfma(aY[ey], Z, vmul(Y, bZ[ez]));
-                const V G3 = vmul(rY[ey], Z);
                 const V G4 = vfma(rA[ey], Z, vpow2(Qz[ez], w[ey]));
-                const V G13 = vadd(G1, G3), G14 = vadd(G1, G4);
+                const V G13 = vfma(rY[ey], Z, G1), G14 = vadd(G1, G4);  // G1 + G3, G1 + G4
 #pragma unroll
                 for (int ex = 0; ex < 3; ++ex)
                     s[ex + 3 * ey + 9 * ez] =
@@ -417,9 +458,9 @@ __device__ __forceinline__ void collide_rr(const MacroR<V> &M, V omega, bool any
             const V G0 = vmul(Y, HZ[ez]);
             const V G1 = vfma(cY[ey], Z, vfma(Y, cZ[ez], vmul(bY[ey], fz.Xp[ez])));
             const V G2 = vfma(aY[ey], Z, vmul(Y, bZ[ez]));
-            const V G3u = vmul(rY1[ey], Z), G3v = vmul(rY2[ey], gz.X[ez]);
+            const V G3v = vmul(rY2[ey], gz.X[ez]);
             const V G4 = vadd(vfma(rA1[ey], Z, vpow2(Qz1[ez], w[ey])), vfma(rA2[ey], gz.X[ez], vpow2(Qz2[ez], w[ey])));
-            const V G13 = vadd(G1, G3u), G14 = vadd(G1, G4);
+            const V G13 = vfma(rY1[ey], Z, G1), G14 = vadd(G1, G4);
 #pragma unroll
             for (int ex = 0; ex < 3; ++ex)
                 s[ex + 3 * ey + 9 * ez] = vfma(vs<V>(xpp[ex]), G0,

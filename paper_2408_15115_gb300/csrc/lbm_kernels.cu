@@ -42,7 +42,7 @@ __global__ void k_init_equilibrium(Geom g, typename Codec<ST>::T *__restrict__ d
     M.ux = u ? (float)u[3 * c] : 0.0f;
     M.uy = u ? (float)u[3 * c + 1] : 0.0f;
     M.uz = u ? (float)u[3 * c + 2] : 0.0f;
-    M.qxx = M.qyy = M.qzz = M.qxy = M.qxz = M.qyz = 0.0f;
+    M.Pxx = M.Pyy = M.Pzz = M.Pxy = M.Pxz = M.Pyz = 0.0f;
     float q[27];
     const float h[3] = {0.0f, 0.0f, 0.0f};
     collide_rr<ST>(M, 1.0f, false, 1.0f, 0.0f, 1.0f, h, q);

@@ -18,10 +18,10 @@
 // (x0 + 2 tx, x0 + 2 tx + 1) of row y0 + (ty & 1), plane z0 + (ty >> 1).
 // Tiles whose sources all lie on interior planes,
 // away from the plane entering the ring window, closed x / y faces and (far-
-// cell launches) the near region take this path; the others run the plain
-// cell-pair code over the same cells (thread t: column t of the tile's 128,
-// both planes).  Both are the same arithmetic
-// (k1_pair_collide_store), so results are bitwise equal to the plain kernel.
+// cell launches) the near region take this path; the others run the one-cell
+// code over the same cells (thread t: column t of the tile's 128, both
+// planes).  Both are the same arithmetic
+// (the lane-generic collision), so results are bitwise equal to the plain kernel.
 // BF16 with stochastic rounding keeps the plain kernel: its random bits are
 // keyed to the (z, z + 1) pairing.
 #include "lbm_cell.cuh"
@@ -102,10 +102,13 @@ __global__ void __launch_bounds__(128, 5)
                xp_meets_near(z0, XP_TZ, S.box_lo[2], S.box_lo_w[2], box.Bz + 2 * NEAR_GROW, g.nz,
                              g.bc_bottom == BC_PERIODIC));
     if (!ok) {
-        // the plain cell-pair path: thread t takes column t of the tile (inline:
-        // an out-of-line call measured 12 % slower for the whole kernel)
+        // the one-cell path: thread t takes column t of the tile, both planes.
+        // Inline and scalar: as an out-of-line call the whole kernel measured
+        // 12 % slower, with the cell-pair code inline 9 % slower (its register
+        // use shapes the x-pair path's allocation).
         const int t = ty * 32 + tx;
-        k1_pair<ST, MODE>(g, src, dst, utop_in, utop_out, S, hbox, box, x0 + t % XP_TX, y0 + t / XP_TX, z0);
+        k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, S, hbox, box, x0 + t % XP_TX, y0 + t / XP_TX, z0);
+        k1_cell<ST, MODE>(g, src, dst, utop_in, utop_out, S, hbox, box, x0 + t % XP_TX, y0 + t / XP_TX, z0 + 1);
         return;
     }
     const int x = x0 + 2 * tx, y = y0 + (ty & 1), zl = z0 + (ty >> 1);

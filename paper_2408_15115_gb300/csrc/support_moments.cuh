@@ -181,18 +181,18 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
     pull27<ST>(g, src, c[0], c[1], c[2], st->s[slot].ring, st->s[slot].reseed, utop_in, q);
     const MacroR<float> M = macro_raw<ST>(moments_raw<ST>(q));
     const float tau = tau_of(g, c[2]);
-    // (1/(2 tau) - 1) P1 with P1 = P1~ / 216 = -q / (216 K)
-    const float k2 = (1.0f - 0.5f / tau) * (INV_SCALE / Codec<ST>::K);
+    // (1/(2 tau) - 1) P1 with P1 = P1~ / 216 = P / (216 K)
+    const float k2 = (0.5f / tau - 1.0f) * (INV_SCALE / Codec<ST>::K);
     const float p = M.drho * (1.0f / 3.0f);
     ba.u[b] = M.ux;
     ba.u[box.nbox + b] = M.uy;
     ba.u[2 * box.nbox + b] = M.uz;
-    ba.s[b] = -p + k2 * M.qxx;
-    ba.s[box.nbox + b] = -p + k2 * M.qyy;
-    ba.s[2 * box.nbox + b] = -p + k2 * M.qzz;
-    ba.s[3 * box.nbox + b] = k2 * M.qxy;
-    ba.s[4 * box.nbox + b] = k2 * M.qxz;
-    ba.s[5 * box.nbox + b] = k2 * M.qyz;
+    ba.s[b] = -p + k2 * M.Pxx;
+    ba.s[box.nbox + b] = -p + k2 * M.Pyy;
+    ba.s[2 * box.nbox + b] = -p + k2 * M.Pzz;
+    ba.s[3 * box.nbox + b] = k2 * M.Pxy;
+    ba.s[4 * box.nbox + b] = k2 * M.Pxz;
+    ba.s[5 * box.nbox + b] = k2 * M.Pyz;
     ba.p[b] = p;
 }
 
