@@ -7,7 +7,8 @@
 // with prefix[r] <= b < prefix[r + 1].  The step graph has the shape of the
 // single-run graph with every node covering all runs:
 //
-//   batch stream: --fork--> bulk collide+stream (far cells of every run) --> join
+//   batch stream: --fork--> bulk collide+stream (far cells: FP32 and stochastically
+//                           rounded runs, then 16-bit runs on x-pairs) ------> join
 //   side stream :       \-> near collide+stream -> particle + markers
 //                           -> support moments + tile lists -> interpolation
 //                           + rows of A -> cycles -> spread ---------------^
@@ -28,7 +29,7 @@ using namespace turret;
 
 namespace {
 
-enum { T_BULK = 0, T_NEAR, T_PM, T_MB, T_IP, T_CYC, T_SP, T_COUNT };
+enum { T_BULK = 0, T_NEAR, T_PM, T_MB, T_IP, T_CYC, T_SP, T_BULK16, T_COUNT };
 
 std::string g_batch_init_err;
 
@@ -97,7 +98,8 @@ static bool build_tables(turret_batch *b) {
                 case T_MB: k = blocks_box_moments_bin(R); break;
                 case T_IP: k = blocks_interp0(R); break;
                 case T_CYC: k = blocks_cycle(R); break;
-                default: k = blocks_spread(R); break;
+                case T_SP: k = blocks_spread(R); break;
+                default: k = blocks_bulk16(R); break;
             }
             b->h_prefix[(size_t)t * (n + 1) + r] = (int)acc;
             acc += k;
@@ -133,6 +135,7 @@ static cudaError_t upload(turret_batch *b) {
         D.storage = R.storage;
         D.split = R.split;
         D.tx = R.tx;
+        D.tx16 = bulk16_tile(R);
     }
     CE(cudaMemcpyAsync(b->d_runs, b->h_runs.data(), b->n * sizeof(RunDesc), cudaMemcpyHostToDevice, b->stream));
     CE(cudaMemcpyAsync(b->d_cdesc, b->h_cdesc.data(), b->n * sizeof(CollideDesc), cudaMemcpyHostToDevice,
@@ -285,6 +288,7 @@ static cudaError_t batch_enqueue(turret_batch *b, int p) {
     CE(cudaEventRecord(b->ev_pred, b->aux));
     CE(launch_batch_collide(PHASE_BULK, b->d_cdesc, tab(T_BULK), n, p, b->total[T_BULK], b->threads, b->minb,
                             b->stream));
+    CE(launch_batch_collide(PHASE_BULK16, b->d_cdesc, tab(T_BULK16), n, p, b->total[T_BULK16], 128, 5, b->stream));
     CE(launch_batch_collide(PHASE_NEAR, b->d_cdesc, tab(T_NEAR), n, p, b->total[T_NEAR], b->threads, 1, b->side));
     CE(cudaStreamWaitEvent(b->side, b->ev_pred, 0));
     CE(launch_batch_box_moments_bin(R, tab(T_MB), n, p, b->total[T_MB], b->side));

@@ -1,6 +1,7 @@
 // lbm_batch.cu -- collide+stream with a chosen tile (the autotuner's timing
 // kernel) and the batched collide+stream and support-moment launches over
 // the (run, block) table of many independent runs.
+#include "lbm_xpair.cuh"
 #include "support_moments.cuh"
 
 namespace turret {
@@ -27,7 +28,8 @@ __global__ void __launch_bounds__(256, MINB) k_collide_tiled(Geom g, const typen
 // Block b belongs to the run r with prefix[r] <= b < prefix[r + 1]; every run
 // keeps its own storage type, window, boundary conditions, relaxation times
 // and tile, read from its descriptor.  PHASE_BULK: the far cells of runs that
-// split (no blocks for the others); PHASE_NEAR: the near region of runs that
+// split (no blocks for the others; 16-bit round-to-nearest runs have theirs
+// in the PHASE_BULK16 launch); PHASE_NEAR: the near region of runs that
 // split, the whole window (with forcing) of runs that do not.
 template <int PHASE, int ST>
 __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb) {
@@ -80,6 +82,46 @@ __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *
     }
 }
 
+// Batched far-cell K1 of 16-bit round-to-nearest runs on x-adjacent pairs
+// (lbm_xpair.cuh), with the register budget of the single-window x-pair
+// kernel (96 registers, five 128-thread blocks per SM) rather than the FP32
+// one the shared launch is held to.  A block owns a tile of tx16 x (128 /
+// tx16) x 2 cells: tx16 / 2 pairs per row, then the rows, then the two planes
+// over its threads; tiles the x-pair path does not admit run the one-cell
+// code (thread t: column t of the tile, both planes).
+template <int ST>
+__device__ __forceinline__ void batch_bulk16_run(const CollideDesc &R, int p, int lb) {
+    using T = typename Codec<ST>::T;
+    const Geom &g = R.g;
+    const T *src = (const T *)R.f[p];
+    T *dst = (T *)R.f[1 - p];
+    const BodySlot &S = R.st->s[p];
+    const int tw = R.tx16, th = 128 / tw, gx = (g.nx + tw - 1) / tw, gy = (g.ny + th - 1) / th;
+    const int x0 = (lb % gx) * tw, y0 = ((lb / gx) % gy) * th, z0 = 2 * (lb / (gx * gy));
+    const int t = (int)threadIdx.x;
+    if (xpair_tile_ok<K1_FAR>(g, S, R.box, x0, y0, z0, tw, th)) {
+        const int hp = tw >> 1, r = t / hp;
+        xpair_cells<ST, K1_FAR>(g, src, dst, R.utop[p], S, R.hbox, R.box, x0 + 2 * (t % hp), y0 + r % th, z0 + r / th);
+        return;
+    }
+    k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, R.box, x0 + t % tw, y0 + t / tw, z0);
+    if (z0 + 1 < g.nz)
+        k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, R.box, x0 + t % tw, y0 + t / tw, z0 + 1);
+}
+
+__global__ void __launch_bounds__(128, 5) k_batch_collide16(const CollideDesc *__restrict__ runs,
+                                                            const int *__restrict__ prefix, int nruns, int p) {
+    constexpr int NW = (int)(sizeof(CollideDesc) / 4);
+    static_assert(sizeof(CollideDesc) % 4 == 0 && NW <= 128, "descriptor staged by one load per thread");
+    __shared__ CollideDesc R;
+    int lb;
+    const int r = block_run(prefix, nruns, lb);
+    if (threadIdx.x < NW)
+        reinterpret_cast<int *>(&R)[threadIdx.x] = __ldg(reinterpret_cast<const int *>(runs + r) + threadIdx.x);
+    __syncthreads();
+    if (R.storage == ST_F16) batch_bulk16_run<ST_F16>(R, p, lb);
+    else batch_bulk16_run<ST_BF16>(R, p, lb);
+}
 
 // Batched K2 + binning: per run nmom(r) moment blocks then its tiles, on
 // f(t+1) in buffer 1 - p and window slot 1 - p (the advanced body).
@@ -151,8 +193,18 @@ static int tile_blocks(int ex, int ey, int ez, int threads, int tx, int pz) {
     return ((ex + tx - 1) / tx) * ((ey + ty - 1) / ty) * ((ez + pz - 1) / pz);
 }
 
+bool bulk16_run(const RunDesc &r) {
+    return r.split && (r.storage == ST_F16 || (r.storage == ST_BF16 && !r.g.sround)) && r.g.nx % 2 == 0;
+}
+
+int bulk16_tile(const RunDesc &r) { return r.g.nx % 64 == 0 ? 64 : 32; }
+
 int blocks_bulk(const RunDesc &r, int threads) {
-    return r.split ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2) : 0;
+    return r.split && !bulk16_run(r) ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, threads, r.tx, 2) : 0;
+}
+
+int blocks_bulk16(const RunDesc &r) {
+    return bulk16_run(r) ? tile_blocks(r.g.nx, r.g.ny, r.g.nz, 128, bulk16_tile(r), 2) : 0;
 }
 
 int blocks_near(const RunDesc &r, int threads) {
@@ -169,7 +221,9 @@ int blocks_box_moments_bin(const RunDesc &r) {
 cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *prefix, int nruns, int p,
                                  int nblocks, int threads, int minb, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (phase == PHASE_NEAR)
+    if (phase == PHASE_BULK16)
+        k_batch_collide16<<<nblocks, 128, 0, s>>>(runs, prefix, nruns, p);
+    else if (phase == PHASE_NEAR)
         k_batch_collide<PHASE_NEAR, 2><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
     else if (minb == 2)
         k_batch_collide<PHASE_BULK, 2><<<nblocks, threads, 0, s>>>(runs, prefix, nruns, p);
@@ -179,7 +233,8 @@ cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *
 }
 
 bool is_batch_bulk_kernel(const void *fn) {
-    return fn == (const void *)k_batch_collide<PHASE_BULK, 2> || fn == (const void *)k_batch_collide<PHASE_BULK, 3>;
+    return fn == (const void *)k_batch_collide<PHASE_BULK, 2> || fn == (const void *)k_batch_collide<PHASE_BULK, 3> ||
+           fn == (const void *)k_batch_collide16;
 }
 
 cudaError_t launch_batch_box_moments_bin(const RunDesc *runs, const int *prefix, int nruns, int p, int nblocks,

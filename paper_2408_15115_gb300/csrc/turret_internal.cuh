@@ -210,7 +210,7 @@ struct RunDesc {
     int tx;              // collide+stream tile width (threads along x)
     MlpDev mlp;          // the force/torque network (predictor mode 2)
 };
-enum { PHASE_BULK = 0, PHASE_NEAR = 1 };
+enum { PHASE_BULK = 0, PHASE_NEAR = 1, PHASE_BULK16 = 2 };
 
 // Run r of block b of a batched launch (largest r < nruns with prefix[r] <=
 // b) by one warp: each pass reads 32 table entries at once and narrows the
@@ -255,7 +255,7 @@ struct CollideDesc {
     float *utop[2];
     DevState *st;
     const float *hbox;
-    int storage, split, tx, pad;
+    int storage, split, tx, tx16;  // tx16: tile width of the 16-bit x-pair bulk launch (bulk16)
 };
 // h arrays of the IBM cycles, selected per run in batched launches
 enum { HSEL_R0 = 0, HSEL_HL = 1, HSEL_HB = 2 };
@@ -377,7 +377,9 @@ bool valid_tile(int threads, int tx, int minb);
 cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, void *dst, const float *utop_in,
                                  float *utop_out, const DevState *st, int slot, const float *hbox,
                                  const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s);
-// Batched K1 of phase PHASE_BULK or PHASE_NEAR over nblocks blocks.
+// Batched K1 of phase PHASE_BULK, PHASE_NEAR or PHASE_BULK16 over nblocks
+// blocks (PHASE_BULK16: the far cells of 16-bit round-to-nearest runs on
+// x-adjacent pairs, 128-thread blocks; threads and minb are ignored).
 cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *prefix, int nruns, int p,
                                  int nblocks, int threads, int minb, cudaStream_t s);
 bool is_batch_bulk_kernel(const void *fn);
@@ -422,6 +424,9 @@ cudaError_t launch_batch_predict(const RunDesc *runs, int nruns, int slot, cudaS
 cudaError_t launch_batch_spread(const RunDesc *runs, const int *prefix, int nruns, int nblocks, cudaStream_t s);
 // Blocks of one run in each batched phase (host side, same formulas as the kernels).
 int blocks_bulk(const RunDesc &r, int threads);
+bool bulk16_run(const RunDesc &r);  // far cells in the 16-bit x-pair bulk launch
+int bulk16_tile(const RunDesc &r);  // its tile width
+int blocks_bulk16(const RunDesc &r);
 int blocks_near(const RunDesc &r, int threads);
 int blocks_particle_markers(const RunDesc &r);
 int blocks_box_moments_bin(const RunDesc &r);
