@@ -101,8 +101,10 @@ typedef struct {
  *   stochastic_rounding 1 (BF16 storage only): the collide+stream stores
  *               round each stored value up or down with probability equal to
  *               its distance from the other neighbour (unbiased rounding),
- *               the random bits a hash of (element, time step): results stay
- *               deterministic.  0: round to nearest even.
+ *               the random bits a hash of (element pair, time step), one hash
+ *               per pair of elements 2k, 2k + 1 of a population array:
+ *               results stay deterministic and independent of the kernel.
+ *               0: round to nearest even.
  *   staged_loads 1 (FP16 / BF16 storage): the bulk collide+stream moves its
  *               tiles' sources and results through shared memory with bulk
  *               tensor copies (a producer warp and four computing warps per

@@ -7,8 +7,8 @@
 // with prefix[r] <= b < prefix[r + 1].  The step graph has the shape of the
 // single-run graph with every node covering all runs:
 //
-//   batch stream: --fork--> bulk collide+stream (far cells: FP32 and stochastically
-//                           rounded runs, then 16-bit runs on x-pairs) ------> join
+//   batch stream: --fork--> bulk collide+stream (far cells: FP32 runs, then
+//                           16-bit runs on x-pairs) --------------------------> join
 //   side stream :       \-> near collide+stream -> particle + markers
 //                           -> support moments + tile lists -> interpolation
 //                           + rows of A -> cycles -> spread ---------------^

@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(256, MINB) k_collide_tiled(Geom g, const typen
 // Block b belongs to the run r with prefix[r] <= b < prefix[r + 1]; every run
 // keeps its own storage type, window, boundary conditions, relaxation times
 // and tile, read from its descriptor.  PHASE_BULK: the far cells of runs that
-// split (no blocks for the others; 16-bit round-to-nearest runs have theirs
-// in the PHASE_BULK16 launch); PHASE_NEAR: the near region of runs that
+// split (no blocks for the others; 16-bit runs have theirs in the
+// PHASE_BULK16 launch); PHASE_NEAR: the near region of runs that
 // split, the whole window (with forcing) of runs that do not.
 template <int PHASE, int ST>
 __device__ __forceinline__ void batch_k1_run(const CollideDesc &R, int p, int lb) {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *
     }
 }
 
-// Batched far-cell K1 of 16-bit round-to-nearest runs on x-adjacent pairs
+// Batched far-cell K1 of 16-bit runs on x-adjacent pairs
 // (lbm_xpair.cuh), with the register budget of the single-window x-pair
 // kernel (96 registers, five 128-thread blocks per SM) rather than the FP32
 // one the shared launch is held to.  A block owns a tile of tx16 x (128 /
@@ -99,7 +99,7 @@ __device__ __forceinline__ void batch_bulk16_run(const CollideDesc &R, int p, in
     const int tw = R.tx16, th = 128 / tw, gx = (g.nx + tw - 1) / tw, gy = (g.ny + th - 1) / th;
     const int x0 = (lb % gx) * tw, y0 = ((lb / gx) % gy) * th, z0 = 2 * (lb / (gx * gy));
     const int t = (int)threadIdx.x;
-    if (xpair_tile_ok<K1_FAR>(g, S, R.box, x0, y0, z0, tw, th)) {
+    if (xpair_tile_ok<K1_FAR, true>(g, S, R.box, x0, y0, z0, tw, th)) {
         const int hp = tw >> 1, r = t / hp;
         xpair_cells<ST, K1_FAR>(g, src, dst, R.utop[p], S, R.hbox, R.box, x0 + 2 * (t % hp), y0 + r % th, z0 + r / th);
         return;
@@ -194,7 +194,7 @@ static int tile_blocks(int ex, int ey, int ez, int threads, int tx, int pz) {
 }
 
 bool bulk16_run(const RunDesc &r) {
-    return r.split && (r.storage == ST_F16 || (r.storage == ST_BF16 && !r.g.sround)) && r.g.nx % 2 == 0;
+    return r.split && (r.storage == ST_F16 || r.storage == ST_BF16) && r.g.nx % 2 == 0;
 }
 
 int bulk16_tile(const RunDesc &r) { return r.g.nx % 64 == 0 ? 64 : 32; }

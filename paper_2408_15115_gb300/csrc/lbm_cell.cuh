@@ -37,8 +37,11 @@ namespace turret {
 // Stochastic rounding of BF16 stores (Geom::sround): the random bits come from
 // the PCG hash of Jarzynski and Olano, "Hash Functions for GPU Rendering"
 // (JCGT 9(3), 2020) -- a linear congruential step followed by O'Neill's PCG
-// RXS-M-XS output permutation -- applied to a key made of the stored element's
-// index and the time step, so a run is reproducible bit for bit.
+// RXS-M-XS output permutation -- applied to a key made of a stored element's
+// index and the time step, so a run is reproducible bit for bit.  One hash
+// serves the two elements 2k and 2k + 1 of a population array (x-adjacent
+// cells when nx is even): the low 16 bits the even one, the high 16 the odd
+// one, so every kernel gives an element the same bits however it pairs cells.
 __device__ __forceinline__ unsigned pcg_hash(unsigned v) {
     const unsigned state = v * 747796405u + 2891336453u;
     const unsigned word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
@@ -47,11 +50,19 @@ __device__ __forceinline__ unsigned pcg_hash(unsigned v) {
 __device__ __forceinline__ unsigned sr_key(int element, long long step) {
     return (unsigned)element + 0x9E3779B9u * (unsigned)step;
 }
+// The 16 random bits of element e (its index in the population arrays).
+__device__ __forceinline__ unsigned sr_bits(int e, long long step) {
+    const unsigned h = pcg_hash(sr_key(e & ~1, step));
+    return (e & 1) ? h >> 16 : h & 0xffffu;
+}
 // bf16 bits of r with its magnitude rounded up with probability equal to the
 // dropped fraction of the last kept bit (16 random bits added below the kept
 // bits, then truncated): unbiased, E[stored] = r.
+__device__ __forceinline__ unsigned short bf16_sr_bits(float r, unsigned rnd16) {
+    return (unsigned short)((__float_as_uint(r) + rnd16) >> 16);
+}
 __device__ __forceinline__ void store_bf16_sr(__nv_bfloat16 *p, float r, unsigned rnd16) {
-    *reinterpret_cast<unsigned short *>(p) = (unsigned short)((__float_as_uint(r) + rnd16) >> 16);
+    *reinterpret_cast<unsigned short *>(p) = bf16_sr_bits(r, rnd16);
 }
 
 __device__ __forceinline__ int zphys(int zl, int ring, int nz) {
@@ -570,8 +581,7 @@ __device__ __forceinline__ void k1_cell(const Geom &g, const typename Codec<ST>:
         const int own = oz + y * g.nx + x;
 #pragma unroll
         for (int i = 0; i < 27; ++i)
-            store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oz)), q[i],
-                          pcg_hash(sr_key(i * ncell + own, S.step)) & 0xffffu);
+            store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oz)), q[i], sr_bits(i * ncell + own, S.step));
         return;
     }
 #pragma unroll
@@ -769,13 +779,13 @@ __device__ __forceinline__ void k1_pair_collide_store(const Geom &g, typename Co
     const int oa = zphys(z[0], ring, g.nz) * (int)g.plane, ob = zphys(z[1], ring, g.nz) * (int)g.plane;
     typename Codec<ST>::T *d = dst + (y * g.nx + x);
     if (ST == ST_BF16 && g.sround) {
-        // one hash per population serves both cells (its low and high halves)
-        const int own = oa + y * g.nx + x;
+        const int own_a = oa + y * g.nx + x, own_b = ob + y * g.nx + x;
 #pragma unroll
         for (int i = 0; i < 27; ++i) {
-            const unsigned r = pcg_hash(sr_key(i * ncell + own, S.step));
-            if (on[0]) store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oa)), q[i].x, r & 0xffffu);
-            if (on[1]) store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + ob)), q[i].y, r >> 16);
+            if (on[0])
+                store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + oa)), q[i].x, sr_bits(i * ncell + own_a, S.step));
+            if (on[1])
+                store_bf16_sr(reinterpret_cast<__nv_bfloat16 *>(d + (i * ncell + ob)), q[i].y, sr_bits(i * ncell + own_b, S.step));
         }
         return;
     }

@@ -141,9 +141,6 @@ template <>
 __device__ __forceinline__ unsigned short to_bits<ST_BF16>(float r) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(r));
 }
-__device__ __forceinline__ unsigned short to_bits_sr(float r, unsigned rnd16) {
-    return (unsigned short)((__float_as_uint(r) + rnd16) >> 16);
-}
 
 __device__ __forceinline__ int wrap(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
@@ -388,14 +385,14 @@ __global__ void __launch_bounds__(STG_CONS + 32, 3)
         if (staged) {
             unsigned short *o = out + b * 27 * STG_OBOX + ty * STG_TX + tx;
             if (ST == ST_BF16 && g.sround) {
-                // the hash of k1_pair_collide_store: one per population and pair
-                const int own = zp[1] * (int)g.plane + y * g.nx + x;
+                // the random bits of every other path (sr_bits of the element;
+                // planes z0 and z0 + 1 are zp[1] and zp[0])
+                const int own_a = zp[1] * (int)g.plane + y * g.nx + x, own_b = zp[0] * (int)g.plane + y * g.nx + x;
                 const int ncell = (int)g.ncell;
 #pragma unroll
                 for (int i = 0; i < 27; ++i) {
-                    const unsigned r = pcg_hash(sr_key(i * ncell + own, S.step));
-                    o[i * STG_OBOX] = to_bits_sr(q[i].x, r & 0xffffu);
-                    o[i * STG_OBOX + STG_TY * STG_TX] = to_bits_sr(q[i].y, r >> 16);
+                    o[i * STG_OBOX] = bf16_sr_bits(q[i].x, sr_bits(i * ncell + own_a, S.step));
+                    o[i * STG_OBOX + STG_TY * STG_TX] = bf16_sr_bits(q[i].y, sr_bits(i * ncell + own_b, S.step));
                 }
             } else {
 #pragma unroll

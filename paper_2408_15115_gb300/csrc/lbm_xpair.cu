@@ -8,9 +8,8 @@
 // boundary planes, the plane entering the ring window, closed x / y faces
 // and, for far-cell launches, the near region) run the one-cell code over the
 // same cells (thread t: column t of the tile's 128, both planes).  Both are
-// the same arithmetic, so results are bitwise equal to the plain kernel.
-// BF16 with stochastic rounding keeps the plain kernel: its random bits are
-// keyed to the (z, z + 1) pairing.
+// the same arithmetic (and, with stochastic rounding, the same random bits),
+// so results are bitwise equal to the plain kernel.
 #include "lbm_xpair.cuh"
 
 namespace turret {
@@ -38,7 +37,7 @@ __global__ void __launch_bounds__(128, 5)
     }
     const BodySlot &S = st->s[slot];
     const int x0 = blockIdx.x * XP_TX, y0 = blockIdx.y * XP_TY, z0 = XP_TZ * blockIdx.z;
-    if (!xpair_tile_ok<MODE>(g, S, box, x0, y0, z0, XP_TX, XP_TY)) {
+    if (!xpair_tile_ok<MODE, false>(g, S, box, x0, y0, z0, XP_TX, XP_TY)) {
         // the one-cell path: thread t takes column t of the tile, both planes.
         // Inline and scalar: as an out-of-line call the whole kernel measured
         // 12 % slower, with the cell-pair code inline 9 % slower (its register
@@ -55,7 +54,7 @@ __global__ void __launch_bounds__(128, 5)
 // Host side.
 
 bool xpair_eligible(const Geom &g, int storage) {
-    return (storage == ST_F16 || (storage == ST_BF16 && !g.sround)) && g.nx % XP_TX == 0 && g.ny % XP_TY == 0 &&
+    return (storage == ST_F16 || storage == ST_BF16) && g.nx % XP_TX == 0 && g.ny % XP_TY == 0 &&
            g.nz % XP_TZ == 0 && g.nz >= 4;
 }
 

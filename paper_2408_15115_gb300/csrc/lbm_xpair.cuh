@@ -12,7 +12,8 @@
 // the sources (x + 1, x + 2) are the high half of the word at x and the low
 // half of the word at x + 2 (45 loads per pair, the extra words from the same
 // cache lines as the neighbouring threads').  Results leave as one 4-byte
-// word per population.  The arithmetic is the lane-generic collision, so a
+// word per population (BF16 with stochastic rounding: one hash per population
+// serves the pair, as sr_bits defines it).  The arithmetic is the lane-generic collision, so a
 // cell gets the bits it gets on any other path.
 #pragma once
 #include "lbm_cell.cuh"
@@ -56,13 +57,15 @@ __device__ __forceinline__ bool xp_meets_near(int c0, int len, int lo, int lo_w,
 }
 
 // Whether the tile [x0, x0 + tw) x [y0, y0 + th) x {z0, z0 + 1} (tw even)
-// can run on x-pairs: inside the window, every source on an interior plane
-// other than the one entering the ring window, no closed x / y face met, and
-// (MODE K1_FAR) no cell of the near region.
-template <int MODE>
+// can run on x-pairs: inside the window (EXTENT: checked here; otherwise the
+// launch guarantees it), every source on an interior plane other than the one
+// entering the ring window, no closed x / y face met, and (MODE K1_FAR) no
+// cell of the near region.
+template <int MODE, bool EXTENT>
 __device__ __forceinline__ bool xpair_tile_ok(const Geom &g, const BodySlot &S, const BoxGeom &box, int x0, int y0,
                                               int z0, int tw, int th) {
-    bool ok = (g.nx & 1) == 0 && x0 + tw <= g.nx && y0 + th <= g.ny && z0 >= 1 && z0 + 3 <= g.nz;
+    bool ok = z0 >= 1 && z0 + 3 <= g.nz;
+    if (EXTENT) ok = ok && (g.nx & 1) == 0 && x0 + tw <= g.nx && y0 + th <= g.ny;
 #pragma unroll
     for (int zs = -1; zs <= 2; ++zs) ok = ok && zphys(z0 + zs, S.ring, g.nz) != S.reseed;
     if (g.bc_x != BC_PERIODIC && (x0 == 0 || x0 + tw == g.nx)) ok = false;
@@ -118,6 +121,17 @@ __device__ __forceinline__ void xpair_cells(const Geom &g, const typename Codec<
     k1_pair_collide_store<ST, MODE, false>(g, dst, utop_out, S, hbox, box, x, y, z, on, q);
     unsigned *d = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned short *>(dst) + zphys(zl, S.ring, g.nz) * plane +
                                                y * nx + x);
+    if (ST == ST_BF16 && g.sround) {
+        // one hash per population serves the pair (sr_bits: low half x, high half x + 1)
+        const int own = zphys(zl, S.ring, g.nz) * plane + y * nx + x;  // even
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const unsigned h = pcg_hash(sr_key(i * ncell + own, S.step));
+            d[(size_t)i * (ncell / 2)] =
+                (unsigned)bf16_sr_bits(q[i].x, h & 0xffffu) | ((unsigned)bf16_sr_bits(q[i].y, h >> 16) << 16);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 27; ++i) d[(size_t)i * (ncell / 2)] = pack2<ST>(q[i]);
 }

@@ -378,8 +378,8 @@ cudaError_t launch_collide_tiled(const Geom &g, int storage, const void *src, vo
                                  float *utop_out, const DevState *st, int slot, const float *hbox,
                                  const BoxGeom &box, bool has_box, int threads, int tx, int minb, cudaStream_t s);
 // Batched K1 of phase PHASE_BULK, PHASE_NEAR or PHASE_BULK16 over nblocks
-// blocks (PHASE_BULK16: the far cells of 16-bit round-to-nearest runs on
-// x-adjacent pairs, 128-thread blocks; threads and minb are ignored).
+// blocks (PHASE_BULK16: the far cells of 16-bit runs on x-adjacent pairs,
+// 128-thread blocks; threads and minb are ignored).
 cudaError_t launch_batch_collide(int phase, const CollideDesc *runs, const int *prefix, int nruns, int p,
                                  int nblocks, int threads, int minb, cudaStream_t s);
 bool is_batch_bulk_kernel(const void *fn);
