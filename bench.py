@@ -279,7 +279,8 @@ def time_window(cfg, dev, K, W, kernel_launches, peaks, events=None):
 
     The coupled step is replayed K times after W warm-up steps (CUDA events on
     the context's stream); then the step's own collide+stream launches
-    (lbm_fluid_step: far cells + near region) `kernel_launches` times.
+    (lbm_fluid_step: far cells, with the near region beside them)
+    `kernel_launches` times.
     Returns the rates, the roofline fractions and the state."""
     import torch
 
@@ -642,8 +643,8 @@ def run_ours(args):
                       "replicas": world},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                        "kernel": "k_collide_stream_far_f32 + near-region k_collide_stream" if cfg["storage"] == "f32"
-                        else "k_collide_stream (far cells + near region)",
+                        "kernel": "k_collide_stream_far_f32, with the near-region k_collide_stream beside it"
+                        if cfg["storage"] == "f32" else "collide+stream (far cells, with the near region beside them)",
                         "algorithmic_bytes_per_launch": bpc * cells,
                         "us_per_launch": k_us, "glups_kernel": cells / (k_us / 1e6) / 1e9,
                         "peak_kind": peak_kind, "particle_steps_per_s": K / (ms / 1e3),

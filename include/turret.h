@@ -211,8 +211,11 @@ TURRET_API turret_status step(turret_ctx *c, int64_t n);
  * h_imm held at its current value; the particle does not move).  Launches
  * only the fused collide+stream kernels a coupled step uses for the window:
  * with a particle whose support box is small against the window, the
- * far-cell launch and then the near-region launch, in order on the context's
- * stream; otherwise one launch over the whole window.  Asynchronous.      */
+ * far-cell launch on the context's stream and the near-region launch beside
+ * it on the context's internal stream (the two write disjoint cells), joined
+ * before the next step, as in the coupled step; otherwise one launch over the
+ * whole window.  Asynchronous: ordered after earlier work on the context's
+ * stream, and later work on it is ordered after both launches.             */
 TURRET_API turret_status lbm_fluid_step(turret_ctx *c, int64_t n);
 
 /* Copies the particle state to the host (waits for the stream); returns the

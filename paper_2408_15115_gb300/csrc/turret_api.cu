@@ -967,19 +967,24 @@ extern "C" turret_status turret_query_predictor(turret_ctx *c, turret_predictor_
 extern "C" turret_status lbm_fluid_step(turret_ctx *c, int64_t n) {
     if (!c) return fail(c, TURRET_EINVAL, "NULL context");
     if (n < 0) return fail(c, TURRET_EINVAL, "negative step count");
-    // the kernels of the coupled step's collide+stream (far cells, then the
-    // near region, which also carries the body slot), so that timing this
-    // call times the step's own bulk launch
+    // the kernels of the coupled step's collide+stream as the step runs them:
+    // the far cells on the context stream and the near region (which also
+    // carries the body slot) beside them on the side stream, so that timing
+    // this call times the step's own collide+stream
     const bool split = c->has_particle && c->split && c->reinject.trigger == 0;
     for (int64_t k = 0; k < n; ++k) {
         const int p = (int)(c->step & 1);
         if (split) {
+            CK(cudaEventRecord(c->ev_fork, c->stream), "fluid step (fork)");
+            CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fluid step (fork)");
             CK(launch_collide_far(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate, p,
                                   c->ba.h, c->box, c->stream, src_map(c, p), dst_map(c, p)),
                "fluid step (far cells)");
             CK(launch_collide_stream(c->geom, c->storage, c->f[p], c->f[1 - p], c->utop[1 - p], c->utop[p], c->dstate,
-                                     p, 1 - p, c->ba.h, c->box, true, REGION_NEAR, c->stream),
+                                     p, 1 - p, c->ba.h, c->box, true, REGION_NEAR, c->side),
                "fluid step (near region)");
+            CK(cudaEventRecord(c->ev_join, c->side), "fluid step (join)");
+            CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "fluid step (join)");
         } else if (!c->has_particle) {
             CK(collide_window(c, p, c->stream), "fluid step");
         } else {
