@@ -64,22 +64,30 @@ __device__ __forceinline__ void mb_block(const Geom &g, const typename Codec<ST>
         int tot[2] = {0, 0};  // identical in every thread
         int par = 0;
         for (int group = 0; group < nm; group += CU * MB_THREADS) {
-            int pb[CU];
+            // skip chunks whose segments' stencil bases all miss [t0 - 3, t0 + 6];
+            // the test is the same in every thread, so a group with no chunk
+            // left is skipped whole, barrier included
+            bool reach[CU], any = false;
 #pragma unroll
             for (int u = 0; u < CU; ++u) {
                 const int chunk = group + u * MB_THREADS;
-                // skip chunks whose segments' stencil bases all miss [t0 - 3, t0 + 6]
-                bool reach = false;
+                reach[u] = false;
                 for (int sg = chunk / MARKER_SEG; sg < nseg && sg * MARKER_SEG < chunk + MB_THREADS; ++sg) {
                     const int *bb = mseg + 6 * sg;
                     bool in = true;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
                         in = in && __ldg(bb + 3 + a) + 3 >= t0[a] && __ldg(bb + a) <= t0[a] + TILE + 2;
-                    reach = reach || in;
+                    reach[u] = reach[u] || in;
                 }
-                const int k = chunk + tid;
-                pb[u] = (reach && k < nm) ? __ldg(mbase + k) : -1;  // culled chunks load nothing
+                any = any || reach[u];
+            }
+            if (!any) continue;
+            int pb[CU];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int k = group + u * MB_THREADS + tid;
+                pb[u] = (reach[u] && k < nm) ? __ldg(mbase + k) : -1;  // culled chunks load nothing
             }
             unsigned bal[CU][2];
             bool hit[CU][2];
