@@ -108,8 +108,9 @@ typedef struct {
  *   staged_loads 1 (FP16 / BF16 storage): the bulk collide+stream moves its
  *               tiles' sources and results through shared memory with bulk
  *               tensor copies (a producer warp and four computing warps per
- *               block) instead of plain 2-byte global loads and stores (0, the
- *               default, measured faster).  Results are identical.          */
+ *               block) instead of the default x-adjacent cell pairs with
+ *               4-byte global loads and stores (0, the default, measured
+ *               faster).  Results are identical.                           */
 typedef struct {
     int32_t force_scheme;
     int32_t rot_form;

@@ -2,30 +2,31 @@
 // its sources and results moved through shared memory by the tensor memory
 // accelerator (opt-in: flags.staged_loads).
 //
-// With FP16 / BF16 storage the plain collide+stream moves every population
-// with 2-byte accesses, which on this part stream at about 5 TB/s where 4- and
-// 16-byte accesses reach the copy bandwidth.  Here the data moves in bulk
-// tensor copies instead.  A block of four computing warps and one producer
-// warp works through a column of STG_TPB tiles of 32 x 4 x 2 cells (two
-// planes, one cell pair per thread, as in the plain kernel), stacked in z.
+// With FP16 / BF16 storage, cell pairs (z, z + 1) move every population with
+// 2-byte accesses, which on this part stream at about 5 TB/s where 4- and
+// 16-byte accesses reach the copy bandwidth (the default kernel therefore
+// pairs x-adjacent cells and moves 4-byte words, lbm_xpair.cuh).  Here the
+// data moves in bulk tensor copies instead.  A block of four computing warps
+// and one producer warp works through a column of STG_TPB tiles of 32 x 4 x 2
+// cells (two planes, one cell pair per thread), stacked in z.
 // Population i of a tile pulls from the tile shifted by -xi_i: the producer
 // issues the source boxes as 4-D bulk tensor copies (x, y, z, population)
 // into an input stage, each box widened to 48 x 4 x 2 so that it starts on a
 // 16-byte boundary at x0 - 8 and covers the +-1 x-shifts, the three
 // populations that differ only in xi_x in one copy (nine per tile).  The
 // computing warps read their 54 values at fixed shared-memory offsets, run the
-// same collision as the plain kernel (k1_pair_collide_store), write the 16-bit
+// same collision as every other path (k1_pair_collide_store), write the 16-bit
 // results to an output tile, and the producer stores it with one bulk tensor
 // copy.  Stages and output tiles are handed over with mbarriers (full / empty
 // per stage, full / empty per output tile).  Results are bitwise identical to
-// the plain kernel.
+// the default kernel.
 //
-// Measured on the 256 x 256 x 512 window, FP16: the plain kernel 0.91 ms per
-// launch, this pipeline 1.6 ms (1.2 ms in a variant without warp
-// specialisation): at 16-bit storage the collision's FP32 arithmetic (about
-// 440 operations per cell) sets a floor of its own, and the shared memory
-// that the staged tiles in flight need leaves too few computing warps per SM
-// to reach it.  The plain kernel therefore stays the default.
+// Measured on the 256 x 256 x 512 window, FP16: cell pairs with 2-byte
+// accesses 0.91 ms per launch, this pipeline 1.6 ms (1.2 ms in a variant
+// without warp specialisation), the default x-pair kernel 0.71 ms: at 16-bit
+// storage the collision's FP32 arithmetic sets a floor of its own, and the
+// shared memory that the staged tiles in flight need leaves too few computing
+// warps per SM to reach it.
 //
 // Periodic x / y edges: the copies read zeros outside the window; the few
 // elements a tile at a periodic edge needs from the far side (one column per
