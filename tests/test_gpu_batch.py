@@ -177,3 +177,49 @@ def test_batched_run_matches_oracle(force_eval):
     assert np.abs(a["F"] - o["F"]).max() / np.abs(o["F"]).max() < 1e-4
     assert np.abs(a["v"] - o["v"]).max() / np.abs(o["v"]).max() < 1e-5
     b.close()
+
+
+def _wide_16bit_runs():
+    """16-bit runs whose far cells fill the batched x-pair launch's 64-wide
+    tiles: an FP16 sliding window with a sphere and a BF16 one with
+    stochastically rounded stores and a tilted ellipsoid (both wide enough for
+    the far/near split), and an FP32 run beside them in the other bulk launch."""
+    from paper_2408_15115_gb300 import turret as T
+    out = []
+    V, Tr = I.sphere(4, 8.0)
+    t = T.Turret(64, 64, 96, 0.03, 2.0, (0, 0, -1e-4), 0, 0, 1, 2, sponge=6, slide=1, anchor_frac=0.3,
+                 storage="f16")
+    t.load_surface(V, Tr, (31.6, 32.2, 30.4), v0=(0.0, 0.0, -0.05), w0=(0.0, 0.001, 0.0))
+    out.append(t)
+    V, Tr = I.ellipsoid(5, (5.0, 3.0, 3.0))
+    V = I.rotate(V, "x", 25.0)
+    t = T.Turret(64, 64, 64, 0.04, 2.0, (0, 0, -1e-4), 0, 0, 1, 2, sponge=4, slide=1, anchor_frac=0.35,
+                 storage="bf16", flags={"stochastic_rounding": 1})
+    t.load_surface(V, Tr, (32.3, 31.4, 25.0), v0=(0.001, 0.0, -0.04))
+    out.append(t)
+    V, Tr = I.sphere(4, 8.0)
+    t = T.Turret(32, 32, 48, 0.05, 2.5, (0, 0, -1e-5), 1, 1, 1, 1)
+    t.load_surface(V, Tr, (15.5, 15.7, 30.2))
+    out.append(t)
+    return out
+
+
+def test_batched_16bit_xpair_launch_equals_runs_alone_bitwise():
+    # the far cells of the two 16-bit runs go through the batched x-pair
+    # launch (64-wide tiles, one-cell code at the boundary planes, the
+    # entering plane and the near region); the same runs alone take the
+    # single-window x-pair kernel: populations and particle state bit for bit
+    from paper_2408_15115_gb300 import turret as T
+    alone = _wide_16bit_runs()
+    for t in alone:
+        t.step(30)
+    ref = [_snapshot(t) for t in alone]
+    for t in alone:
+        t.close()
+    runs = _wide_16bit_runs()
+    b = T.Batch(runs)
+    b.step(30)
+    for t, r in zip(runs, ref):
+        _assert_same(_snapshot(t), r)
+    assert abs(runs[0].state()["origin"][2]) >= 1 and abs(runs[1].state()["origin"][2]) >= 1  # both slid
+    b.close()
