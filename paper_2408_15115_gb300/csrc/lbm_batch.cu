@@ -92,21 +92,22 @@ __global__ void __launch_bounds__(256, MINB) k_batch_collide(const CollideDesc *
 template <int ST>
 __device__ __forceinline__ void batch_bulk16_run(const CollideDesc &R, int p, int lb) {
     using T = typename Codec<ST>::T;
-    const Geom &g = R.g;
+    const Geom g = R.g;  // by value: operands in registers, not re-read from the staged descriptor
+    const BoxGeom box = R.box;
     const T *src = (const T *)R.f[p];
     T *dst = (T *)R.f[1 - p];
     const BodySlot &S = R.st->s[p];
     const int tw = R.tx16, th = 128 / tw, gx = (g.nx + tw - 1) / tw, gy = (g.ny + th - 1) / th;
     const int x0 = (lb % gx) * tw, y0 = ((lb / gx) % gy) * th, z0 = 2 * (lb / (gx * gy));
     const int t = (int)threadIdx.x;
-    if (xpair_tile_ok<K1_FAR, true>(g, S, R.box, x0, y0, z0, tw, th)) {
+    if (xpair_tile_ok<K1_FAR, true>(g, S, box, x0, y0, z0, tw, th)) {
         const int hp = tw >> 1, r = t / hp;
-        xpair_cells<ST, K1_FAR>(g, src, dst, R.utop[p], S, R.hbox, R.box, x0 + 2 * (t % hp), y0 + r % th, z0 + r / th);
+        xpair_cells<ST, K1_FAR>(g, src, dst, R.utop[p], S, R.hbox, box, x0 + 2 * (t % hp), y0 + r % th, z0 + r / th);
         return;
     }
-    k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, R.box, x0 + t % tw, y0 + t / tw, z0);
+    k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, x0 + t % tw, y0 + t / tw, z0);
     if (z0 + 1 < g.nz)
-        k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, R.box, x0 + t % tw, y0 + t / tw, z0 + 1);
+        k1_cell<ST, K1_FAR>(g, src, dst, R.utop[1 - p], R.utop[p], S, R.hbox, box, x0 + t % tw, y0 + t / tw, z0 + 1);
 }
 
 __global__ void __launch_bounds__(128, 5) k_batch_collide16(const CollideDesc *__restrict__ runs,
